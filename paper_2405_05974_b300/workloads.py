@@ -1,0 +1,55 @@
+"""The synthetic workloads: mechanism sizes, state distributions and seeds.
+
+The sizes mirror the paper's three QSS-reduced mechanisms (13-4-CH4,
+35-18-nC12H26, 55-33-nC7H16; Section 3.2) at the scale of the tiny,
+hydrocarbon and large workloads used throughout this package.  Every input
+is synthetic and seeded; see ``mechgen``.
+"""
+from .mechgen import MechConfig, StateConfig
+
+MECHS = {
+    # 9 transported + 3 QSS, 30 reversible reactions (5 third-body),
+    # one 2-species coupled QSS group.
+    "tiny": MechConfig(name="tiny_9_3_30", n_transported=9, n_qss=3, n_reactions=30,
+                       n_third_body=5, n_troe=0, qss_groups=[2, 1], seed=0,
+                       all_reversible=True, max_carbon=2),
+    # 35 + 18 species, 268 reactions (40 third-body, 25 Troe falloff),
+    # QSS groups of size <= 4.
+    "hydrocarbon": MechConfig(name="hc_35_18_268", n_transported=35, n_qss=18,
+                              n_reactions=268, n_third_body=40, n_troe=25,
+                              qss_groups=[4, 3, 2, 2, 2, 1, 1, 1, 1, 1], seed=1,
+                              max_carbon=4),
+    # 53 + 35 species, 1000 reactions (120 third-body, 80 Troe, 10% duplicates),
+    # one 6-species group, the others <= 3.
+    "large": MechConfig(name="large_53_35_1000", n_transported=53, n_qss=35,
+                        n_reactions=1000, n_third_body=120, n_troe=80,
+                        qss_groups=[6, 3, 3, 3, 2, 2, 2, 2] + [1] * 12, seed=2,
+                        dup_fraction=0.10, max_carbon=6),
+}
+
+STATES = {
+    "tiny": StateConfig(T_range=(1000.0, 2500.0), P_range_atm=(1.0, 1.0), P_log_uniform=False,
+                        dirichlet_alpha=0.5, seed=0),
+    "hydrocarbon": StateConfig(T_range=(900.0, 2800.0), P_range_atm=(1.0, 40.0),
+                               P_log_uniform=True, dirichlet_alpha=0.3,
+                               near_pure_fraction=0.05, seed=101),
+    "large": StateConfig(T_range=(700.0, 3000.0), P_range_atm=(1.0, 60.0), P_log_uniform=False,
+                         dirichlet_alpha=0.2, seed=102),
+    # implicit-step workload: hydrocarbon mechanism and state distribution
+    "implicit": StateConfig(T_range=(900.0, 2800.0), P_range_atm=(1.0, 40.0),
+                            P_log_uniform=True, dirichlet_alpha=0.3,
+                            near_pure_fraction=0.05, seed=103),
+}
+
+NCELLS = {"tiny": 4096, "hydrocarbon": 1 << 20, "large": 1 << 20, "implicit": 1 << 20}
+IMPLICIT_DT = 1.0e-6
+
+_cache = {}
+
+
+def mechanism(key: str) -> dict:
+    """The seeded mechanism dictionary of workload ``key`` (memoised)."""
+    from .mechgen import generate_mechanism
+    if key not in _cache:
+        _cache[key] = generate_mechanism(MECHS[key])
+    return _cache[key]
