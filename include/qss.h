@@ -1,0 +1,157 @@
+/*
+ * qss.h -- C ABI of the B300 QSS chemistry library (libqss.so).
+ *
+ * The library evaluates, per computational cell, the net production rates
+ * (wdot) of a quasi-steady-state (QSS) reduced reaction mechanism and the
+ * analytic chemical Jacobian of f = (wdot, Tdot) with respect to
+ * phi = (C_1..C_N, T), and advances cells by one implicit backward-Euler step.
+ * References are to Hassanaly et al., "Symbolic construction of the chemical
+ * Jacobian of quasi-steady state (QSS) chemistries for Exascale computing
+ * platforms":
+ *   rates of progress / production rates ... Section 2.1, Eqs. (progRates), (ReacMech)
+ *   QSS relations and their linear system .. Section 2.1 Eq. (QSSi), Section 2.3 Eq. (full_QSSsystem)
+ *   resolution order (Tarjan SCC) .......... Section 2.3, Appendix B
+ *   state vector and Jacobian .............. Section 3.1, Eq. (JacExptr)
+ *   chain rule through C_QSS ............... Section 3.2, Eq. (JQSS)
+ *   symbolic construction with CSE ......... Section 3.2.2
+ *
+ * Conventions shared by every entry point
+ *   - Units are SI: rho kg/m^3, T K, concentrations mol/m^3, wdot mol/m^3/s,
+ *     Tdot K/s, time s.
+ *   - Arrays are FP64 structure-of-arrays with a leading dimension ld >= ncells:
+ *       rho[c], T[c], Tdot[c]            c < ncells
+ *       Y[k * ld + c], wdot[k * ld + c]  k < N (transported species only)
+ *       jac[(i * (N+1) + j) * ld + c]    row i = d f_i, column j = d/d phi_j,
+ *                                        index N stands for temperature.
+ *   - "Device" arrays are device pointers on the mechanism's device; "host"
+ *     arrays are host pointers (page-locked memory gives full copy speed).
+ *   - The caller owns every array; the library never frees or retains one
+ *     beyond the call.  Only a mechanism's module and its staging buffers, and
+ *     a server's queues and buffers, belong to the library.
+ *   - Device-array calls are asynchronous on `stream` (a CUstream /
+ *     cudaStream_t of the mechanism's device; NULL = the legacy default
+ *     stream) and return once the work is enqueued.
+ *   - Return values report argument, launch and allocation errors (qss_status);
+ *     qss_last_error() gives a message for the calling thread.  Per-cell
+ *     numerical failures of the implicit step are reported in cell_status and
+ *     never abort the launch.
+ *   - ncells == 0 is valid and does nothing.
+ */
+#ifndef QSS_H
+#define QSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qss_mech_s* qss_mech_t;
+typedef struct qss_server_s* qss_server_t;
+
+typedef enum {
+  QSS_OK = 0,
+  QSS_ERR_INVALID_ARG = -1,   /* null pointer, ld < ncells, unknown option      */
+  QSS_ERR_MECH_FORMAT = -2,   /* unreadable or inconsistent artefact             */
+  QSS_ERR_CUDA = -3,          /* a CUDA driver call failed (message has details) */
+  QSS_ERR_OOM = -4,           /* device or host allocation failed                */
+  QSS_ERR_NOT_CONVERGED = -5, /* reserved                                        */
+  QSS_ERR_TIMEOUT = -6,       /* a wait exceeded its time limit                  */
+  QSS_ERR_BUDGET = -7,        /* request larger than the server's memory budget  */
+  QSS_ERR_UNIMPLEMENTED = -8
+} qss_status;
+
+/* Linear-algebra precision of the implicit step's Newton systems. */
+enum { QSS_LU_FP64 = 0, QSS_LU_FP32_IR = 1 };
+
+/* Per-cell outcome of qss_implicit_step. */
+enum {
+  QSS_CELL_CONVERGED = 0,   /* Newton converged                              */
+  QSS_CELL_MAXITER = 1,     /* iteration cap reached                         */
+  QSS_CELL_NONFINITE = 2,   /* an iterate or residual became NaN/Inf         */
+  QSS_CELL_SINGULAR = 3     /* zero pivot in the Newton matrix                */
+};
+
+/* ---------------------------------------------------------------------------
+ * Mechanisms.  An artefact directory is produced by the mechanism compiler
+ * (paper_2405_05974_b300.qssc): mech.cubin (sm_103a) and meta.txt.
+ * qss_mech_load loads it on `device` (the primary context, shared with the
+ * CUDA runtime) and returns a handle owned by the caller, released with
+ * qss_mech_free.  Errors: QSS_ERR_INVALID_ARG (null arguments),
+ * QSS_ERR_MECH_FORMAT (missing/inconsistent files), QSS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out);
+void qss_mech_free(qss_mech_t mech);
+
+/* Sizes of a loaded mechanism and its molar masses W[N] (kg/mol; the pointer
+ * stays valid until qss_mech_free).  Any output pointer may be NULL. */
+int qss_mech_info(qss_mech_t mech, int* n_transported, int* n_qss, int* n_reactions,
+                  const double** W_host);
+
+/* Production rates (Eqs. progRates, ReacMech, with the QSS concentrations from
+ * Eq. full_QSSsystem solved in SCC order).  Device arrays rho, T, Y (inputs),
+ * wdot [N][ld] (output), Tdot [ld] (output, may be NULL). */
+int qss_wdot(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho, const double* T,
+             const double* Y, double* wdot, double* Tdot, void* stream);
+
+/* Analytic Jacobian, Eq. (JacExptr) with the chain rule of Eq. (JQSS), of
+ * f = (wdot, Tdot) with respect to phi = (C, T), constant volume.  Device
+ * arrays; jac [(N+1)^2][ld] is required, wdot [N][ld] and Tdot [ld] may be
+ * NULL (they are computed anyway). */
+int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
+                 const double* T, const double* Y, double* jac, double* wdot, double* Tdot,
+                 void* stream);
+
+/* The same as qss_jacobian for HOST arrays with ld = ncells.  The batch is
+ * processed in chunks of `chunk` cells (0 = automatic) through two device
+ * staging buffers owned by the mechanism handle, with host->device copies,
+ * kernels and device->host copies of consecutive chunks overlapped on two
+ * streams.  Synchronous: returns when all outputs are in host memory.
+ * `stream` is unused (reserved).  Errors: QSS_ERR_OOM if the staging buffers
+ * cannot be allocated. */
+int qss_jacobian_host(qss_mech_t mech, int64_t ncells, const double* rho, const double* T,
+                      const double* Y, double* jac, double* wdot, double* Tdot, int64_t chunk,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Implicit step.  One backward-Euler step at constant volume (rho fixed) of
+ * dC/dt = wdot, dT/dt = Tdot: Newton on G(phi) = phi - phi0 - dt f(phi) with
+ * the matrix I - dt J (the analytic Jacobian re-evaluated every iteration).
+ * The Newton update is accepted when its weighted RMS norm with weights
+ * 1 / (rtol |phi_i| + atol_i) is <= 1.  precision = QSS_LU_FP64 factors the
+ * matrix with partial pivoting in FP64; QSS_LU_FP32_IR factors it in FP32
+ * and refines the solution with FP64 residuals until the correction is below
+ * refine_tol relative (or max_refine sweeps); rates, equilibrium constants,
+ * the QSS solve and the Newton residual stay FP64 in both forms.
+ * T [ld] and Y [N][ld] are updated in place (device arrays); dt is a device
+ * array [ld] (dt_stride = 1) or a single device value (dt_stride = 0).
+ * iters and cell_status (device int32 [ld]) may be NULL.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int max_iter;        /* Newton iteration cap (default 20)                 */
+  double rtol;         /* default 1e-12                                      */
+  double atol_C;       /* mol/m^3, default 1e-20                             */
+  double atol_T;       /* K, default 1e-10                                   */
+  int max_refine;      /* FP32_IR refinement sweeps (default 10)             */
+  double refine_tol;   /* FP32_IR relative correction target (default 1e-14) */
+} qss_newton_opts;
+
+int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt,
+                      int dt_stride, const double* rho, double* T, double* Y, int precision,
+                      const qss_newton_opts* opts, int32_t* iters, int32_t* cell_status,
+                      void* stream);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char* qss_last_error(void);
+
+/* Measured FP64 fused-multiply-add throughput of `device` in TFLOP/s
+ * (2 flops per FMA), from a dependent-chain microbenchmark run for about
+ * `millis` milliseconds.  Used as the FP64 roofline denominator. */
+int qss_measure_fp64_peak(int device, int millis, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSS_H */

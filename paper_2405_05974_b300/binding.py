@@ -1,0 +1,195 @@
+"""Python binding of libqss.so (ctypes; argument marshalling only).
+
+Every computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no fallback: if the shared library or the
+mechanism artefact is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqss.so")
+
+QSS_OK = 0
+QSS_ERRORS = {-1: "INVALID_ARG", -2: "MECH_FORMAT", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
+              -6: "TIMEOUT", -7: "BUDGET", -8: "UNIMPLEMENTED"}
+QSS_LU_FP64 = 0
+QSS_LU_FP32_IR = 1
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+class QSSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qss error {code} ({QSS_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("atol_C", ctypes.c_double),
+                ("atol_T", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
+
+
+def lib():
+    """The loaded libqss.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2405_05974_b300.build_ext`")
+        L = ctypes.CDLL(LIB_PATH)
+        L.qss_last_error.restype = ctypes.c_char_p
+        L.qss_mech_load.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.qss_mech_free.argtypes = [_vp]
+        L.qss_mech_free.restype = None
+        L.qss_mech_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+        L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.qss_jacobian_host.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]
+        L.qss_implicit_step.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                                        ctypes.POINTER(NewtonOpts), _vp, _vp, _vp]
+        L.qss_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != QSS_OK:
+        raise QSSError(rc, lib().qss_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def measure_fp64_peak(device: int = 0, millis: int = 200) -> float:
+    out = ctypes.c_double()
+    check(lib().qss_measure_fp64_peak(device, millis, ctypes.byref(out)))
+    return out.value
+
+
+class Mechanism:
+    """A compiled mechanism loaded on one GPU."""
+
+    def __init__(self, artefact_dir: str, device: int = 0):
+        self.dir = artefact_dir
+        self.device = device
+        h = _vp()
+        check(lib().qss_mech_load(artefact_dir.encode(), device, ctypes.byref(h)))
+        self.h = h
+        N, Q, M = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        W = ctypes.POINTER(ctypes.c_double)()
+        check(lib().qss_mech_info(h, ctypes.byref(N), ctypes.byref(Q), ctypes.byref(M), ctypes.byref(W)))
+        self.N, self.Q, self.M = N.value, Q.value, M.value
+        self.W = [W[i] for i in range(self.N)]
+
+    @classmethod
+    def from_dict(cls, mech: dict, device: int = 0, **build_kw):
+        from .qssc.build import build_mechanism
+        return cls(build_mechanism(mech, **build_kw), device)
+
+    @property
+    def n(self):
+        return self.N + 1
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qss_mech_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ checks
+    def _check_state(self, rho, T, Y, ncells):
+        for nm, t in (("rho", rho), ("T", T), ("Y", Y)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError(f"{nm} must be a contiguous float64 CUDA tensor")
+        ld = T.shape[0]
+        if rho.shape != (ld,) or Y.shape != (self.N, ld):
+            raise ValueError("shape mismatch: rho[ld], T[ld], Y[N][ld]")
+        nc = ld if ncells is None else int(ncells)
+        return nc, ld
+
+    def _out(self, t, shape, like):
+        if t is None:
+            return torch.empty(shape, dtype=torch.float64, device=like.device)
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"output must be a contiguous float64 CUDA tensor of shape {shape}")
+        return t
+
+    # -------------------------------------------------------------- calls
+    def wdot(self, rho, T, Y, wdot=None, Tdot=None, ncells=None, stream=None, want_Tdot=True):
+        nc, ld = self._check_state(rho, T, Y, ncells)
+        wdot = self._out(wdot, (self.N, ld), T)
+        if want_Tdot:
+            Tdot = self._out(Tdot, (ld,), T)
+        check(lib().qss_wdot(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(wdot), _ptr(Tdot),
+                             _stream(stream)))
+        return wdot, Tdot
+
+    def jacobian(self, rho, T, Y, jac=None, wdot=None, Tdot=None, ncells=None, stream=None,
+                 want_rates=True):
+        nc, ld = self._check_state(rho, T, Y, ncells)
+        n = self.n
+        jac = self._out(jac, (n * n, ld), T)
+        if want_rates:
+            wdot = self._out(wdot, (self.N, ld), T)
+            Tdot = self._out(Tdot, (ld,), T)
+        check(lib().qss_jacobian(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
+                                 _ptr(Tdot), _stream(stream)))
+        return jac, wdot, Tdot
+
+    def jacobian_host(self, rho, T, Y, jac=None, wdot=None, Tdot=None, chunk=0):
+        """Host (CPU, ideally pinned) float64 tensors; synchronous."""
+        for nm, t in (("rho", rho), ("T", T), ("Y", Y)):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous float64 host tensor")
+        nc = T.shape[0]
+        n = self.n
+        if jac is None:
+            jac = torch.empty((n * n, nc), dtype=torch.float64, pin_memory=True)
+        check(lib().qss_jacobian_host(self.h, nc, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
+                                      _ptr(Tdot), chunk, None))
+        return jac, wdot, Tdot
+
+    def implicit_step(self, rho, T, Y, dt, precision=QSS_LU_FP64, ncells=None, iters=None,
+                      status=None, opts: Optional[NewtonOpts] = None, stream=None):
+        """Advance (T, Y) in place by one backward-Euler step of size dt."""
+        nc, ld = self._check_state(rho, T, Y, ncells)
+        if not isinstance(dt, torch.Tensor):
+            dt = torch.full((1,), float(dt), dtype=torch.float64, device=T.device)
+        if not (dt.is_cuda and dt.dtype == torch.float64):
+            raise ValueError("dt must be a float64 CUDA tensor")
+        stride = 1 if dt.numel() > 1 else 0
+        if stride and dt.shape[0] < ld:
+            raise ValueError("dt must have ld entries or one")
+        if iters is None:
+            iters = torch.empty(ld, dtype=torch.int32, device=T.device)
+        if status is None:
+            status = torch.empty(ld, dtype=torch.int32, device=T.device)
+        check(lib().qss_implicit_step(self.h, nc, ld, _ptr(dt), stride, _ptr(rho), _ptr(T), _ptr(Y),
+                                      precision, ctypes.byref(opts) if opts is not None else None,
+                                      _ptr(iters), _ptr(status), _stream(stream)))
+        return iters, status

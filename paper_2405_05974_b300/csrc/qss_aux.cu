@@ -1,0 +1,21 @@
+// Auxiliary kernels of libqss (compiled to qss_aux.cubin for sm_103a).
+//
+// qss_fp64_fma_probe: dependent FMA chains, 8 independent chains per thread,
+// for the FP64 roofline denominator.  Each thread performs iters * 8 FMAs and
+// writes one value so that nothing is eliminated.
+extern "C" __global__ void qss_fp64_fma_probe(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+  for (int it = 0; it < iters; ++it) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+// Writes `n` doubles (used to evict the L2 between timed iterations).
+extern "C" __global__ void qss_l2_flush(double* buf, long long n, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    buf[i] = v + (double)i;
+}

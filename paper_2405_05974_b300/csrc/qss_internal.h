@@ -1,0 +1,42 @@
+// Internal declarations shared by the runtime's translation units.
+#pragma once
+#include <cuda.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qss.h"
+
+struct qss_mech_s {
+  int device = 0;
+  CUdevice dev = 0;
+  CUcontext ctx = nullptr;
+  CUmodule mod = nullptr;
+  CUfunction f_wdot = nullptr, f_jac = nullptr;
+  CUfunction f_newton[2] = {nullptr, nullptr};   // FP64 LU, FP32 LU + FP64 refinement
+  int N = 0, Q = 0, M = 0, block = 0;
+  std::vector<double> W;
+  std::string name, digest, dir;
+  // host-array path: two staging buffers and streams, one call at a time
+  std::mutex mu;
+  CUdeviceptr stage[2] = {0, 0};
+  size_t stage_bytes = 0;
+  CUstream st[2] = {nullptr, nullptr};
+};
+
+namespace qss {
+extern thread_local std::string g_err;
+int fail(int code, const std::string& msg);
+int cu_fail(CUresult r, const char* what);
+std::string lib_dir();
+int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx);
+int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
+                 CUstream stream, unsigned shmem);
+}  // namespace qss
+
+#define CU_TRY(call)                                   \
+  do {                                                 \
+    CUresult r__ = (call);                             \
+    if (r__ != CUDA_SUCCESS) return qss::cu_fail(r__, #call); \
+  } while (0)

@@ -1,0 +1,276 @@
+// libqss.so: host runtime of the B300 QSS chemistry library (C ABI in qss.h).
+//
+// Written against the CUDA driver API only: mechanism artefacts are cubins
+// (sm_103a) loaded into the device's primary context, which the CUDA runtime
+// (and PyTorch) share, so device pointers and streams pass through unchanged.
+#include "qss.h"
+
+#include <cuda.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "qss_internal.h"
+#include "qss_driver.h"
+
+namespace qss {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cu_fail(CUresult r, const char* what) {
+  const char* s = nullptr;
+  if (drv().ok) drv().cuGetErrorString(r, &s);
+  return fail(QSS_ERR_CUDA, std::string(what) + ": " + (s ? s : "unknown CUDA error"));
+}
+
+std::string lib_dir() {
+  Dl_info info;
+  if (dladdr((void*)&lib_dir, &info) && info.dli_fname) {
+    std::string p(info.dli_fname);
+    size_t k = p.rfind('/');
+    return k == std::string::npos ? std::string(".") : p.substr(0, k);
+  }
+  return ".";
+}
+
+int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx) {
+  if (!drv().ok) return fail(QSS_ERR_CUDA, "CUDA driver (libcuda.so.1) is not available");
+  CU_TRY(drv().cuInit(0));
+  int count = 0;
+  CU_TRY(drv().cuDeviceGetCount(&count));
+  if (device < 0 || device >= count) return fail(QSS_ERR_INVALID_ARG, "device ordinal out of range");
+  CU_TRY(drv().cuDeviceGet(dev, device));
+  CU_TRY(drv().cuDevicePrimaryCtxRetain(ctx, *dev));
+  CU_TRY(drv().cuCtxSetCurrent(*ctx));
+  return QSS_OK;
+}
+
+int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
+                 CUstream stream, unsigned shmem) {
+  if (ncells == 0) return QSS_OK;
+  int64_t grid = (ncells + block - 1) / block;
+  if (grid > INT_MAX) return fail(QSS_ERR_INVALID_ARG, "ncells too large for one launch");
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  CU_TRY(drv().cuLaunchKernel(f, (unsigned)grid, 1, 1, (unsigned)block, 1, 1, shmem, stream, args,
+                        nullptr));
+  return QSS_OK;
+}
+
+}  // namespace qss
+
+using namespace qss;
+
+extern "C" {
+
+const char* qss_last_error(void) { return g_err.c_str(); }
+
+int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
+  if (!artefact_dir || !out) return fail(QSS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  std::string dir(artefact_dir);
+  std::ifstream meta(dir + "/meta.txt");
+  if (!meta) return fail(QSS_ERR_MECH_FORMAT, "cannot open " + dir + "/meta.txt");
+  qss_mech_s* m = new qss_mech_s();
+  m->dir = dir;
+  std::string line;
+  while (std::getline(meta, line)) {
+    std::istringstream ls(line);
+    std::string key;
+    ls >> key;
+    if (key == "name") ls >> m->name;
+    else if (key == "digest") ls >> m->digest;
+    else if (key == "N") ls >> m->N;
+    else if (key == "Q") ls >> m->Q;
+    else if (key == "M") ls >> m->M;
+    else if (key == "block") ls >> m->block;
+    else if (key == "W") {
+      double w;
+      while (ls >> w) m->W.push_back(w);
+    }
+  }
+  if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N) {
+    delete m;
+    return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
+  }
+  int rc = ctx_for_device(device, &m->dev, &m->ctx);
+  if (rc) { delete m; return rc; }
+  m->device = device;
+  CUresult r = drv().cuModuleLoad(&m->mod, (dir + "/mech.cubin").c_str());
+  if (r != CUDA_SUCCESS) {
+    drv().cuDevicePrimaryCtxRelease(m->dev);
+    delete m;
+    return cu_fail(r, "drv().cuModuleLoad(mech.cubin)");
+  }
+  const char* need[] = {"qss_wdot_kernel", "qss_jac_kernel"};
+  CUfunction* slot[] = {&m->f_wdot, &m->f_jac};
+  for (int i = 0; i < 2; ++i) {
+    r = drv().cuModuleGetFunction(slot[i], m->mod, need[i]);
+    if (r != CUDA_SUCCESS) {
+      drv().cuModuleUnload(m->mod);
+      drv().cuDevicePrimaryCtxRelease(m->dev);
+      delete m;
+      return fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + need[i]);
+    }
+  }
+  // optional kernels (implicit step)
+  if (drv().cuModuleGetFunction(&m->f_newton[0], m->mod, "qss_newton_fp64_kernel") != CUDA_SUCCESS)
+    m->f_newton[0] = nullptr;
+  if (drv().cuModuleGetFunction(&m->f_newton[1], m->mod, "qss_newton_fp32ir_kernel") != CUDA_SUCCESS)
+    m->f_newton[1] = nullptr;
+  *out = m;
+  return QSS_OK;
+}
+
+void qss_mech_free(qss_mech_t m) {
+  if (!m) return;
+  drv().cuCtxSetCurrent(m->ctx);
+  for (int b = 0; b < 2; ++b) {
+    if (m->stage[b]) drv().cuMemFree(m->stage[b]);
+    if (m->st[b]) drv().cuStreamDestroy(m->st[b]);
+  }
+  if (m->mod) drv().cuModuleUnload(m->mod);
+  drv().cuDevicePrimaryCtxRelease(m->dev);
+  delete m;
+}
+
+int qss_mech_info(qss_mech_t m, int* n_transported, int* n_qss, int* n_reactions,
+                  const double** W_host) {
+  if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
+  if (n_transported) *n_transported = m->N;
+  if (n_qss) *n_qss = m->Q;
+  if (n_reactions) *n_reactions = m->M;
+  if (W_host) *W_host = m->W.data();
+  return QSS_OK;
+}
+
+static int check_cells(qss_mech_t m, int64_t ncells, int64_t ld) {
+  if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
+  if (ncells < 0) return fail(QSS_ERR_INVALID_ARG, "ncells < 0");
+  if (ld < ncells) return fail(QSS_ERR_INVALID_ARG, "ld < ncells");
+  return QSS_OK;
+}
+
+int qss_wdot(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+             const double* Y, double* wdot, double* Tdot, void* stream) {
+  int rc = check_cells(m, ncells, ld);
+  if (rc) return rc;
+  if (ncells == 0) return QSS_OK;
+  if (!rho || !T || !Y || !wdot) return fail(QSS_ERR_INVALID_ARG, "null array");
+  long long nc = ncells, l = ld;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot};
+  return launch_cells(m, m->f_wdot, ncells, m->block, args, (CUstream)stream, 0);
+}
+
+int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                 const double* Y, double* jac, double* wdot, double* Tdot, void* stream) {
+  int rc = check_cells(m, ncells, ld);
+  if (rc) return rc;
+  if (ncells == 0) return QSS_OK;
+  if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
+  long long nc = ncells, l = ld;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot};
+  return launch_cells(m, m->f_jac, ncells, m->block, args, (CUstream)stream, 0);
+}
+
+static int copy2d(void* dst, bool dst_host, size_t dpitch, const void* src, bool src_host,
+                  size_t spitch, size_t width, size_t height, CUstream s) {
+  CUDA_MEMCPY2D c;
+  std::memset(&c, 0, sizeof(c));
+  if (src_host) {
+    c.srcMemoryType = CU_MEMORYTYPE_HOST;
+    c.srcHost = src;
+  } else {
+    c.srcMemoryType = CU_MEMORYTYPE_DEVICE;
+    c.srcDevice = (CUdeviceptr)src;
+  }
+  if (dst_host) {
+    c.dstMemoryType = CU_MEMORYTYPE_HOST;
+    c.dstHost = dst;
+  } else {
+    c.dstMemoryType = CU_MEMORYTYPE_DEVICE;
+    c.dstDevice = (CUdeviceptr)dst;
+  }
+  c.srcPitch = spitch;
+  c.dstPitch = dpitch;
+  c.WidthInBytes = width;
+  c.Height = height;
+  CU_TRY(drv().cuMemcpy2DAsync(&c, s));
+  return QSS_OK;
+}
+
+int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const double* T,
+                      const double* Y, double* jac, double* wdot, double* Tdot, int64_t chunk,
+                      void* stream) {
+  (void)stream;
+  int rc = check_cells(m, ncells, ncells);
+  if (rc) return rc;
+  if (ncells == 0) return QSS_OK;
+  if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
+  std::lock_guard<std::mutex> lock(m->mu);
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  const int N = m->N, n = N + 1;
+  int64_t S = chunk > 0 ? chunk : 65536;
+  S = std::min<int64_t>(S, ncells);
+  S = (S + 31) / 32 * 32;
+  const size_t per_cell = (size_t)(2 + N + N + 1 + n * n);
+  const size_t need = per_cell * (size_t)S * sizeof(double);
+  if (m->stage_bytes < need) {
+    for (int b = 0; b < 2; ++b) {
+      if (m->stage[b]) { drv().cuMemFree(m->stage[b]); m->stage[b] = 0; }
+      CUresult r = drv().cuMemAlloc(&m->stage[b], need);
+      if (r != CUDA_SUCCESS) {
+        m->stage_bytes = 0;
+        return fail(QSS_ERR_OOM, "cannot allocate host-path staging buffers");
+      }
+    }
+    m->stage_bytes = need;
+  }
+  for (int b = 0; b < 2; ++b)
+    if (!m->st[b]) CU_TRY(drv().cuStreamCreate(&m->st[b], CU_STREAM_NON_BLOCKING));
+  const size_t P = (size_t)S * sizeof(double);
+  int64_t nchunks = (ncells + S - 1) / S;
+  for (int64_t ci = 0; ci < nchunks; ++ci) {
+    int b = (int)(ci & 1);
+    CUstream s = m->st[b];
+    int64_t c0 = ci * S;
+    int64_t cs = std::min<int64_t>(S, ncells - c0);
+    double* base = (double*)m->stage[b];
+    double* d_rho = base;
+    double* d_T = base + S;
+    double* d_Y = base + 2 * S;
+    double* d_w = base + (2 + N) * S;
+    double* d_Td = base + (2 + 2 * N) * S;
+    double* d_J = base + (3 + 2 * N) * S;
+    const size_t w = (size_t)cs * sizeof(double), hp = (size_t)ncells * sizeof(double);
+    if ((rc = copy2d(d_rho, false, P, rho + c0, true, hp, w, 1, s))) return rc;
+    if ((rc = copy2d(d_T, false, P, T + c0, true, hp, w, 1, s))) return rc;
+    if ((rc = copy2d(d_Y, false, P, Y + c0, true, hp, w, N, s))) return rc;
+    long long nc = cs, l = S;
+    double* wp = d_w;
+    double* tp = d_Td;
+    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp};
+    if ((rc = launch_cells(m, m->f_jac, cs, m->block, args, s, 0))) return rc;
+    if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, (size_t)n * n, s))) return rc;
+    if (wdot && (rc = copy2d(wdot + c0, true, hp, d_w, false, P, w, N, s))) return rc;
+    if (Tdot && (rc = copy2d(Tdot + c0, true, hp, d_Td, false, P, w, 1, s))) return rc;
+  }
+  CU_TRY(drv().cuStreamSynchronize(m->st[0]));
+  CU_TRY(drv().cuStreamSynchronize(m->st[1]));
+  return QSS_OK;
+}
+
+}  // extern "C"

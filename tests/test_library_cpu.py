@@ -1,0 +1,112 @@
+"""CPU-side checks of the boundary and the mechanism compiler (no GPU)."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_05974_b300 import binding, build_ext, mechgen, workloads
+from paper_2405_05974_b300.qssc import build as qbuild
+from paper_2405_05974_b300.qssc import graph as qgraph
+from paper_2405_05974_b300.qssc import mech as qmech
+from paper_2405_05974_b300.qssc import model as qmodel
+from tests import mechs as hm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(qss_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    build_ext.build()
+    L = ctypes.CDLL(binding.LIB_PATH)
+    names = _declared_functions()
+    assert len(names) >= 9
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+def test_calls_without_driver_report_errors():
+    L = binding.lib()
+    h = ctypes.c_void_p()
+    rc = L.qss_mech_load(b"/nonexistent", 0, ctypes.byref(h))
+    assert rc == -2
+    art = qbuild.build_mechanism(workloads.mechanism("tiny"))
+    rc = L.qss_mech_load(art.encode(), 0, ctypes.byref(h))
+    assert rc in (-3, 0)   # no driver on a CPU-only machine
+    if rc:
+        assert L.qss_last_error()
+    assert L.qss_wdot(None, 1, 1, None, None, None, None, None, None) == -1
+
+
+def test_compiler_tarjan_fig2():
+    g = json.load(open(os.path.join(GOLDEN, "tarjan_fig2.json")))
+    names = sorted({v for e in g["edges_as_drawn"] for v in e})
+    ix = {nm: i for i, nm in enumerate(names)}
+    adj = [[] for _ in names]
+    for a, b in g["edges_as_drawn"]:
+        adj[ix[a]].append(ix[b])
+    comps = qgraph.tarjan_scc(adj)
+    assert sorted(sorted(names[v] for v in c) for c in comps) == sorted(sorted(c) for c in g["expected_sccs"])
+    pos = {v: ci for ci, c in enumerate(comps) for v in c}
+    for u, nb in enumerate(adj):
+        for v in nb:
+            assert pos[v] <= pos[u]
+    ce = qgraph.condensed_edges(adj, comps)
+    assert len(ce) == 1
+    # agrees with the oracle's independent implementation
+    oc = oracle.tarjan(len(names), [(ix[a], ix[b]) for a, b in g["edges_as_drawn"]])
+    assert sorted(map(sorted, oc)) == sorted(map(sorted, comps))
+
+
+@pytest.mark.parametrize("key", ["tiny", "hydrocarbon"])
+def test_symbolic_model_matches_oracle(key):
+    """The compiler's symbolic model, evaluated in Python, against the oracle."""
+    m = workloads.mechanism(key)
+    ir = qmech.parse(m)
+    mod = qmodel.build_model(ir)
+    om = oracle.OracleMech(m)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], 4)
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    C = om.conc(rho, Y)
+    N = ir.N
+    n = N + 1
+    outs = list(mod.wdot) + [mod.Tdot] + [mod.jac[i][j] for i in range(n) for j in range(n)]
+    for c in range(4):
+        env = {mod.C[k]: C[k, c] for k in range(N)}
+        env[mod.T] = T[c]
+        v = np.array(mod.g.evaluate(outs, env, fns=mod.bind))
+        assert np.all(np.abs(v[:N] - ref["wdot"][:, c]) <= 2 * eb["wdot"][:, c] + 1e-300)
+        assert abs(v[N] - ref["Tdot"][c]) <= 2 * eb["Tdot"][c]
+        assert np.all(np.abs(v[N + 1:] - ref["jac"][:, c]) <= 2 * eb["jac"][:, c] + 1e-300)
+    assert sorted(map(len, mod.groups)) == sorted(map(len, m["planned_qss_groups"]))
+
+
+def test_compiler_rejects_quadratic_qss_coupling():
+    sp = [hm.species("A", {"H": 2}), hm.species("N2", {"N": 2}),
+          hm.species("q1", {"H": 1}, qss=True), hm.species("q2", {"H": 1}, qss=True)]
+    m = hm.mech("quad", sp, [hm.reaction({"q1": 1, "q2": 1}, {"A": 1}, 1e12)])
+    with pytest.raises(qmech.MechanismError):
+        qmech.parse(m)
+
+
+def test_artefact_build_tiny():
+    art = qbuild.build_mechanism(workloads.mechanism("tiny"))
+    assert os.path.exists(os.path.join(art, "mech.cubin"))
+    meta = qbuild.load_meta(art)
+    assert meta["N"] == 9 and meta["Q"] == 3 and meta["M"] == 30
+    assert meta["flops_jac"] > meta["flops_wdot"] > 0
+    assert "qss_jac_kernel" in meta["kernels"]
