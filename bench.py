@@ -1,0 +1,316 @@
+"""Benchmark: wdot + analytic Jacobian throughput of the QSS hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload hydrocarbon|tiny|large] [--ncells C]
+
+One step = one pass of the hot path (state unpack, thermo, rates, falloff,
+QSS solve, production rates, temperature equation, analytic Jacobian through
+the QSS chain rule) over one batch of cells of the workload, launched through
+the C ABI (qss_jacobian).  The default workload is the hydrocarbon-scale
+synthetic mechanism (35 transported + 18 QSS species, 268 reactions) at 2^20
+cells.  Inputs and outputs exceed the 126 MB L2 (310 MB in, 11 GB out), so no
+L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank processes its own
+batch (weak scaling, no collective on the data path); the time is the max over
+ranks.  ``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "wdot+Jacobian cells/s"
+UNIT = "cells/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="hydrocarbon", choices=["tiny", "hydrocarbon", "large"])
+    p.add_argument("--ncells", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                f = [x.strip() for x in out.split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(s[0]) for s in self.samples) if v is not None]
+        mx = [v for v in (num(s[1]) for s in self.samples) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (torchrun)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+def traffic_from_profile(kernel, workload, artefact_key, ncells):
+    """DRAM bytes per launch from the committed ncu summary of this kernel
+    (lines starting with '@'), if it was taken on the current artefact; the
+    capture's bytes per cell are scaled to the launch's cells."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if line.startswith("@") and ":" in line:
+            k, v = line[1:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        if vals.get("artefact_key") != artefact_key:
+            return None
+        return float(vals["dram_bytes_per_cell"]) * ncells
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(mech, states_cfg, seconds, ncells_cap=1 << 20):
+    """The oracle (C++ with OpenMP over cells, as it stands) on a bounded
+    sample of the workload's cells, on all host cores."""
+    import oracle
+    from paper_2405_05974_b300 import mechgen
+    om = oracle.OracleMech(mech)
+    cores = os.cpu_count() or 1
+    chunk = 512
+    done = 0
+    gen_s = 0.0
+    t0 = time.perf_counter()
+    while done < ncells_cap:
+        cfg = type(states_cfg)(**{**states_cfg.__dict__, "seed": states_cfg.seed + 7 + done})
+        g0 = time.perf_counter()
+        rho, T, Y = mechgen.generate_states(mech, cfg, chunk)
+        gen_s += time.perf_counter() - g0
+        om.eval(rho, T, Y, jac=True, nthreads=cores)
+        done += chunk
+        if time.perf_counter() - t0 - gen_s >= seconds:
+            break
+        chunk = min(chunk * 2, 8192)
+    el = time.perf_counter() - t0 - gen_s
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} seeded cells of the workload, wdot+Tdot+Jacobian, "
+                      f"{el:.1f} s on {cores} host threads (input generation excluded)"}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    a = parse()
+    rank, world, local, pg = dist_setup()
+    from paper_2405_05974_b300 import workloads
+    key = a.workload
+    mech = workloads.mechanism(key)
+    ncells = a.ncells or workloads.NCELLS[key]
+    cfg = {"workload": f"{mech['name']} wdot+Jacobian", "ncells_per_gpu": ncells,
+           "mechanism": {"transported": sum(1 for s in mech["species"] if not s["qss"]),
+                         "qss": sum(1 for s in mech["species"] if s["qss"]),
+                         "reactions": len(mech["reactions"])},
+           "layout": "SoA fp64, ld = ncells", "l2": "inputs and outputs larger than L2 (no flush)",
+           "parallelism": f"independent batches x{world}"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        base = None
+        per = max(2.0, a.cpu_seconds / max(a.steps + a.warmup, 1))
+        for s in range(a.warmup + a.steps):
+            b = cpu_baseline(mech, workloads.STATES[key], seconds=per, ncells_cap=1 << 16)
+            if s >= a.warmup:
+                vals.append(b["value"])
+                base = b
+        v = float(np.median(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ncells / v * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded)", "config": cfg,
+                "cpu_baseline": {**base, "value": v},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_2405_05974_b300 import binding, mechgen
+    from paper_2405_05974_b300.qssc.build import build_mechanism, load_meta
+    torch.cuda.set_device(local)
+    art = build_mechanism(mech)
+    meta = load_meta(art)
+    gm = binding.Mechanism(art, local)
+    st_cfg = workloads.STATES[key]
+    st_cfg = type(st_cfg)(**{**st_cfg.__dict__, "seed": st_cfg.seed + 1000 * rank})
+    rho, T, Y = mechgen.generate_states(mech, st_cfg, ncells)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    r, t, y = d(rho), d(T), d(Y)
+    n = gm.n
+    J = torch.empty((n * n, ncells), dtype=torch.float64, device="cuda")
+    w = torch.empty((gm.N, ncells), dtype=torch.float64, device="cuda")
+    td = torch.empty(ncells, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gm.jacobian(r, t, y, jac=J, wdot=w, Tdot=td, stream=stream)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    peak = binding.measure_fp64_peak(local, 200)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        g0.record(stream)
+        for i in range(a.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+    barrier(pg)
+    total_ms = max_over_ranks(pg, g0.elapsed_time(g1))
+    per = [e0.elapsed_time(e1) for e0, e1 in ev]
+    ms_step = total_ms / a.steps
+    value = ncells * world * a.steps / (total_ms * 1e-3)
+    kernel_ms = float(np.mean(per))
+    flops_cell = meta["flops_jac"]
+    achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
+    traffic = traffic_from_profile("qss_jac_kernel", key, meta["artefact_key"], ncells)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "measured live on this GPU: FP64 DFMA microbenchmark "
+                           "(qss_measure_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
+            "flops_per_cell": flops_cell, "fp64_instr_per_cell_est": meta.get("fp64_instr_jac"),
+            "kernel": "qss_jac_kernel", "kernel_ms": kernel_ms,
+            "hbm_algorithmic_gbs": (8.0 * (2 + gm.N + gm.N + 1 + n * n) * ncells) / (kernel_ms * 1e-3) / 1e9}
+
+    e2e = None
+    if not a.no_e2e:
+        rh = torch.from_numpy(rho).pin_memory()
+        th = torch.from_numpy(T).pin_memory()
+        yh = torch.from_numpy(np.ascontiguousarray(Y)).pin_memory()
+        Jh = torch.empty((n * n, ncells), dtype=torch.float64).pin_memory()
+        wh = torch.empty((gm.N, ncells), dtype=torch.float64).pin_memory()
+        tdh = torch.empty(ncells, dtype=torch.float64).pin_memory()
+        gm.jacobian_host(rh, th, yh, jac=Jh, wdot=wh, Tdot=tdh)     # warm-up (staging alloc)
+        e_steps = max(1, min(a.steps, 3))
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            gm.jacobian_host(rh, th, yh, jac=Jh, wdot=wh, Tdot=tdh)
+        el = max_over_ranks(pg, time.perf_counter() - t0)
+        nchunks = -(-ncells // 65536)
+        e2e = {"value": ncells * world * e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (2 + gm.N) * ncells,
+               "d2h_bytes_per_step": 8 * (n * n + gm.N + 1) * ncells,
+               "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
+               "gpu_launches_per_step": nchunks}
+        del Jh
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        cpu = cpu_baseline(mech, workloads.STATES[key], a.cpu_seconds)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
+            "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": a.steps, "clocks": clk.summary(),
+            "kernel": {"ptxas": meta["kernels"].get("qss_jac_kernel", {}),
+                       "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

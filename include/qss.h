@@ -150,6 +150,12 @@ const char* qss_last_error(void);
  * `millis` milliseconds.  Used as the FP64 roofline denominator. */
 int qss_measure_fp64_peak(int device, int millis, double* tflops);
 
+/* Diagnostics: evaluates the device math routines used by generated code,
+ * elementwise on device arrays x[n] -> y[n] (fn 0 = table-driven exp,
+ * 1 = CUDA library exp, 2 = log, 3 = reciprocal).  Used by the tests that
+ * compare the table-driven exp with the library and with exact values. */
+int qss_selftest_math(int device, int fn, int64_t n, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,7 @@ def lib():
         L.qss_implicit_step.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
                                         ctypes.POINTER(NewtonOpts), _vp, _vp, _vp]
         L.qss_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.qss_selftest_math.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _vp, _vp, _vp]
         _lib = L
     return _lib
 
@@ -84,6 +85,13 @@ def measure_fp64_peak(device: int = 0, millis: int = 200) -> float:
     out = ctypes.c_double()
     check(lib().qss_measure_fp64_peak(device, millis, ctypes.byref(out)))
     return out.value
+
+
+def selftest_math(fn: int, x: torch.Tensor, device: int = 0) -> torch.Tensor:
+    """Device math routine `fn` (0 table exp, 1 library exp, 2 log, 3 rcp) on x."""
+    y = torch.empty_like(x)
+    check(lib().qss_selftest_math(device, fn, x.numel(), _ptr(x), _ptr(y), _stream(None)))
+    return y
 
 
 class Mechanism:

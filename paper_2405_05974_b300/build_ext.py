@@ -41,8 +41,9 @@ def build(force: bool = False, verbose: bool = False):
         subprocess.check_call(cmd)
         os.replace(LIB + ".tmp", LIB)
     aux_src = os.path.join(CSRC, "qss_aux.cu")
-    if force or _newer(AUX, [aux_src]):
-        cmd = ["nvcc", "-cubin", *ARCH, "-O3", "-lineinfo", "-o", AUX + ".tmp", aux_src]
+    aux_deps = [aux_src, os.path.join(CSRC, "qss_device.cuh"), os.path.join(CSRC, "qss_exp_table.inc")]
+    if force or _newer(AUX, aux_deps):
+        cmd = ["nvcc", "-cubin", *ARCH, "-O3", "-lineinfo", "-I", CSRC, "-o", AUX + ".tmp", aux_src]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)

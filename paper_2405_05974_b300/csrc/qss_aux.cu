@@ -1,3 +1,5 @@
+#include "qss_device.cuh"
+
 // Auxiliary kernels of libqss (compiled to qss_aux.cubin for sm_103a).
 //
 // qss_fp64_fma_probe: dependent FMA chains, 8 independent chains per thread,
@@ -18,4 +20,21 @@ extern "C" __global__ void qss_l2_flush(double* buf, long long n, double v) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     buf[i] = v + (double)i;
+}
+
+// Elementwise evaluation of the device math used by generated code, for tests:
+// fn 0 = qss_exp_table, 1 = library exp, 2 = qss_log, 3 = qss_rcp.
+extern "C" __global__ void qss_math_probe(int fn, long long n, const double* __restrict__ x,
+                                          double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r;
+  switch (fn) {
+    case 0: r = qss_exp_table(v); break;
+    case 1: r = exp(v); break;
+    case 2: r = qss_log(v); break;
+    default: r = qss_rcp(v); break;
+  }
+  y[i] = r;
 }

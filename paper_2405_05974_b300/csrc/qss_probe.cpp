@@ -58,3 +58,27 @@ extern "C" int qss_measure_fp64_peak(int device, int millis, double* tflops) {
   drv().cuDevicePrimaryCtxRelease(dev);
   return status;
 }
+
+extern "C" int qss_selftest_math(int device, int fn, int64_t n, const double* x, double* y,
+                                 void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y)) || fn < 0 || fn > 3) return fail(QSS_ERR_INVALID_ARG, "bad argument");
+  if (n == 0) return QSS_OK;
+  CUdevice dev;
+  CUcontext ctx;
+  int rc = ctx_for_device(device, &dev, &ctx);
+  if (rc) return rc;
+  static CUmodule mod = nullptr;
+  static CUfunction f = nullptr;
+  if (!mod) {
+    std::string path = lib_dir() + "/qss_aux.cubin";
+    CU_TRY(drv().cuModuleLoad(&mod, path.c_str()));
+    CU_TRY(drv().cuModuleGetFunction(&f, mod, "qss_math_probe"));
+  }
+  long long nn = n;
+  void* args[] = {&fn, &nn, &x, &y};
+  const int block = 256;
+  long long grid = (n + block - 1) / block;
+  CU_TRY(drv().cuLaunchKernel(f, (unsigned)grid, 1, 1, block, 1, 1, 0, (CUstream)stream, args, nullptr));
+  drv().cuDevicePrimaryCtxRelease(dev);
+  return QSS_OK;
+}

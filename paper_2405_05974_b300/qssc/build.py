@@ -26,7 +26,7 @@ REPO = os.path.dirname(PKG)
 DEFAULT_ROOT = os.path.join(REPO, "build", "mech")
 NVCC = os.environ.get("QSS_NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-TEMPLATES = ["qss_device.cuh", "qss_kernels.cuh", "qss_newton.cuh"]
+TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_kernels.cuh", "qss_newton.cuh"]
 COMPILER_VERSION = "1"
 
 

@@ -6,7 +6,7 @@ so that every value is produced shortly before its first use and every output
 is stored as soon as it is final (the emission order plays the role of the
 paper's subexpression recycling, Alg. 3: a value's register is free after its
 last use, which the register allocator sees directly).  A product used once
-by a sum is emitted as ``fma``.  Constants are literals (nvcc places FP64
+by a sum is emitted as ``fma`` (also when the product is shared).  Constants are literals (nvcc places FP64
 literals in the constant bank, the "constant global arrays" of Appendix A).
 
 Two device functions are produced per mechanism:
@@ -84,16 +84,28 @@ class Emitter:
                 inline.add(n)
             elif op == FACT:
                 inline.add(n)
+        # Fused multiply-add: a sum node absorbs one product operand as fma.
+        # A product whose every user absorbs it is never materialised (the
+        # multiply is repeated inside each fma at no cost: an fma is one
+        # instruction, the same as the add it replaces).  Materialising a
+        # product shared by k sums costs 1 + k instructions, absorbing it k.
         fma_of = {}
         for n in seen:
             if g.op[n] in (ADD, SUB):
                 a, b = [self._resolve(x) for x in g.args[n]]
-                for which, x in ((0, a), (1, b)):
-                    xx = x
-                    if g.op[xx] == MUL and refc[xx] == 1 and xx not in inline:
-                        fma_of[n] = (which, xx)
-                        inline.add(xx)
-                        break
+                cands = [(w, x) for w, x in ((0, a), (1, b)) if g.op[x] == MUL and x not in inline]
+                if not cands:
+                    continue
+                if len(cands) == 2:
+                    cands.sort(key=lambda wx: refc[wx[1]])
+                fma_of[n] = cands[0]
+        absorbed = Counter()
+        for n, (_, x) in fma_of.items():
+            absorbed[x] += 1
+        root_set = set(roots)
+        for x, k in absorbed.items():
+            if k == refc[x] and x not in root_set:
+                inline.add(x)
         names: Dict[int, str] = {}
         lines: List[str] = []
         counts = Counter()
@@ -175,13 +187,35 @@ class Emitter:
         for (fmt, node), root in zip(outputs, roots):
             visit(root)
             lines.append(indent + fmt.format(v=ref(root)))
+        # algorithmic count: each DAG operation once, independent of fusion
+        dag = Counter()
+        for n in seen:
+            op = g.op[n]
+            if op in (ADD, SUB):
+                dag["add"] += 1
+            elif op == MUL:
+                dag["mul"] += 1
+            elif op == RECIP:
+                dag["rcp"] += 1
+            elif op == EXP:
+                dag["exp"] += 1
+            elif op == LOG:
+                dag["log"] += 1
+        counts["dag_flops"] = sum(dag.values())
         return lines, counts
 
 
 def algorithmic_flops(counts) -> int:
-    """FP64 operations of the emitted DAG: add/sub/mul/rcp/exp/log = 1, fma = 2."""
-    return (counts["add"] + counts["mul"] + 2 * counts["fma"] + counts["rcp"] + counts["exp"]
-            + counts["log"])
+    """FP64 operations of the CSE'd DAG: each add/sub/mul/reciprocal/exp/log node
+    counts once (an fma in the emitted code is the add plus the multiply it
+    absorbed, so the count does not depend on how products were fused)."""
+    return counts["dag_flops"]
+
+
+def fp64_instructions(counts, exp_cost=10, log_cost=36, rcp_cost=10) -> int:
+    """Estimated FP64-pipe instructions per cell of the emitted code."""
+    return (counts["add"] + counts["mul"] + counts["fma"] + exp_cost * counts["exp"]
+            + log_cost * counts["log"] + rcp_cost * counts["rcp"])
 
 
 def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
@@ -229,6 +263,7 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
+        "fp64_instr_wdot": fp64_instructions(cnt_w), "fp64_instr_jac": fp64_instructions(cnt_j),
         "dag_nodes": len(g.op), "jac_nnz": sum(1 for i in range(n) for c in range(n)
                                                if model.jac[i][c] != g.ZERO),
     }

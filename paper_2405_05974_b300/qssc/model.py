@@ -54,6 +54,7 @@ class Model:
     groups: List[List[int]]         # QSS solve order (QSS indices)
     cq_value: List[int]
     stats: dict = field(default_factory=dict)
+    parts: dict = field(default_factory=dict)
 
 
 class _Builder:
@@ -330,6 +331,7 @@ class _Builder:
             J[N][c] = acc
         model = Model(ir=ir, g=g, C=self.C, T=self.T, wdot=omega[:N], Tdot=Tdot_ph, jac=J,
                       bind=self.bind, groups=groups, cq_value=cqv)
+        model.parts = {"G": Gm, "X": X, "P": P, "A": A}
         model.stats = {"nodes": len(g.op), "n_third_body_tables": len(Mkeys),
                        "groups": [len(c) for c in groups]}
         return model
