@@ -14,7 +14,8 @@ struct qss_mech_s {
   CUcontext ctx = nullptr;
   CUmodule mod = nullptr;
   CUfunction f_wdot = nullptr, f_jac = nullptr;
-  CUfunction f_newton[2] = {nullptr, nullptr};   // FP64 LU, FP32 LU + FP64 refinement
+  CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
+  CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
   std::vector<double> W;
   std::string name, digest, dir;
@@ -23,6 +24,9 @@ struct qss_mech_s {
   CUdeviceptr stage[2] = {0, 0};
   size_t stage_bytes = 0;
   CUstream st[2] = {nullptr, nullptr};
+  // implicit step: Newton matrices of one chunk of cells (grown on demand)
+  CUdeviceptr newton_scratch = 0;
+  size_t newton_scratch_bytes = 0;
 };
 
 namespace qss {

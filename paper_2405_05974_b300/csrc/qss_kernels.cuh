@@ -30,13 +30,26 @@ qss_wdot_kernel(long long ncells, long long ld, const double* __restrict__ rho,
   qss_eval_wdot(C, __ldg(T + c), wdot + c, Tdot ? Tdot + c : nullptr, ld);
 }
 
+// f = (wdot, Tdot) and J.  State from (rho, T, Y) or, when phi is given, from
+// phi[k * ld + c] = (C_1..C_N, T) (the implicit step's iterate); cells with
+// active[c] == 0 are skipped when `active` is given.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                const double* __restrict__ T, const double* __restrict__ Y,
-               double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot) {
+               double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot,
+               const double* __restrict__ phi, const int* __restrict__ active) {
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (c >= ncells) return;
+  if (active && !active[c]) return;
   double C[QSS_N];
-  qss_unpack(c, ld, rho, Y, C);
-  qss_eval_jac(C, __ldg(T + c), wdot ? wdot + c : nullptr, Tdot ? Tdot + c : nullptr, jac + c, ld);
+  double Tc;
+  if (phi) {
+#pragma unroll
+    for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + c];
+    Tc = phi[QSS_N * ld + c];
+  } else {
+    qss_unpack(c, ld, rho, Y, C);
+    Tc = __ldg(T + c);
+  }
+  qss_eval_jac(C, Tc, wdot ? wdot + c : nullptr, Tdot ? Tdot + c : nullptr, jac + c, ld, ld);
 }

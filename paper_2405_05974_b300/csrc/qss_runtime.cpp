@@ -127,10 +127,11 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     }
   }
   // optional kernels (implicit step)
-  if (drv().cuModuleGetFunction(&m->f_newton[0], m->mod, "qss_newton_fp64_kernel") != CUDA_SUCCESS)
-    m->f_newton[0] = nullptr;
-  if (drv().cuModuleGetFunction(&m->f_newton[1], m->mod, "qss_newton_fp32ir_kernel") != CUDA_SUCCESS)
-    m->f_newton[1] = nullptr;
+  const char* opt[] = {"qss_newton_update_fp64_kernel", "qss_newton_update_fp32ir_kernel",
+                       "qss_newton_setup_kernel", "qss_newton_finish_kernel"};
+  CUfunction* oslot[] = {&m->f_newton[0], &m->f_newton[1], &m->f_newton_setup, &m->f_newton_finish};
+  for (int i = 0; i < 4; ++i)
+    if (drv().cuModuleGetFunction(oslot[i], m->mod, opt[i]) != CUDA_SUCCESS) *oslot[i] = nullptr;
   *out = m;
   return QSS_OK;
 }
@@ -142,6 +143,7 @@ void qss_mech_free(qss_mech_t m) {
     if (m->stage[b]) drv().cuMemFree(m->stage[b]);
     if (m->st[b]) drv().cuStreamDestroy(m->st[b]);
   }
+  if (m->newton_scratch) drv().cuMemFree(m->newton_scratch);
   if (m->mod) drv().cuModuleUnload(m->mod);
   drv().cuDevicePrimaryCtxRelease(m->dev);
   delete m;
@@ -182,7 +184,9 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   if (ncells == 0) return QSS_OK;
   if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
   long long nc = ncells, l = ld;
-  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot};
+  const double* phi = nullptr;
+  const int* active = nullptr;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &active};
   return launch_cells(m, m->f_jac, ncells, m->block, args, (CUstream)stream, 0);
 }
 
@@ -262,7 +266,9 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
     long long nc = cs, l = S;
     double* wp = d_w;
     double* tp = d_Td;
-    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp};
+    const double* phi = nullptr;
+    const int* active = nullptr;
+    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp, &phi, &active};
     if ((rc = launch_cells(m, m->f_jac, cs, m->block, args, s, 0))) return rc;
     if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, (size_t)n * n, s))) return rc;
     if (wdot && (rc = copy2d(wdot + c0, true, hp, d_w, false, P, w, N, s))) return rc;

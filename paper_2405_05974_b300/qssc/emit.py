@@ -10,9 +10,9 @@ by a sum is emitted as ``fma`` (also when the product is shared).  Constants are
 literals in the constant bank, the "constant global arrays" of Appendix A).
 
 Two device functions are produced per mechanism:
-  qss_eval_wdot(C, T, wdot, Tdot, stride)
-  qss_eval_jac (C, T, wdot, Tdot, jac, stride)
-with outputs written at ``out[i * stride]``.
+  qss_eval_wdot(C, T, wdot, Tdot, wstride)
+  qss_eval_jac (C, T, wdot, Tdot, jac, wstride, jstride)
+with outputs written at ``wdot[i * wstride]`` and ``jac[e * jstride]``.
 """
 from __future__ import annotations
 
@@ -226,14 +226,14 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
     inputs = {model.C[k]: f"C{k}" for k in range(N)}
     inputs[model.T] = "T"
     em = Emitter(model, inputs)
-    out_w = [(f"if (wdot) wdot[{i} * stride] = {{v}};", model.wdot[i]) for i in range(N)]
+    out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
     out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
     body_w, cnt_w = em.emit(out_w + out_t, indent="  ")
     # Jacobian: column by column, so that dC_Q/dphi for one column is live at a time
     out_j = []
     for c in range(n):
         for i in range(n):
-            out_j.append((f"jac[{i * n + c} * stride] = {{v}};", model.jac[i][c]))
+            out_j.append((f"jac[{i * n + c} * jstride] = {{v}};", model.jac[i][c]))
     em2 = Emitter(model, inputs)
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
     hdr = [
@@ -252,11 +252,11 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
     src = "\n".join(hdr)
     src += "\n".join([
         "__device__ __forceinline__ void qss_eval_wdot(const double* __restrict__ C, const double T,",
-        "    double* __restrict__ wdot, double* __restrict__ Tdot, const long long stride) {",
+        "    double* __restrict__ wdot, double* __restrict__ Tdot, const long long wstride) {",
         *unpack, *body_w, "}", "",
         "__device__ __forceinline__ void qss_eval_jac(const double* __restrict__ C, const double T,",
         "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
-        "    const long long stride) {",
+        "    const long long wstride, const long long jstride) {",
         *unpack, *body_j, "}", ""])
     meta = {
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,

@@ -1,0 +1,142 @@
+"""GPU implicit (backward-Euler) step against the CPU oracle's step.
+
+The oracle and both GPU forms run the same algorithm (Newton on
+G = phi - phi0 - dt f with I - dt J, the analytic J re-evaluated every
+iteration, the weighted-RMS stopping rule).  Two converged Newton iterates
+differ by at most the sum of their last updates, which the stopping rule
+bounds by rtol |phi_i| + atol_i each, plus rounding noise; the gates below
+are that bound with margin:
+  FP64 LU     vs oracle:   |d phi_i| <= 1e-10 |phi_i| + 10 atol_i
+  FP32 LU+IR  vs FP64 LU:  |d phi_i| <= 1e-8  |phi_i| + 10 atol_i
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_05974_b300 import binding, mechgen, workloads
+from paper_2405_05974_b300.qssc.build import build_mechanism
+from tests import mechs as hm
+
+pytestmark = pytest.mark.gpu
+
+ATOL_C, ATOL_T, RTOL = 1e-20, 1e-10, 1e-12
+_cache = {}
+
+
+def mech(key):
+    if key not in _cache:
+        m = workloads.mechanism(key)
+        _cache[key] = (m, binding.Mechanism(build_mechanism(m), 0), oracle.OracleMech(m))
+    return _cache[key]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_step(gm, rho, T, Y, dt, precision, ncells=None):
+    r, t, y = dev(rho), dev(T), dev(Y)
+    dtt = dev(np.atleast_1d(np.asarray(dt, dtype=np.float64)))
+    it, st = gm.implicit_step(r, t, y, dtt, precision=precision, ncells=ncells)
+    torch.cuda.synchronize()
+    return t.cpu().numpy(), y.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+
+
+def phi_of(om, rho, T, Y):
+    return np.vstack([om.conc(rho, Y), T[None, :]])
+
+
+def close(pa, pb, rel, N):
+    atol = np.r_[np.full(N, ATOL_C), ATOL_T][:, None]
+    return np.abs(pa - pb) <= rel * np.abs(pb) + 10 * atol
+
+
+@pytest.mark.parametrize("key,ncells", [("tiny", 4096), ("hydrocarbon", 1024)])
+def test_implicit_step_parity(key, ncells):
+    m, gm, om = mech(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    dt = workloads.IMPLICIT_DT
+    To, Yo, ito, sto = om.be_step(rho, T, Y, dt, max_iter=20)
+    T64, Y64, it64, st64 = gpu_step(gm, rho, T, Y, dt, binding.QSS_LU_FP64)
+    T32, Y32, it32, st32 = gpu_step(gm, rho, T, Y, dt, binding.QSS_LU_FP32_IR)
+    N = gm.N
+    both = (sto == 0) & (st64 == 0)
+    assert both.sum() >= 0.25 * ncells, (np.bincount(sto), np.bincount(st64))
+    # the same cells converge (Newton paths only differ by rounding)
+    agree = np.mean((sto == 0) == (st64 == 0))
+    assert agree >= 0.97, agree
+    po, p64, p32 = phi_of(om, rho, To, Yo), phi_of(om, rho, T64, Y64), phi_of(om, rho, T32, Y32)
+    ok = close(p64[:, both], po[:, both], 1e-10, N)
+    assert ok.all(), np.argwhere(~ok)[:5]
+    both32 = (st32 == 0) & (st64 == 0)
+    assert np.mean((st32 == 0) == (st64 == 0)) >= 0.97
+    ok = close(p32[:, both32], p64[:, both32], 1e-8, N)
+    assert ok.all(), np.argwhere(~ok)[:5]
+    # iteration counts follow the oracle's
+    assert np.mean(np.abs(it64[both].astype(int) - ito[both]) <= 1) >= 0.95
+    # mass: sum_k Y_k is unchanged by a converged step (rho fixed)
+    assert np.allclose(Y64[:, both].sum(0), Y[:, both].sum(0), rtol=1e-11, atol=0)
+    print(key, "oracle", np.bincount(sto, minlength=4), "fp64", np.bincount(st64, minlength=4),
+          "fp32ir", np.bincount(st32, minlength=4), "iters fp64 mean %.2f fp32ir %.2f" %
+          (it64[st64 == 0].mean(), it32[st32 == 0].mean()))
+
+
+def test_linear_closed_form():
+    """A <=> B with Tdot = 0: the step is the 2x2 linear solve (Newton reaches it
+    in one update, the second confirms)."""
+    T0 = 1300.0
+    sp = [hm.species("A", {"C": 1, "H": 2, "O": 1}, nasa=[1.0, 0, 0, 0, 0, 0, 0.0]),
+          hm.species("B", {"C": 1, "H": 2, "O": 1}, nasa=[1.0, 0, 0, 0, 0, 0, -0.4]),
+          hm.species("N2", {"N": 2})]
+    mm = hm.mech("ab_lin", sp, [hm.reaction({"A": 1}, {"B": 1}, 2.0e6)])
+    gm = binding.Mechanism(build_mechanism(mm), 0)
+    CA0, CB0 = 1.5, 0.25
+    rho, T, Y = mechgen.concentrations_to_state(mm, np.array([[CA0], [CB0], [1.0]]), np.array([T0]))
+    dt = 3e-7
+    kf, kb = 2.0e6, 2.0e6 / math.exp(-0.4)
+    CA = ((1 + dt * kb) * CA0 + dt * kb * CB0) / (1 + dt * kf + dt * kb)
+    W = np.array([s["W"] for s in mm["species"]])
+    for prec in (binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR):
+        T1, Y1, it, st = gpu_step(gm, rho, T, Y, dt, prec)
+        C1 = rho * Y1[:, 0] / W
+        assert st[0] == 0 and it[0] <= 2
+        assert C1[0] == pytest.approx(CA, rel=1e-13)
+        assert C1[1] == pytest.approx(CA0 + CB0 - CA, rel=1e-13)
+        assert T1[0] == pytest.approx(T0, rel=1e-15)
+
+
+def test_per_cell_dt_and_ragged_tail():
+    key = "tiny"
+    m, gm, om = mech(key)
+    ncells, ld = 1000 - 13, 1000
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells, ld=ld)
+    dts = np.exp(np.random.default_rng(2).uniform(np.log(1e-7), np.log(1e-5), ld))
+    r, t, y = dev(rho), dev(T), dev(Y)
+    it = torch.full((ld,), -7, dtype=torch.int32, device="cuda")
+    st = torch.full((ld,), -7, dtype=torch.int32, device="cuda")
+    gm.implicit_step(r, t, y, dev(dts), precision=binding.QSS_LU_FP64, ncells=ncells, iters=it, status=st)
+    torch.cuda.synchronize()
+    t, y, it, st = t.cpu().numpy(), y.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    assert (it[ncells:] == -7).all() and (st[ncells:] == -7).all()
+    assert np.array_equal(t[ncells:], T[ncells:]) and np.array_equal(y[:, ncells:], Y[:, ncells:])
+    To, Yo, ito, sto = om.be_step(rho, T, Y, dts, ncells=ncells, max_iter=20)
+    both = (sto[:ncells] == 0) & (st[:ncells] == 0)
+    assert both.mean() > 0.5
+    p, po = phi_of(om, rho, t, y)[:, :ncells], phi_of(om, rho, To, Yo)[:, :ncells]
+    assert close(p[:, both], po[:, both], 1e-10, gm.N).all()
+
+
+def test_empty_and_bad_arguments():
+    _, gm, _ = mech("tiny")
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    Y = torch.zeros((gm.N, 8), dtype=torch.float64, device="cuda")
+    L = binding.lib()
+    assert L.qss_implicit_step(gm.h, 0, 8, x.data_ptr(), 0, x.data_ptr(), x.data_ptr(), Y.data_ptr(),
+                               0, None, None, None, None) == 0
+    assert L.qss_implicit_step(gm.h, 9, 8, x.data_ptr(), 0, x.data_ptr(), x.data_ptr(), Y.data_ptr(),
+                               0, None, None, None, None) == -1
+    assert L.qss_implicit_step(gm.h, 8, 8, x.data_ptr(), 0, x.data_ptr(), x.data_ptr(), Y.data_ptr(),
+                               7, None, None, None, None) == -1
