@@ -142,6 +142,47 @@ int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double*
                       const qss_newton_opts* opts, int32_t* iters, int32_t* cell_status,
                       void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving (continuous batching of implicit-step requests on one GPU).
+ *
+ * qss_serve_create allocates a device arena of budget_bytes (the memory
+ * budget) and starts a scheduler thread with n_streams streams.  A request is
+ * one backward-Euler step (qss_implicit_step semantics, dt a scalar) of
+ * `ncells` cells given in HOST arrays with leading dimension ncells: rho
+ * [ncells], T [ncells] and Y [N][ncells] (updated in place when the request
+ * completes), iters / cell_status [ncells] (may be NULL).  The arrays must stay
+ * valid and untouched until qss_serve_wait returns for the request (page-locked
+ * memory gives full copy speed).  Queued requests are admitted in arrival
+ * order as soon as a stream slot and arena memory are free; queued requests of
+ * the same mechanism and precision are merged into one launch of up to
+ * max_batch_cells cells.  Per-cell results do not depend on the batch a request
+ * lands in.  Errors at submit: QSS_ERR_BUDGET if the request alone exceeds the
+ * budget or max_batch_cells.  qss_serve_wait blocks until the request is done
+ * (timeout_us < 0: no limit; otherwise QSS_ERR_TIMEOUT after timeout_us and the
+ * request stays pending); it returns the request's status and releases its id.
+ * qss_serve_destroy finishes queued and running work, then frees everything.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int n_streams;                   /* concurrent batches (default 4)              */
+  int64_t max_batch_cells;         /* cells per merged launch (default 262144)    */
+  const qss_newton_opts* newton;   /* NULL: qss_implicit_step defaults            */
+} qss_serve_opts;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, queued, in_flight, batches, cells_completed;
+  uint64_t bytes_in_use, bytes_peak;
+  double p50_latency_us, p99_latency_us, mean_latency_us;  /* submit -> completion */
+  double cells_per_s;   /* completed cells / (last completion - first submission) */
+} qss_serve_stats_t;
+
+int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts, qss_server_t* out);
+int qss_serve_submit(qss_server_t server, qss_mech_t mech, int64_t ncells, const double* rho,
+                     double* T, double* Y, double dt, int precision, int32_t* iters,
+                     int32_t* cell_status, uint64_t* req_id);
+int qss_serve_wait(qss_server_t server, uint64_t req_id, int64_t timeout_us, int* req_status);
+int qss_serve_stats(qss_server_t server, qss_serve_stats_t* out);
+void qss_serve_destroy(qss_server_t server);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* qss_last_error(void);
 

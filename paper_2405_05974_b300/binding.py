@@ -38,6 +38,22 @@ class NewtonOpts(ctypes.Structure):
                 ("refine_tol", ctypes.c_double)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int), ("max_batch_cells", ctypes.c_int64),
+                ("newton", ctypes.POINTER(NewtonOpts))]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_uint64) for nm in ("submitted", "completed", "rejected", "queued",
+                                                 "in_flight", "batches", "cells_completed",
+                                                 "bytes_in_use", "bytes_peak")] + \
+               [(nm, ctypes.c_double) for nm in ("p50_latency_us", "p99_latency_us",
+                                                 "mean_latency_us", "cells_per_s")]
+
+    def as_dict(self):
+        return {nm: getattr(self, nm) for nm, _ in self._fields_}
+
+
 def lib():
     """The loaded libqss.so (raises if it has not been built)."""
     global _lib
@@ -60,6 +76,14 @@ def lib():
                                         ctypes.POINTER(NewtonOpts), _vp, _vp, _vp]
         L.qss_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.qss_selftest_math.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _vp, _vp, _vp]
+        L.qss_serve_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ServeOpts),
+                                       ctypes.POINTER(_vp)]
+        L.qss_serve_submit.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                       _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.qss_serve_wait.argtypes = [_vp, ctypes.c_uint64, _i64, ctypes.POINTER(ctypes.c_int)]
+        L.qss_serve_stats.argtypes = [_vp, ctypes.POINTER(ServeStats)]
+        L.qss_serve_destroy.argtypes = [_vp]
+        L.qss_serve_destroy.restype = None
         _lib = L
     return _lib
 
@@ -201,3 +225,57 @@ class Mechanism:
                                       precision, ctypes.byref(opts) if opts is not None else None,
                                       _ptr(iters), _ptr(status), _stream(stream)))
         return iters, status
+
+
+class Server:
+    """Continuous-batching server of implicit-step requests (host arrays)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 8 << 30, n_streams: int = 4,
+                 max_batch_cells: int = 1 << 18, newton: Optional[NewtonOpts] = None):
+        self._newton = newton
+        o = ServeOpts(n_streams, max_batch_cells,
+                      ctypes.pointer(newton) if newton is not None else None)
+        h = _vp()
+        check(lib().qss_serve_create(device, budget_bytes, ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, mech: Mechanism, rho, T, Y, dt: float, precision=QSS_LU_FP64, iters=None,
+               status=None) -> int:
+        """Queue one request; rho[n], T[n], Y[N][n] are host float64 tensors
+        (T, Y updated in place on completion).  Returns the request id."""
+        for nm, t in (("rho", rho), ("T", T), ("Y", Y)):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous float64 host tensor")
+        n = T.shape[0]
+        if rho.shape != (n,) or Y.shape != (mech.N, n):
+            raise ValueError("shape mismatch")
+        rid = ctypes.c_uint64()
+        check(lib().qss_serve_submit(self.h, mech.h, n, _ptr(rho), _ptr(T), _ptr(Y), float(dt), precision,
+                                     _ptr(iters), _ptr(status), ctypes.byref(rid)))
+        self._keep[rid.value] = (rho, T, Y, iters, status)
+        return rid.value
+
+    def wait(self, rid: int, timeout_us: int = -1) -> int:
+        st = ctypes.c_int()
+        rc = lib().qss_serve_wait(self.h, rid, timeout_us, ctypes.byref(st))
+        if rc != -6:
+            self._keep.pop(rid, None)
+        check(rc)
+        return st.value
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        check(lib().qss_serve_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qss_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -15,13 +15,18 @@ using namespace qss;
 namespace {
 constexpr size_t kScratchBudget = size_t(4) << 30;   // bytes of Newton scratch per handle
 
+}  // namespace
+
+namespace qss {
 struct NewtonOptsDev {   // layout of QssNewtonOpts in qss_newton.cuh
   int max_iter;
   double rtol, atol_C, atol_T;
   int max_refine;
   double refine_tol;
 };
+}  // namespace qss
 
+namespace {
 int ensure_scratch(qss_mech_s* m, size_t bytes) {
   if (m->newton_scratch_bytes >= bytes) return QSS_OK;
   if (m->newton_scratch) {
@@ -36,63 +41,102 @@ int ensure_scratch(qss_mech_s* m, size_t bytes) {
 }
 }  // namespace
 
-extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const double* dt,
-                                 int dt_stride, const double* rho, double* T, double* Y,
-                                 int precision, const qss_newton_opts* opts, int32_t* iters,
-                                 int32_t* cell_status, void* stream) {
+namespace qss {
+
+size_t newton_scratch_per_cell(const qss_mech_s* m, int precision) {
+  (void)precision;   // both forms keep J in FP64; the FP32 factors live in registers
+  const int n = m->N + 1;
+  return (size_t)n * n * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int);
+}
+
+int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
+                        const double* rho, double* T, double* Y, int precision,
+                        const qss_newton_opts* opts, qss_newton_opts* o) {
   if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
   if (ncells < 0 || ld < ncells) return fail(QSS_ERR_INVALID_ARG, "bad sizes (ncells < 0 or ld < ncells)");
   if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR)
     return fail(QSS_ERR_INVALID_ARG, "unknown precision");
   if (dt_stride != 0 && dt_stride != 1) return fail(QSS_ERR_INVALID_ARG, "dt_stride must be 0 or 1");
+  *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-14};
+  if (opts) *o = *opts;
+  if (o->max_iter < 1 || o->max_refine < 0 || !(o->rtol >= 0) || !(o->atol_C >= 0) ||
+      !(o->atol_T >= 0) || !(o->refine_tol >= 0))
+    return fail(QSS_ERR_INVALID_ARG, "bad Newton options");
   if (ncells == 0) return QSS_OK;
   if (!dt || !rho || !T || !Y) return fail(QSS_ERR_INVALID_ARG, "null array");
   if (!m->f_newton[precision] || !m->f_newton_setup || !m->f_newton_finish)
     return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no Newton kernels");
-  qss_newton_opts o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-14};
-  if (opts) o = *opts;
-  if (o.max_iter < 1 || o.max_refine < 0 || !(o.rtol >= 0) || !(o.atol_C >= 0) || !(o.atol_T >= 0) ||
-      !(o.refine_tol >= 0))
-    return fail(QSS_ERR_INVALID_ARG, "bad Newton options");
-  NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
-  std::lock_guard<std::mutex> lock(m->mu);
-  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  return QSS_OK;
+}
+
+// Enqueue one implicit step on `stream` using the given device scratch
+// (scratch_bytes of it, 256-byte aligned), in chunks of as many cells as fit.
+int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
+                    const double* rho, double* T, double* Y, int precision,
+                    const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
+                    CUdeviceptr scratch, size_t scratch_bytes) {
+  if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
-  const size_t per_cell = (size_t)n * n * (sizeof(double) + (precision ? sizeof(float) : 0)) +
-                          (size_t)3 * n * sizeof(double) + 3 * sizeof(int);
-  int64_t chunk = (int64_t)std::max<size_t>(kScratchBudget / per_cell, 32);
+  const size_t per_cell = newton_scratch_per_cell(m, precision);
+  int64_t chunk = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell) / 32 * 32;
+  if (chunk < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
   chunk = std::min<int64_t>(chunk, (ncells + 31) / 32 * 32);
-  chunk = (chunk + 31) / 32 * 32;
-  int rc = ensure_scratch(m, per_cell * (size_t)chunk + 256);
-  if (rc) return rc;
+  NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
   const size_t S = (size_t)chunk;
-  double* M64 = (double*)m->newton_scratch;
+  double* M64 = (double*)scratch;
   double* PHI = M64 + (size_t)n * n * S;
   double* PHI0 = PHI + (size_t)n * S;
   double* F = PHI0 + (size_t)n * S;
   int* ACT = (int*)(F + (size_t)n * S);
   int* ST = ACT + S;
   int* IT = ST + S;
-  float* M32 = precision ? (float*)(IT + S) : nullptr;
+  int* LIST[2] = {IT + S, IT + 2 * S};
+  int* NACT = IT + 3 * S;   // two counters (S is a multiple of 32, so they fit in the tail)
   long long sld = chunk, l = ld;
-  CUstream st = (CUstream)stream;
+  int rc;
+  const int upd_threads = 128;   // QSS_UPD_WARPS warps of 32 lanes, one cell per warp at a time
   for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
     long long cells = std::min<int64_t>(chunk, ncells - c0), cc0 = c0;
-    void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &sld};
+    void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld};
     if ((rc = launch_cells(m, m->f_newton_setup, cells, m->block, a_setup, st, 0))) return rc;
-    const double* nul = nullptr;
-    double* Fw = F;
-    double* FT = F + (size_t)m->N * S;
-    const double* phic = PHI;
-    const int* actc = ACT;
-    void* a_jac[] = {&cells, &sld, &nul, &nul, &nul, &M64, &Fw, &FT, &phic, &actc};
-    void* a_upd[] = {&cells, &cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &M32, &ACT, &ST, &IT, &sld, &od};
     for (int it = 0; it < o.max_iter; ++it) {
+      const int cur = it & 1, nxt = cur ^ 1;
+      const double* nul = nullptr;
+      double* Fw = F;
+      double* FT = F + (size_t)m->N * S;
+      const double* phic = PHI;
+      const int* lc = LIST[cur];
+      const int* nc = NACT + cur;
+      int* nn = NACT + nxt;
+      void* a_jac[] = {&cells, &sld, &nul, &nul, &nul, &M64, &Fw, &FT, &phic, &lc, &nc, &nn};
       if ((rc = launch_cells(m, m->f_jac, cells, m->block, a_jac, st, 0))) return rc;
-      if ((rc = launch_cells(m, m->f_newton[precision], cells, m->block, a_upd, st, 0))) return rc;
+      int* l2 = LIST[nxt];
+      void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
+                       &lc, &nc, &l2, &nn, &sld, &od};
+      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
     }
     void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld};
     if ((rc = launch_cells(m, m->f_newton_finish, cells, m->block, a_fin, st, 0))) return rc;
   }
   return QSS_OK;
+}
+
+}  // namespace qss
+
+extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const double* dt,
+                                 int dt_stride, const double* rho, double* T, double* Y,
+                                 int precision, const qss_newton_opts* opts, int32_t* iters,
+                                 int32_t* cell_status, void* stream) {
+  qss_newton_opts o;
+  int rc = check_implicit_args(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, opts, &o);
+  if (rc || ncells == 0) return rc;
+  std::lock_guard<std::mutex> lock(m->mu);
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  const size_t per_cell = newton_scratch_per_cell(m, precision);
+  int64_t want = std::min<int64_t>((int64_t)(kScratchBudget / per_cell), (ncells + 31) / 32 * 32);
+  want = std::max<int64_t>((want + 31) / 32 * 32, 32);
+  rc = ensure_scratch(m, per_cell * (size_t)want + 256);
+  if (rc) return rc;
+  return implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,
+                         (CUstream)stream, m->newton_scratch, m->newton_scratch_bytes);
 }

@@ -37,6 +37,15 @@ std::string lib_dir();
 int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx);
 int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
                  CUstream stream, unsigned shmem);
+// implicit step (qss_implicit.cpp)
+size_t newton_scratch_per_cell(const qss_mech_s* m, int precision);
+int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
+                        const double* rho, double* T, double* Y, int precision,
+                        const qss_newton_opts* opts, qss_newton_opts* o);
+int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
+                    const double* rho, double* T, double* Y, int precision,
+                    const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
+                    CUdeviceptr scratch, size_t scratch_bytes);
 }  // namespace qss
 
 #define CU_TRY(call)                                   \

@@ -30,24 +30,29 @@ qss_wdot_kernel(long long ncells, long long ld, const double* __restrict__ rho,
   qss_eval_wdot(C, __ldg(T + c), wdot + c, Tdot ? Tdot + c : nullptr, ld);
 }
 
-// f = (wdot, Tdot) and J.  State from (rho, T, Y) or, when phi is given, from
-// phi[k * ld + c] = (C_1..C_N, T) (the implicit step's iterate); cells with
-// active[c] == 0 are skipped when `active` is given.
+// f = (wdot, Tdot) and J.  State from (rho, T, Y) or, in list mode (phi and
+// list given), of the t-th cell of the list: s = list[t] for t < *nact, state
+// phi[k * ld + s] = (C_1..C_N, T), outputs written at column t.  In list mode
+// thread 0 also clears *nact_next, the counter the following Newton update
+// fills.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                const double* __restrict__ T, const double* __restrict__ Y,
                double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot,
-               const double* __restrict__ phi, const int* __restrict__ active) {
+               const double* __restrict__ phi, const int* __restrict__ list,
+               const int* __restrict__ nact, int* __restrict__ nact_next) {
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
-  if (c >= ncells) return;
-  if (active && !active[c]) return;
   double C[QSS_N];
   double Tc;
   if (phi) {
+    if (c == 0) *nact_next = 0;
+    if (c >= *nact) return;
+    const long long s = list[c];
 #pragma unroll
-    for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + c];
-    Tc = phi[QSS_N * ld + c];
+    for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
+    Tc = phi[QSS_N * ld + s];
   } else {
+    if (c >= ncells) return;
     qss_unpack(c, ld, rho, Y, C);
     Tc = __ldg(T + c);
   }

@@ -3,36 +3,52 @@
 // Newton on G(phi) = phi - phi0 - dt f(phi), phi = (C, T), f = (wdot, Tdot) at
 // constant volume, with the matrix M = I - dt J where J is the analytic
 // Jacobian, re-evaluated every iteration.  One Newton iteration is two
-// launches, one thread per cell:
-//   qss_jac_kernel (phi mode)        f and J at the current iterate
-//   qss_newton_update_*_kernel       M = I - dt J, factor, solve, update phi,
-//                                    convergence test
-// so that the long generated body is compiled once (in qss_jac_kernel) and the
-// linear algebra runs at its own occupancy.  Cells that have converged (or
-// failed) are inactive and return at once in both kernels; the host enqueues
-// max_iter iterations without synchronising.
-//   update_fp64    LU of M with partial pivoting in FP64.
-//   update_fp32ir  M equilibrated by powers of two (rows, then columns), LU
-//                  with partial pivoting in FP32, the solution refined with
-//                  FP64 residuals b - M x until the correction is below
-//                  refine_tol relative or max_refine sweeps.
+// launches over the cells that are still iterating (a compacted list):
+//   qss_jac_kernel (list mode)   f and J at the current iterate, one thread
+//                                per cell (the generated body is compiled in
+//                                this one kernel only)
+//   qss_newton_update_*_kernel   M = I - dt J, factorisation, solve, update of
+//                                phi, convergence test, next list
+// The host enqueues max_iter iterations without synchronising: once a cell
+// has converged or failed it leaves the list, so later launches cost only what
+// the remaining cells need.
+//
+// The update kernel factors one cell's matrix at a time per warp: lane r holds
+// row r (rows 32.. in a second register slot); partial pivoting picks the row
+// with the largest |a| among rows not yet pivoted (warp arg-max, lowest index
+// on ties; rows stay in place and their pivot order is recorded), pivot-row
+// entries are broadcast with shuffles, and the right-hand side is eliminated
+// with the matrix.  The matrix never leaves registers.
+//   update_fp64    factorisation and solve in FP64.
+//   update_fp32ir  M equilibrated by powers of two (rows, then columns),
+//                  factorisation in FP32; the solution refined with FP64
+//                  residuals g - M x (M re-read in FP64) until the correction
+//                  is below refine_tol relative, stops shrinking, or after
+//                  max_refine sweeps.
 // Rates, equilibrium constants, the QSS solve, J, M and the Newton residual
 // are FP64 in both forms.
 //
-// Scratch (global memory, structure of arrays with leading dimension sld, for
-// one chunk of cells, s = c - c0):
-//   M64[e * sld + s], e = i * NN + j   J, then the FP64 Newton matrix / factors
-//   M32[e * sld + s]                   the FP32 factors (FP32_IR only)
-//   PHI, PHI0, F [k * sld + s]         iterate, initial state, f
-//   ACT, ST, IT [s]                    active flag, status, iteration count
-// Every access of a warp to one entry is one contiguous segment; only the row
-// swaps of pivoting touch different rows per thread.
+// Scratch (global memory, one chunk of `cells` cells, leading dimension sld;
+// s = cell - c0, t = position in the active list):
+//   M64[e * sld + t], e = i * NN + j     J of the t-th active cell
+//   F [k * sld + t]                       f, then g = -G, then the update x
+//   PHI, PHI0 [k * sld + s]               iterate, initial state
+//   ACT, ST, IT [s]                       active flag, status, iterations
+//   LIST[2][sld], NACT[2]                 active lists (double-buffered)
 #pragma once
+
+#include <type_traits>
 
 #define QSS_CELL_CONVERGED 0
 #define QSS_CELL_MAXITER 1
 #define QSS_CELL_NONFINITE 2
 #define QSS_CELL_SINGULAR 3
+
+#if QSS_NN > 64
+#error "the warp-cooperative Newton solver supports at most 63 transported species"
+#endif
+#define QSS_NSLOT ((QSS_NN + 31) / 32)
+#define QSS_UPD_WARPS 4
 
 __device__ __forceinline__ bool qss_finite(double x) {
   return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -49,91 +65,29 @@ __device__ __forceinline__ int qss_ilogb(double x) {
   return ex == 0 ? -1100 : ex - 1023;
 }
 
-__device__ __forceinline__ double qss_pow2(int e) {   // 2^e, |e| <= 1022
+__device__ __forceinline__ double qss_pow2(int e) {   // 2^e, e clamped to [-1000, 1000]
+  e = max(min(e, 1000), -1000);
   return __hiloint2double((e + 1023) << 20, 0);
 }
 
-// Magnitude key for pivot search: integer order of |x| for doubles (keeps the
-// comparisons off the FP64 pipe), |x| itself for floats.
-__device__ __forceinline__ long long qss_mag(double x) { return qss_absbits(x); }
-__device__ __forceinline__ float qss_mag(float x) { return fabsf(x); }
-
-// In-place LU with partial pivoting (physical row swaps) of an NN x NN matrix
-// stored at A[e * sld], e = i * NN + j.  Returns false on a zero pivot.
-template <class R>
-__device__ __forceinline__ bool qss_lu(R* __restrict__ A, const long long sld, int* __restrict__ perm) {
-#pragma unroll 1
-  for (int k = 0; k < QSS_NN; ++k) {
-    int p = k;
-    auto best = qss_mag(A[(k * QSS_NN + k) * sld]);
-#pragma unroll 1
-    for (int i = k + 1; i < QSS_NN; ++i) {
-      const auto v = qss_mag(A[(i * QSS_NN + k) * sld]);
-      if (v > best) { best = v; p = i; }
-    }
-    perm[k] = p;
-    if (!(best > 0)) return false;
-    if (p != k) {
-#pragma unroll 1
-      for (int j = 0; j < QSS_NN; ++j) {
-        const R t = A[(k * QSS_NN + j) * sld];
-        A[(k * QSS_NN + j) * sld] = A[(p * QSS_NN + j) * sld];
-        A[(p * QSS_NN + j) * sld] = t;
-      }
-    }
-    const R inv = R(1) / A[(k * QSS_NN + k) * sld];
-#pragma unroll 1
-    for (int i = k + 1; i < QSS_NN; ++i) {
-      const R l = A[(i * QSS_NN + k) * sld] * inv;
-      A[(i * QSS_NN + k) * sld] = l;
-      if (l != R(0)) {
-#pragma unroll 4
-        for (int j = k + 1; j < QSS_NN; ++j)
-          A[(i * QSS_NN + j) * sld] = fma(-l, A[(k * QSS_NN + j) * sld], A[(i * QSS_NN + j) * sld]);
-      }
-    }
-  }
-  return true;
+// Magnitude key for pivot search (an integer, so that the comparisons and the
+// warp reduction stay off the FP64 pipe).
+__device__ __forceinline__ long long qss_key(double x) { return qss_absbits(x); }
+__device__ __forceinline__ long long qss_key(float x) {
+  return (long long)(__float_as_int(x) & 0x7fffffff);
 }
 
-// Solve with the factors of qss_lu: x = M^-1 b (b permuted and overwritten).
-template <class R>
-__device__ __forceinline__ void qss_lu_solve(const R* __restrict__ A, const long long sld,
-                                             const int* __restrict__ perm, R* __restrict__ b) {
-#pragma unroll 1
-  for (int k = 0; k < QSS_NN; ++k) {
-    const int p = perm[k];
-    if (p != k) { const R t = b[k]; b[k] = b[p]; b[p] = t; }
-  }
-#pragma unroll 1
-  for (int i = 1; i < QSS_NN; ++i) {
-    R s = b[i];
-#pragma unroll 4
-    for (int j = 0; j < i; ++j) s = fma(-A[(i * QSS_NN + j) * sld], b[j], s);
-    b[i] = s;
-  }
-#pragma unroll 1
-  for (int i = QSS_NN - 1; i >= 0; --i) {
-    R s = b[i];
-#pragma unroll 4
-    for (int j = i + 1; j < QSS_NN; ++j) s = fma(-A[(i * QSS_NN + j) * sld], b[j], s);
-    b[i] = s / A[(i * QSS_NN + i) * sld];
-  }
-}
-
-struct QssNewtonOpts {
-  int max_iter;
-  double rtol, atol_C, atol_T;
-  int max_refine;
-  double refine_tol;
-};
+__device__ __forceinline__ double qss_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float qss_shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_newton_setup_kernel(long long cells, long long c0, long long ld, const double* __restrict__ rho,
                         const double* __restrict__ T, const double* __restrict__ Y,
                         double* __restrict__ PHI, double* __restrict__ PHI0, int* __restrict__ ACT,
-                        int* __restrict__ ST, int* __restrict__ IT, long long sld) {
+                        int* __restrict__ ST, int* __restrict__ IT, int* __restrict__ LIST,
+                        int* __restrict__ NACT, long long sld) {
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  if (s == 0) { NACT[0] = (int)cells; NACT[1] = 0; }
   if (s >= cells) return;
   const long long c = c0 + s;
   const double r = rho[c];
@@ -148,139 +102,345 @@ qss_newton_setup_kernel(long long cells, long long c0, long long ld, const doubl
   ACT[s] = 1;
   ST[s] = QSS_CELL_MAXITER;
   IT[s] = 0;
+  LIST[s] = (int)s;
+}
+
+struct QssNewtonOpts {
+  int max_iter;
+  double rtol, atol_C, atol_T;
+  int max_refine;
+  double refine_tol;
+};
+
+// Factor the rows a[slot][j] (row r = lane + 32 slot) with partial pivoting,
+// eliminating the right-hand side y[slot] with them.  On return row r holds
+// multipliers in the columns before its pivot order ord[slot] and its row of
+// U from there on; y holds the forward-substituted right-hand side; piv[k]
+// (shared) is the row pivoted at step k and pinv[k] the reciprocal of its
+// pivot.  Returns false on a zero pivot.
+template <class R>
+__device__ __forceinline__ bool qss_warp_factor(R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
+                                                int (&ord)[QSS_NSLOT], int* __restrict__ piv,
+                                                double* __restrict__ pinv, const int lane) {
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) ord[sl] = (lane + 32 * sl < QSS_NN) ? QSS_NN : -1;
+#pragma unroll
+  for (int k = 0; k < QSS_NN; ++k) {
+    long long best = -1;
+    int brow = QSS_NN;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const long long key = (ord[sl] == QSS_NN) ? qss_key(a[sl][k]) : -1LL;
+      if (key > best) { best = key; brow = lane + 32 * sl; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+      if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+    }
+    if (best <= 0) return false;
+    const int pl = brow & 31, ps = brow >> 5;
+    if (lane == 0) piv[k] = brow;
+    R pv = a[0][k], py = y[0];
+#pragma unroll
+    for (int sl = 1; sl < QSS_NSLOT; ++sl)
+      if (ps == sl) { pv = a[sl][k]; py = y[sl]; }
+    pv = qss_shfl(pv, pl);
+    py = qss_shfl(py, pl);
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl)
+      if (lane == pl && ps == sl) ord[sl] = k;
+    const R inv = R(1) / pv;
+    if (lane == 0) pinv[k] = (double)inv;
+    R l[QSS_NSLOT];
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const bool elim = ord[sl] == QSS_NN;
+      l[sl] = elim ? a[sl][k] * inv : R(0);
+      if (elim) a[sl][k] = l[sl];
+      y[sl] = fma(-l[sl], py, y[sl]);
+    }
+#pragma unroll
+    for (int j = k + 1; j < QSS_NN; ++j) {
+      R pj = a[0][j];
+#pragma unroll
+      for (int sl = 1; sl < QSS_NSLOT; ++sl)
+        if (ps == sl) pj = a[sl][j];
+      pj = qss_shfl(pj, pl);
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) a[sl][j] = fma(-l[sl], pj, a[sl][j]);
+    }
+  }
+  return true;
+}
+
+// Forward substitution of a new right-hand side with the stored multipliers.
+template <class R>
+__device__ __forceinline__ void qss_warp_forward(const R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
+                                                 const int (&ord)[QSS_NSLOT],
+                                                 const int* __restrict__ piv) {
+#pragma unroll
+  for (int k = 0; k < QSS_NN; ++k) {
+    const int p = piv[k];
+    const int pl = p & 31, ps = p >> 5;
+    R py = y[0];
+#pragma unroll
+    for (int sl = 1; sl < QSS_NSLOT; ++sl)
+      if (ps == sl) py = y[sl];
+    py = qss_shfl(py, pl);
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl)
+      if (ord[sl] > k) y[sl] = fma(-a[sl][k], py, y[sl]);
+  }
+}
+
+// Back substitution (column oriented): x_k from the row of pivot order k,
+// k = NN-1 .. 0.  Lane (k & 31) keeps x_k in xo[k >> 5], so that every lane
+// ends with the entries of x whose index is lane + 32 slot.
+template <class R>
+__device__ __forceinline__ void qss_warp_back(const R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
+                                              const int (&ord)[QSS_NSLOT],
+                                              const int* __restrict__ piv,
+                                              const double* __restrict__ pinv, R (&xo)[QSS_NSLOT],
+                                              const int lane) {
+#pragma unroll
+  for (int k = QSS_NN - 1; k >= 0; --k) {
+    const int p = piv[k];
+    const int pl = p & 31, ps = p >> 5;
+    R v = y[0];
+#pragma unroll
+    for (int sl = 1; sl < QSS_NSLOT; ++sl)
+      if (ps == sl) v = y[sl];
+    const R xk = qss_shfl(v, pl) * (R)pinv[k];
+    if (lane == (k & 31)) xo[k >> 5] = xk;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl)
+      if (ord[sl] >= 0 && ord[sl] < k) y[sl] = fma(-a[sl][k], xk, y[sl]);
+  }
+}
+
+__device__ __forceinline__ double qss_mentry(const double* __restrict__ M64, long long sld,
+                                             long long tq, int r, int j, double hq) {
+  const double m = -hq * M64[(r * QSS_NN + j) * sld + tq];
+  return (j == r) ? 1.0 + m : m;
 }
 
 template <bool FP32IR>
-__device__ __forceinline__ void qss_newton_update(const long long s, const double h,
-                                                  double* __restrict__ PHI, const double* __restrict__ PHI0,
-                                                  const double* __restrict__ F, double* __restrict__ M64,
-                                                  float* __restrict__ M32, int* __restrict__ ACT,
-                                                  int* __restrict__ ST, int* __restrict__ IT,
-                                                  const long long sld, const QssNewtonOpts o) {
-  double b[QSS_NN], x[QSS_NN], g[QSS_NN], f[QSS_NN];
-  int perm[QSS_NN];
-  IT[s] += 1;
-  double* A = M64 + s;
-  bool ok = true;
+__device__ __forceinline__ void qss_newton_update(
+    long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
+    const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,
+    int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT, const int* __restrict__ LIST,
+    const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
+    const QssNewtonOpts o) {
+  using R = typename std::conditional<FP32IR, float, double>::type;
+  __shared__ int sh_piv[QSS_UPD_WARPS][QSS_NN];
+  __shared__ double sh_x[QSS_UPD_WARPS][QSS_NN + 1];
+  __shared__ double sh_pinv[QSS_UPD_WARPS][QSS_NN];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long t0 = ((long long)blockIdx.x * QSS_UPD_WARPS + w) * 32;
+  const int nact = *NACT;
+  if (t0 >= nact) return;
+  const long long t = t0 + lane;
+  bool mine = t < nact;
+  const int s = mine ? LIST[t] : 0;
+  double h = 0.0;
+  if (mine) {   // g = -G(phi) into F, own cell
+    h = dt[dt_stride ? c0 + s : 0];
+    IT[s] += 1;
+    bool ok = true;
 #pragma unroll
-  for (int i = 0; i < QSS_NN; ++i) {
-    b[i] = -(PHI[i * sld + s] - PHI0[i * sld + s] - h * F[i * sld + s]);
-    ok = ok && qss_finite(b[i]);
-  }
-  // M = I - h J in place
-#pragma unroll 1
-  for (int e = 0; e < QSS_NN * QSS_NN; ++e) {
-    const double v = -h * A[e * sld];
-    A[e * sld] = (e % (QSS_NN + 1) == 0) ? 1.0 + v : v;
-    ok = ok && qss_finite(v);
-  }
-  if (!ok) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; return; }
-  if (!FP32IR) {
-    if (!qss_lu<double>(A, sld, perm)) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; return; }
-#pragma unroll
-    for (int i = 0; i < QSS_NN; ++i) x[i] = b[i];
-    qss_lu_solve<double>(A, sld, perm, x);
-  } else {
-    // power-of-two equilibration: rows, then columns
-    int er[QSS_NN], ec[QSS_NN];
-#pragma unroll 1
     for (int i = 0; i < QSS_NN; ++i) {
+      const double g = -(PHI[i * sld + s] - PHI0[i * sld + s] - h * F[i * sld + t]);
+      F[i * sld + t] = g;
+      ok = ok && qss_finite(g);
+    }
+    if (!ok) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; mine = false; }
+  }
+  __syncwarp();
+  unsigned todo = __ballot_sync(0xffffffffu, mine);
+  unsigned failed = 0;
+  while (todo) {
+    const int q = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const double hq = __shfl_sync(0xffffffffu, h, q);
+    const long long tq = t0 + q;
+    R a[QSS_NSLOT][QSS_NN];
+    R y[QSS_NSLOT];
+    int ord[QSS_NSLOT];
+    int er[QSS_NSLOT];
+    double gr[QSS_NSLOT];
+    bool fin = true;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int r = lane + 32 * sl;
+      const bool live = r < QSS_NN;
+      gr[sl] = live ? F[r * sld + tq] : 0.0;
+      er[sl] = 0;
       long long mx = 0;
-#pragma unroll 4
-      for (int j = 0; j < QSS_NN; ++j) mx = max(mx, qss_absbits(A[(i * QSS_NN + j) * sld]));
-      const int e = qss_ilogb(__longlong_as_double(mx));
-      er[i] = e < -1000 ? 0 : e;
-    }
-#pragma unroll 1
-    for (int j = 0; j < QSS_NN; ++j) {
-      int emax = -1100;
-#pragma unroll 4
-      for (int i = 0; i < QSS_NN; ++i) {
-        const double v = A[(i * QSS_NN + j) * sld];
-        if (qss_absbits(v) != 0) emax = max(emax, qss_ilogb(v) - er[i]);
-      }
-      ec[j] = emax < -1000 ? 0 : emax;
-    }
-    float* Fm = M32 + s;
-#pragma unroll 1
-    for (int i = 0; i < QSS_NN; ++i) {
-#pragma unroll 4
-      for (int j = 0; j < QSS_NN; ++j) {
-        const int e = -(er[i] + ec[j]);
-        const double scaled = A[(i * QSS_NN + j) * sld] * qss_pow2(max(min(e, 1000), -1000));
-        Fm[(i * QSS_NN + j) * sld] = (float)scaled;
-      }
-    }
-    if (!qss_lu<float>(Fm, sld, perm)) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; return; }
-    // x = D_c (LU32)^-1 D_r b, refined with FP64 residuals
-    float y[QSS_NN];
-#pragma unroll
-    for (int i = 0; i < QSS_NN; ++i) { x[i] = 0.0; g[i] = b[i]; f[i] = b[i]; }
-#pragma unroll 1
-    for (int sweep = 0; sweep <= o.max_refine; ++sweep) {
-      // the right-hand side is row-scaled, then normalised by a power of two
-      long long rmx = 0;
-#pragma unroll
-      for (int i = 0; i < QSS_NN; ++i) {
-        b[i] = f[i] * qss_pow2(max(min(-er[i], 1000), -1000));
-        rmx = max(rmx, qss_absbits(b[i]));
-      }
-      const int es = max(min(qss_ilogb(__longlong_as_double(rmx)), 1000), -1000);
-      const double rs = qss_pow2(-es);
-#pragma unroll
-      for (int i = 0; i < QSS_NN; ++i) y[i] = (float)(b[i] * rs);
-      qss_lu_solve<float>(Fm, sld, perm, y);
-      double dmax = 0.0, xmax = 0.0;
 #pragma unroll
       for (int j = 0; j < QSS_NN; ++j) {
-        const double d = (double)y[j] * qss_pow2(max(min(es - ec[j], 1000), -1000));
-        x[j] += d;
-        dmax = fmax(dmax, fabs(d));
-        xmax = fmax(xmax, fabs(x[j]));
+        const double m = live ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
+        fin = fin && qss_finite(m);
+        if (FP32IR) mx = max(mx, qss_absbits(m));
+        else a[sl][j] = m;
       }
-      if (dmax <= o.refine_tol * xmax || sweep == o.max_refine) break;
-      // residual f = g - M x in FP64
-#pragma unroll 1
-      for (int i = 0; i < QSS_NN; ++i) {
-        double acc = g[i];
-#pragma unroll 4
-        for (int j = 0; j < QSS_NN; ++j) acc = fma(-A[(i * QSS_NN + j) * sld], x[j], acc);
-        f[i] = acc;
+      if (FP32IR) {
+        const int e = qss_ilogb(__longlong_as_double(mx));
+        er[sl] = e < -1000 ? 0 : e;
+      }
+      y[sl] = FP32IR ? R(0) : (R)gr[sl];
+    }
+    if (!__all_sync(0xffffffffu, fin)) {
+      if (lane == q) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
+      failed |= 1u << q;
+      continue;
+    }
+    double csr[QSS_NSLOT];   // column scales of this lane's columns (lane + 32 slot)
+    if (FP32IR) {
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) csr[sl] = 1.0;
+#pragma unroll
+      for (int j = 0; j < QSS_NN; ++j) {
+        double mj[QSS_NSLOT];
+        int em = -1100;
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+          const int r = lane + 32 * sl;
+          mj[sl] = r < QSS_NN ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
+          if (qss_absbits(mj[sl]) != 0) em = max(em, qss_ilogb(mj[sl]) - er[sl]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, off));
+        const int ec = em < -1000 ? 0 : em;
+        if (lane == (j & 31)) csr[j >> 5] = qss_pow2(-ec);
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) a[sl][j] = (R)(mj[sl] * qss_pow2(-(er[sl] + ec)));
       }
     }
+    if (!qss_warp_factor<R>(a, y, ord, sh_piv[w], sh_pinv[w], lane)) {
+      if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
+      failed |= 1u << q;
+      continue;
+    }
+    __syncwarp();
+    double xo[QSS_NSLOT];   // this lane's entries of the solution (index lane + 32 slot)
+    if (!FP32IR) {
+      R xr[QSS_NSLOT];
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) xr[sl] = 0;
+      qss_warp_back<R>(a, y, ord, sh_piv[w], sh_pinv[w], xr, lane);
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = (double)xr[sl];
+    } else {
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = 0.0;
+      double prev = 1e308;
+#pragma unroll 1
+      for (int sweep = 0; sweep <= o.max_refine; ++sweep) {
+        // scaled residual rows: D_r (g - M x), x shared by the warp in sh_x
+        double res[QSS_NSLOT];
+        long long rmx = 0;
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+          const int r = lane + 32 * sl;
+          double acc = gr[sl];
+          if (sweep > 0 && r < QSS_NN) {
+#pragma unroll 6
+            for (int j = 0; j < QSS_NN; ++j) acc = fma(-qss_mentry(M64, sld, tq, r, j, hq), sh_x[w][j], acc);
+          }
+          res[sl] = r < QSS_NN ? acc * qss_pow2(-er[sl]) : 0.0;
+          rmx = max(rmx, qss_absbits(res[sl]));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) rmx = max(rmx, __shfl_xor_sync(0xffffffffu, rmx, off));
+        if (rmx == 0) break;
+        const int es = qss_ilogb(__longlong_as_double(rmx));
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) y[sl] = (float)(res[sl] * qss_pow2(-es));
+        qss_warp_forward<R>(a, y, ord, sh_piv[w]);
+        R dr[QSS_NSLOT];
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) dr[sl] = 0;
+        qss_warp_back<R>(a, y, ord, sh_piv[w], sh_pinv[w], dr, lane);
+        double dmax = 0.0, xmax = 0.0;
+        __syncwarp();
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+          const int j = lane + 32 * sl;
+          if (j < QSS_NN) {
+            const double d = (double)dr[sl] * csr[sl] * qss_pow2(es);
+            xo[sl] += d;
+            sh_x[w][j] = xo[sl];
+            dmax = fmax(dmax, fabs(d));
+            xmax = fmax(xmax, fabs(xo[sl]));
+          }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+          xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+        }
+        __syncwarp();
+        if (dmax <= o.refine_tol * xmax || dmax >= 0.5 * prev) break;
+        prev = dmax;
+      }
+    }
+    // the update x of cell q back to F (column tq)
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int j = lane + 32 * sl;
+      if (j < QSS_NN) F[j * sld + tq] = xo[sl];
+    }
+    __syncwarp();
   }
+  __syncwarp();
+  if (!mine || ((failed >> lane) & 1u)) return;
+  // own cell: update phi, convergence test, next list
   double acc = 0.0;
   bool fin = true;
 #pragma unroll
   for (int i = 0; i < QSS_NN; ++i) {
-    const double p = PHI[i * sld + s] + x[i];
+    const double x = F[i * sld + t];
+    const double p = PHI[i * sld + s] + x;
     PHI[i * sld + s] = p;
-    const double w = o.rtol * fabs(p) + (i < QSS_N ? o.atol_C : o.atol_T);
-    const double q = x[i] / w;
-    acc = fma(q, q, acc);
+    const double wgt = o.rtol * fabs(p) + (i < QSS_N ? o.atol_C : o.atol_T);
+    const double qv = x / wgt;
+    acc = fma(qv, qv, acc);
     fin = fin && qss_finite(p);
   }
-  if (!fin) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; return; }
-  if (acc <= (double)QSS_NN) { ST[s] = QSS_CELL_CONVERGED; ACT[s] = 0; return; }
-  if (IT[s] >= o.max_iter) ACT[s] = 0;   // status stays MAXITER
+  bool keep = false;
+  if (!fin) {
+    ST[s] = QSS_CELL_NONFINITE;
+    ACT[s] = 0;
+  } else if (acc <= (double)QSS_NN) {
+    ST[s] = QSS_CELL_CONVERGED;
+    ACT[s] = 0;
+  } else if (IT[s] >= o.max_iter) {
+    ACT[s] = 0;   // status stays MAXITER
+  } else {
+    keep = true;
+  }
+  if (keep) LIST2[atomicAdd(NACT2, 1)] = s;
 }
 
-#define QSS_UPDATE_PARAMS                                                                        \
-  long long cells, long long c0, const double* __restrict__ dt, int dt_stride,                   \
-      double* __restrict__ PHI, const double* __restrict__ PHI0, const double* __restrict__ F,   \
-      double* __restrict__ M64, float* __restrict__ M32, int* __restrict__ ACT,                  \
-      int* __restrict__ ST, int* __restrict__ IT, long long sld, QssNewtonOpts o
+#define QSS_UPDATE_PARAMS                                                                         \
+  long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,          \
+      const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,    \
+      int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT,                          \
+      const int* __restrict__ LIST, const int* __restrict__ NACT, int* __restrict__ LIST2,        \
+      int* __restrict__ NACT2, long long sld, QssNewtonOpts o
 
-extern "C" __global__ void __launch_bounds__(QSS_BLOCK) qss_newton_update_fp64_kernel(QSS_UPDATE_PARAMS) {
-  const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
-  if (s >= cells || !ACT[s]) return;
-  qss_newton_update<false>(s, dt[dt_stride ? c0 + s : 0], PHI, PHI0, F, M64, M32, ACT, ST, IT, sld, o);
+extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS * 32)
+qss_newton_update_fp64_kernel(QSS_UPDATE_PARAMS) {
+  qss_newton_update<false>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
+                           NACT2, sld, o);
 }
 
-extern "C" __global__ void __launch_bounds__(QSS_BLOCK) qss_newton_update_fp32ir_kernel(QSS_UPDATE_PARAMS) {
-  const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
-  if (s >= cells || !ACT[s]) return;
-  qss_newton_update<true>(s, dt[dt_stride ? c0 + s : 0], PHI, PHI0, F, M64, M32, ACT, ST, IT, sld, o);
+extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS * 32)
+qss_newton_update_fp32ir_kernel(QSS_UPDATE_PARAMS) {
+  qss_newton_update<true>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
+                          NACT2, sld, o);
 }
 
 // Write the state back: T, Y (rho fixed), iterations and status.

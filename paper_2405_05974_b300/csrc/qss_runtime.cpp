@@ -185,8 +185,9 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
   long long nc = ncells, l = ld;
   const double* phi = nullptr;
-  const int* active = nullptr;
-  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &active};
+  const int* list = nullptr;
+  int* none = nullptr;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &list, &none};
   return launch_cells(m, m->f_jac, ncells, m->block, args, (CUstream)stream, 0);
 }
 
@@ -267,8 +268,9 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
     double* wp = d_w;
     double* tp = d_Td;
     const double* phi = nullptr;
-    const int* active = nullptr;
-    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp, &phi, &active};
+    const int* list = nullptr;
+    int* none = nullptr;
+    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp, &phi, &list, &list, &none};
     if ((rc = launch_cells(m, m->f_jac, cs, m->block, args, s, 0))) return rc;
     if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, (size_t)n * n, s))) return rc;
     if (wdot && (rc = copy2d(wdot + c0, true, hp, d_w, false, P, w, N, s))) return rc;

@@ -1,0 +1,126 @@
+"""Serving loop: continuous batching of implicit-step requests.
+
+Each request's result must not depend on what it was batched with: cells are
+independent, so a request served alone, served merged with others, and run
+through qss_implicit_step directly must agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2405_05974_b300 import binding, mechgen, workloads
+from paper_2405_05974_b300.qssc.build import build_mechanism
+
+pytestmark = pytest.mark.gpu
+
+_m = {}
+
+
+def mech(key):
+    if key not in _m:
+        m = workloads.mechanism(key)
+        _m[key] = (m, binding.Mechanism(build_mechanism(m), 0))
+    return _m[key]
+
+
+def host_state(key, n, seed):
+    m, _ = mech(key)
+    cfg = workloads.STATES[key]
+    cfg = type(cfg)(**{**cfg.__dict__, "seed": seed})
+    rho, T, Y = mechgen.generate_states(m, cfg, n)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    return pin(rho), pin(T), pin(Y)
+
+
+def clone(state):
+    return tuple(x.clone().pin_memory() for x in state)
+
+
+def direct(key, state, dt, prec):
+    _, gm = mech(key)
+    r, t, y = (x.cuda() for x in state)
+    it, st = gm.implicit_step(r, t, y, dt, precision=prec)
+    torch.cuda.synchronize()
+    return t.cpu(), y.cpu(), st.cpu()
+
+
+@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
+def test_same_result_alone_and_in_the_mix(prec):
+    _, tiny = mech("tiny")
+    _, hc = mech("hydrocarbon")
+    probe = host_state("tiny", 777, 11)
+    dt = 2e-6
+    ref_T, ref_Y, ref_st = direct("tiny", clone(probe), dt, prec)
+    srv = binding.Server(0, budget_bytes=2 << 30, n_streams=1, max_batch_cells=1 << 15)
+    try:
+        alone = clone(probe)
+        st_alone = torch.empty(777, dtype=torch.int32).pin_memory()
+        rid = srv.submit(tiny, *alone, dt, prec, status=st_alone)
+        assert srv.wait(rid) == 0
+        # a mix queued behind a long request (one stream): other tiny requests
+        # are merged with the probe, hydrocarbon ones form their own batches
+        head = host_state("hydrocarbon", 30000, 77)
+        ids, keep = [srv.submit(hc, *head, 1e-6, prec)], [head]
+        for i in range(6):
+            s = host_state("tiny", 300 + 97 * i, 100 + i)
+            keep.append(s)
+            ids.append(srv.submit(tiny, *s, dt * (1 + i), prec))
+            h = host_state("hydrocarbon", 256 + 50 * i, 200 + i)
+            keep.append(h)
+            ids.append(srv.submit(hc, *h, 1e-6, prec))
+            if i == 3:
+                mixed = clone(probe)
+                st_mixed = torch.empty(777, dtype=torch.int32).pin_memory()
+                mid = srv.submit(tiny, *mixed, dt, prec, status=st_mixed)
+        for r in ids + [mid]:
+            assert srv.wait(r) == 0
+        st = srv.stats()
+        assert st["completed"] == 15 and st["queued"] == 0
+        assert st["batches"] < 10          # queued requests were merged
+        assert st["p50_latency_us"] <= st["p99_latency_us"]
+    finally:
+        srv.close()
+    for got_T, got_Y, got_st in ((alone[1], alone[2], st_alone), (mixed[1], mixed[2], st_mixed)):
+        assert torch.equal(got_T, ref_T) and torch.equal(got_Y, ref_Y)
+        assert torch.equal(got_st, ref_st)
+
+
+def test_budget_admission_and_rejection():
+    _, hc = mech("hydrocarbon")
+    per_cell = 37 * 8 * 4 + 36 * 36 * 8 + 3 * 36 * 8   # io + FP64 scratch, approx
+    budget = 64 << 20
+    srv = binding.Server(0, budget_bytes=budget, n_streams=4, max_batch_cells=1 << 20)
+    try:
+        big = host_state("hydrocarbon", (budget // per_cell) * 2, 5)
+        with pytest.raises(binding.QSSError) as e:
+            srv.submit(hc, *big, 1e-6)
+        assert e.value.code == -7
+        # many requests that fit only a few at a time: all complete
+        reqs = [host_state("hydrocarbon", 2000, 300 + i) for i in range(8)]
+        refs = [direct("hydrocarbon", clone(s), 1e-6, binding.QSS_LU_FP64) for s in reqs]
+        ids = [srv.submit(hc, *s, 1e-6) for s in reqs]
+        for rid in ids:
+            assert srv.wait(rid) == 0
+        st = srv.stats()
+        assert st["bytes_peak"] <= budget and st["rejected"] == 1
+        for s, (rT, rY, _) in zip(reqs, refs):
+            assert torch.equal(s[1], rT) and torch.equal(s[2], rY)
+    finally:
+        srv.close()
+
+
+def test_wait_timeout_then_completion():
+    _, hc = mech("hydrocarbon")
+    srv = binding.Server(0, budget_bytes=4 << 30)
+    try:
+        s = host_state("hydrocarbon", 60000, 9)
+        rid = srv.submit(hc, *s, 1e-6)
+        try:
+            srv.wait(rid, timeout_us=0)
+        except binding.QSSError as e:
+            assert e.code == -6
+        assert srv.wait(rid) == 0
+        with pytest.raises(binding.QSSError):
+            srv.wait(rid)            # id released
+    finally:
+        srv.close()
