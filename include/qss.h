@@ -183,6 +183,27 @@ int qss_serve_wait(qss_server_t server, uint64_t req_id, int64_t timeout_us, int
 int qss_serve_stats(qss_server_t server, qss_serve_stats_t* out);
 void qss_serve_destroy(qss_server_t server);
 
+/* The implicit step for callers that cannot let the library allocate device
+ * memory (the paper has no counterpart; this is a deployment variant).  Same
+ * arguments, semantics and results as qss_implicit_step, but the Newton
+ * scratch is a fixed 64 MiB array in the library's device memory instead of
+ * memory the library allocates: applications that reserve and manage all of
+ * the GPU's memory themselves, or loops that must not pay the synchronisation
+ * an allocation can imply, call this one.  It calls no allocation routine; the
+ * cells are processed in chunks that fit the array.  Every GPU that loads the
+ * library holds the array until the process exits.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current), so make it before any stream capture.  Every call uses the same
+ * array: two calls whose work overlaps on the GPU (different streams, or
+ * different mechanism handles) race and corrupt each other; order them on one
+ * stream.  The array keeps the last call's contents; each call initialises
+ * every value it reads.  Errors: QSS_ERR_BUDGET if 32 cells of the mechanism
+ * need more scratch than the array holds (the message gives both sizes). */
+int qss_implicit_step_noalloc(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt,
+                              int dt_stride, const double* rho, double* T, double* Y,
+                              int precision, const qss_newton_opts* opts, int32_t* iters,
+                              int32_t* cell_status, void* stream);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* qss_last_error(void);
 

@@ -29,13 +29,26 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+NOALLOC = "qss_noalloc.cu"   # the only CUDA-runtime translation unit (static cudart)
+
+
 def build(force: bool = False, verbose: bool = False):
     srcs = [os.path.join(CSRC, s) for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     hdrs = [os.path.join(CSRC, "qss_internal.h"), os.path.join(CSRC, "qss_driver.h"), os.path.join(INCLUDE, "qss.h")]
-    if force or _newer(LIB, srcs + hdrs):
+    cu = os.path.join(CSRC, NOALLOC)
+    obj = os.path.join(PKG, "qss_noalloc.o")
+    if force or _newer(obj, [cu] + hdrs):
+        cmd = ["nvcc", "-c", *ARCH, "-O3", "-Xcompiler", "-fPIC", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
+               "-o", obj + ".tmp.o", cu]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        os.replace(obj + ".tmp.o", obj)
+    if force or _newer(LIB, srcs + hdrs + [obj]):
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
                "-I", INCLUDE, "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include"), "-o", LIB + ".tmp",
-               *srcs, "-lpthread", "-ldl"]
+               *srcs, obj, "-L", os.path.join(CUDA_HOME, "lib64"), "-lcudart_static", "-lrt",
+               "-lpthread", "-ldl"]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
