@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-implicit", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
 
@@ -184,6 +187,106 @@ def cpu_baseline(mech, states_cfg, seconds, ncells_cap=1 << 20):
 
 
 # ---------------------------------------------------------------------------
+# implicit step (backward Euler, FP64 LU vs FP32 LU + FP64 refinement)
+# ---------------------------------------------------------------------------
+def implicit_bench(gm, mech, ncells, dt, oracle_sample=0):
+    """One timed step per precision on the implicit workload (2^20 hydrocarbon
+    cells, dt = 1e-6 s) after one warm-up step."""
+    import torch
+    from paper_2405_05974_b300 import binding, mechgen, workloads
+    rho, T, Y = mechgen.generate_states(mech, workloads.STATES["implicit"], ncells)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    r = d(rho)
+    dtt = torch.full((1,), dt, dtype=torch.float64, device="cuda")
+    res = {}
+    out = {}
+    for prec, name in ((binding.QSS_LU_FP64, "fp64"), (binding.QSS_LU_FP32_IR, "fp32ir")):
+        times = []
+        for rep in range(2):
+            t, y = d(T), d(Y)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            it, st = gm.implicit_step(r, t, y, dtt, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = times[-1]
+        stn, itn = st.cpu().numpy(), it.cpu().numpy()
+        out[name] = (t.cpu().numpy(), y.cpu().numpy(), stn)
+        conv = stn == 0
+        res[name] = {"cells_per_s": ncells / (ms * 1e-3), "ms": ms,
+                     "status_counts": {"converged": int(conv.sum()), "maxiter": int((stn == 1).sum()),
+                                       "nonfinite": int((stn == 2).sum()), "singular": int((stn == 3).sum())},
+                     "newton_iters_mean": float(itn[conv].mean()) if conv.any() else None,
+                     "newton_iters_max": int(itn[conv].max()) if conv.any() else None}
+    a, b = out["fp64"], out["fp32ir"]
+    both = (a[2] == 0) & (b[2] == 0)
+    W = np.array(gm.W)[:, None]
+    ca, cb = rho[None, :] * a[1] / W, rho[None, :] * b[1] / W
+    pa, pb = np.vstack([ca, a[0][None]]), np.vstack([cb, b[0][None]])
+    atol = np.r_[np.full(gm.N, 1e-20), 1e-10][:, None]
+    rel = np.max(np.abs(pa - pb) / (np.abs(pa) + 10 * atol), axis=0)[both]
+    res["fp32ir_vs_fp64"] = {"cells_converged_both": int(both.sum()),
+                             "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
+                             "median_rel": float(np.median(rel)) if both.any() else None,
+                             "max_rel": float(rel.max()) if both.any() else None,
+                             "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell"}
+    res["speedup_fp32ir_over_fp64"] = res["fp32ir"]["cells_per_s"] / res["fp64"]["cells_per_s"]
+    res["workload"] = f"{mech['name']} backward Euler, dt = {dt:g} s, {ncells} cells"
+    return res
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson request stream over the continuous-batching server
+# ---------------------------------------------------------------------------
+def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, load=0.7):
+    import torch
+    from paper_2405_05974_b300 import binding, mechgen, workloads
+    rng = np.random.default_rng(seed)
+    lo, hi = 256, 65536
+    mean_cells = (hi - lo) / np.log(hi / lo)
+    rate = load * capacity_cells_s / mean_cells
+    pools = {}
+    for key, gm in mechs.items():
+        m = workloads.mechanism(key)
+        rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], hi)
+        pools[key] = (gm, rho, T, np.ascontiguousarray(Y))
+    keys = list(mechs)
+    srv = binding.Server(0, budget_bytes=60 << 30, n_streams=4, max_batch_cells=1 << 18)
+    reqs = []
+    t0 = time.perf_counter()
+    t_next = t0
+    while True:
+        now = time.perf_counter()
+        if now - t0 >= seconds:
+            break
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.005))
+            continue
+        key = keys[rng.choice(len(keys), p=weights)]
+        gm, rho, T, Y = pools[key]
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        dt = float(np.exp(rng.uniform(np.log(1e-7), np.log(1e-5))))
+        off = int(rng.integers(0, hi - n + 1))
+        rh = torch.from_numpy(rho[off:off + n].copy()).pin_memory()
+        th = torch.from_numpy(T[off:off + n].copy()).pin_memory()
+        yh = torch.from_numpy(np.ascontiguousarray(Y[:, off:off + n])).pin_memory()
+        reqs.append((srv.submit(gm, rh, th, yh, dt, precision), n))
+        t_next += rng.exponential(1.0 / rate)
+    for rid, _ in reqs:
+        srv.wait(rid)
+    el = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return {"requests": len(reqs), "offered_rate_per_s": rate, "cells": int(sum(n for _, n in reqs)),
+            "p50_latency_ms": st["p50_latency_us"] / 1e3, "p99_latency_ms": st["p99_latency_us"] / 1e3,
+            "cells_per_s": st["cells_per_s"], "batches": st["batches"],
+            "bytes_peak": st["bytes_peak"], "wall_s": el}
+
+
+# ---------------------------------------------------------------------------
 def main():
     a = parse()
     rank, world, local, pg = dist_setup()
@@ -297,6 +400,20 @@ def main():
                "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
                "gpu_launches_per_step": nchunks}
         del Jh
+    implicit = None
+    if not a.no_implicit and key == "hydrocarbon":
+        implicit = implicit_bench(gm, mech, workloads.NCELLS["implicit"], workloads.IMPLICIT_DT)
+    serving = None
+    if not a.no_serve and key == "hydrocarbon" and rank == 0:
+        from paper_2405_05974_b300 import binding as _b
+        mechs = {"tiny": _b.Mechanism(build_mechanism(workloads.mechanism("tiny")), local), "hydrocarbon": gm}
+        weights = [0.25, 0.75]
+        serving = {"mix": "tiny 0.25 / hydrocarbon 0.75 (the large mechanism is not in the mix: see design notes)",
+                   "sizes": "log-uniform 256..65536 cells", "dt": "log-uniform 1e-7..1e-5 s",
+                   "budget_bytes": 60 << 30, "load": 0.7}
+        for prec, name in ((_b.QSS_LU_FP32_IR, "fp32ir"), (_b.QSS_LU_FP64, "fp64")):
+            cap = implicit[name]["cells_per_s"] if implicit else 2e5
+            serving[name] = serve_bench(mechs, weights, prec, a.serve_seconds, cap)
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = cpu_baseline(mech, workloads.STATES[key], a.cpu_seconds)
@@ -307,6 +424,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
             "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps, "clocks": clk.summary(),
+            "implicit": implicit, "serving": serving,
             "kernel": {"ptxas": meta["kernels"].get("qss_jac_kernel", {}),
                        "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}
     print(json.dumps(line), flush=True)

@@ -94,7 +94,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   int* NACT = IT + 3 * S;   // two counters (S is a multiple of 32, so they fit in the tail)
   long long sld = chunk, l = ld;
   int rc;
-  const int upd_threads = 128;   // QSS_UPD_WARPS warps of 32 lanes, one cell per warp at a time
+  const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
   for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
     long long cells = std::min<int64_t>(chunk, ncells - c0), cc0 = c0;
     void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld};

@@ -48,7 +48,11 @@
 #error "the warp-cooperative Newton solver supports at most 63 transported species"
 #endif
 #define QSS_NSLOT ((QSS_NN + 31) / 32)
-#define QSS_UPD_WARPS 4
+// warps per update block: the FP32_IR form stages one matrix per warp in
+// shared memory (NN x (NN+1) doubles), within the 48 KB static limit
+#define QSS_MSTRIDE (QSS_NN + 1)
+#define QSS_MBYTES (QSS_NN * QSS_MSTRIDE * 8)
+#define QSS_UPD_WARPS (QSS_MBYTES * 4 <= 44000 ? 4 : (QSS_MBYTES * 2 <= 44000 ? 2 : 1))
 
 __device__ __forceinline__ bool qss_finite(double x) {
   return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -237,6 +241,8 @@ __device__ __forceinline__ void qss_newton_update(
   __shared__ int sh_piv[QSS_UPD_WARPS][QSS_NN];
   __shared__ double sh_x[QSS_UPD_WARPS][QSS_NN + 1];
   __shared__ double sh_pinv[QSS_UPD_WARPS][QSS_NN];
+  // FP32_IR: per-warp copy of the FP64 Newton matrix (padded rows)
+  __shared__ double sh_m[FP32IR ? QSS_UPD_WARPS * QSS_NN * QSS_MSTRIDE : 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long t0 = ((long long)blockIdx.x * QSS_UPD_WARPS + w) * 32;
   const int nact = *NACT;
@@ -271,6 +277,18 @@ __device__ __forceinline__ void qss_newton_update(
     int er[QSS_NSLOT];
     double gr[QSS_NSLOT];
     bool fin = true;
+    double* Ms = &sh_m[FP32IR ? w * QSS_NN * QSS_MSTRIDE : 0];   // this warp's copy of M = I - hq J
+    if (FP32IR) {
+      // one pass over J in global memory: consecutive entries across lanes
+#pragma unroll 4
+      for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
+        const int r = e / QSS_NN, j = e - r * QSS_NN;
+        const double m = -hq * M64[e * sld + tq];
+        fin = fin && qss_finite(m);
+        Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
+      }
+      __syncwarp();
+    }
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int r = lane + 32 * sl;
@@ -280,10 +298,13 @@ __device__ __forceinline__ void qss_newton_update(
       long long mx = 0;
 #pragma unroll
       for (int j = 0; j < QSS_NN; ++j) {
-        const double m = live ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
-        fin = fin && qss_finite(m);
-        if (FP32IR) mx = max(mx, qss_absbits(m));
-        else a[sl][j] = m;
+        if (FP32IR) {
+          if (live) mx = max(mx, qss_absbits(Ms[r * QSS_MSTRIDE + j]));
+        } else {
+          const double m = live ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
+          fin = fin && qss_finite(m);
+          a[sl][j] = m;
+        }
       }
       if (FP32IR) {
         const int e = qss_ilogb(__longlong_as_double(mx));
@@ -307,7 +328,7 @@ __device__ __forceinline__ void qss_newton_update(
 #pragma unroll
         for (int sl = 0; sl < QSS_NSLOT; ++sl) {
           const int r = lane + 32 * sl;
-          mj[sl] = r < QSS_NN ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
+          mj[sl] = r < QSS_NN ? Ms[r * QSS_MSTRIDE + j] : 0.0;
           if (qss_absbits(mj[sl]) != 0) em = max(em, qss_ilogb(mj[sl]) - er[sl]);
         }
 #pragma unroll
@@ -347,7 +368,7 @@ __device__ __forceinline__ void qss_newton_update(
           double acc = gr[sl];
           if (sweep > 0 && r < QSS_NN) {
 #pragma unroll 6
-            for (int j = 0; j < QSS_NN; ++j) acc = fma(-qss_mentry(M64, sld, tq, r, j, hq), sh_x[w][j], acc);
+            for (int j = 0; j < QSS_NN; ++j) acc = fma(-Ms[r * QSS_MSTRIDE + j], sh_x[w][j], acc);
           }
           res[sl] = r < QSS_NN ? acc * qss_pow2(-er[sl]) : 0.0;
           rmx = max(rmx, qss_absbits(res[sl]));

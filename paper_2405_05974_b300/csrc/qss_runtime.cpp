@@ -126,12 +126,22 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
       return fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + need[i]);
     }
   }
-  // optional kernels (implicit step)
+  // optional kernels (implicit step), in newton.cubin
   const char* opt[] = {"qss_newton_update_fp64_kernel", "qss_newton_update_fp32ir_kernel",
                        "qss_newton_setup_kernel", "qss_newton_finish_kernel"};
   CUfunction* oslot[] = {&m->f_newton[0], &m->f_newton[1], &m->f_newton_setup, &m->f_newton_finish};
+  if (drv().cuModuleLoad(&m->mod_newton, (dir + "/newton.cubin").c_str()) != CUDA_SUCCESS)
+    m->mod_newton = nullptr;
   for (int i = 0; i < 4; ++i)
-    if (drv().cuModuleGetFunction(oslot[i], m->mod, opt[i]) != CUDA_SUCCESS) *oslot[i] = nullptr;
+    if (!m->mod_newton || drv().cuModuleGetFunction(oslot[i], m->mod_newton, opt[i]) != CUDA_SUCCESS)
+      *oslot[i] = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    int tpb = 0;
+    if (m->f_newton[i] &&
+        drv().cuFuncGetAttribute(&tpb, CU_FUNC_ATTRIBUTE_MAX_THREADS_PER_BLOCK, m->f_newton[i]) == CUDA_SUCCESS &&
+        tpb > 0)
+      m->upd_threads[i] = tpb;
+  }
   *out = m;
   return QSS_OK;
 }
@@ -145,6 +155,7 @@ void qss_mech_free(qss_mech_t m) {
   }
   if (m->newton_scratch) drv().cuMemFree(m->newton_scratch);
   if (m->mod) drv().cuModuleUnload(m->mod);
+  if (m->mod_newton) drv().cuModuleUnload(m->mod_newton);
   drv().cuDevicePrimaryCtxRelease(m->dev);
   delete m;
 }
