@@ -134,7 +134,7 @@ typedef struct {
   double atol_C;       /* mol/m^3, default 1e-20                             */
   double atol_T;       /* K, default 1e-10                                   */
   int max_refine;      /* FP32_IR refinement sweeps (default 10)             */
-  double refine_tol;   /* FP32_IR relative correction target (default 1e-14) */
+  double refine_tol;   /* FP32_IR relative correction target (default 1e-8)  */
 } qss_newton_opts;
 
 int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt,

@@ -57,7 +57,7 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
   if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR)
     return fail(QSS_ERR_INVALID_ARG, "unknown precision");
   if (dt_stride != 0 && dt_stride != 1) return fail(QSS_ERR_INVALID_ARG, "dt_stride must be 0 or 1");
-  *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-14};
+  *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8};
   if (opts) *o = *opts;
   if (o->max_iter < 1 || o->max_refine < 0 || !(o->rtol >= 0) || !(o->atol_C >= 0) ||
       !(o->atol_T >= 0) || !(o->refine_tol >= 0))

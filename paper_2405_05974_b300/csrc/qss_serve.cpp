@@ -321,7 +321,7 @@ int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts
   int rc = ctx_for_device(device, &s->dev, &s->ctx);
   if (rc) { delete s; return rc; }
   s->device = device;
-  s->newton = {20, 1e-12, 1e-20, 1e-10, 10, 1e-14};
+  s->newton = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8};
   if (opts) {
     if (opts->n_streams > 0) s->n_streams = opts->n_streams;
     if (opts->max_batch_cells > 0) s->max_batch_cells = opts->max_batch_cells;
