@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-implicit", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-variants", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -239,6 +240,53 @@ def implicit_bench(gm, mech, ncells, dt, oracle_sample=0):
 
 
 # ---------------------------------------------------------------------------
+# Section 3.3 figures: simplified Jacobians, FD Jacobian
+# ---------------------------------------------------------------------------
+def variants_bench(key, gm, r, t, y, ncells_fd=1 << 18):
+    """The relative Frobenius error (Eq. frobErr) of the exact, constant-QSS
+    and zero-QSS Jacobians against the central FD Jacobian (step 1e-4) over
+    100 states of the Section 3.3.1 protocol, the nonzero fraction of their
+    species blocks (Table memQSS), and the throughput of the FD Jacobian
+    kernel against the analytic one on the bench workload's first cells."""
+    import torch
+    from paper_2405_05974_b300 import analysis, binding, mechgen, workloads
+    from paper_2405_05974_b300.qssc.build import build_mechanism
+    mech = workloads.mechanism(key)
+    rng = np.random.default_rng(11)
+    C = rng.uniform(1e-4, 1.0, size=(gm.N, 100))
+    Tp = rng.uniform(300.0, 1300.0, size=100)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    pr, pt, py = (d(x) for x in mechgen.concentrations_to_state(mech, C, Tp))
+    Jfd = gm.jacobian_fd(pr, pt, py, 1e-4, 1e-4)
+    out = {"protocol": "100 states, C ~ U[1e-4, 1] mol/m^3, T ~ U[300, 1300] K, central FD step 1e-4",
+           "eps_J": {}, "nonzero_fraction": {}}
+    for v in ("exact", "const_qss", "zero_qss"):
+        vm = gm if v == "exact" else binding.Mechanism(build_mechanism(mech, jac_variant=v), gm.device)
+        J, _, _ = vm.jacobian(pr, pt, py)
+        out["eps_J"][v] = analysis.frobenius_error(J, Jfd)
+        out["nonzero_fraction"][v] = analysis.nonzero_fraction(J, gm.N)
+    nc = min(ncells_fd, t.shape[0])
+    n = gm.n
+    J = torch.empty((n * n, t.shape[0]), dtype=torch.float64, device="cuda")
+    ms = {}
+    for name, fn in (("analytic", lambda: gm.jacobian(r, t, y, jac=J, ncells=nc, want_rates=False)),
+                     ("fd", lambda: gm.jacobian_fd(r, t, y, 1e-4, 1e-4, jac=J, ncells=nc))):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1)
+    out["fd_jacobian_cells_per_s"] = nc / (ms["fd"] * 1e-3)
+    out["analytic_jacobian_cells_per_s"] = nc / (ms["analytic"] * 1e-3)
+    out["analytic_over_fd_speedup"] = ms["fd"] / ms["analytic"]
+    out["timing_cells"] = nc
+    del J
+    return out
+
+
+# ---------------------------------------------------------------------------
 # serving: Poisson request stream over the continuous-batching server
 # ---------------------------------------------------------------------------
 def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, load=0.7):
@@ -323,10 +371,10 @@ def main():
         return
 
     import torch
-    from paper_2405_05974_b300 import binding, mechgen
+    from paper_2405_05974_b300 import autotune, binding, mechgen
     from paper_2405_05974_b300.qssc.build import build_mechanism, load_meta
     torch.cuda.set_device(local)
-    art = build_mechanism(mech)
+    art = autotune.artefact(mech, torch.cuda.get_device_name(local))
     meta = load_meta(art)
     gm = binding.Mechanism(art, local)
     st_cfg = workloads.STATES[key]
@@ -400,6 +448,9 @@ def main():
                "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
                "gpu_launches_per_step": nchunks}
         del Jh
+    variants = None
+    if not a.no_variants and rank == 0 and key in ("tiny", "hydrocarbon"):
+        variants = variants_bench(key, gm, r, t, y)
     implicit = None
     if not a.no_implicit and key == "hydrocarbon":
         implicit = implicit_bench(gm, mech, workloads.NCELLS["implicit"], workloads.IMPLICIT_DT)
@@ -424,8 +475,9 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
             "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps, "clocks": clk.summary(),
-            "implicit": implicit, "serving": serving,
+            "implicit": implicit, "serving": serving, "jacobian_variants": variants,
             "kernel": {"ptxas": meta["kernels"].get("qss_jac_kernel", {}),
+                       "defines": meta.get("defines", []),
                        "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}
     print(json.dumps(line), flush=True)
 

@@ -75,7 +75,8 @@ enum {
 
 /* ---------------------------------------------------------------------------
  * Mechanisms.  An artefact directory is produced by the mechanism compiler
- * (paper_2405_05974_b300.qssc): mech.cubin (sm_103a) and meta.txt.
+ * (paper_2405_05974_b300.qssc): jac.cubin, wdot.cubin, newton.cubin (sm_103a)
+ * and meta.txt.
  * qss_mech_load loads it on `device` (the primary context, shared with the
  * CUDA runtime) and returns a handle owned by the caller, released with
  * qss_mech_free.  Errors: QSS_ERR_INVALID_ARG (null arguments),
@@ -102,6 +103,24 @@ int qss_wdot(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho, con
 int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
                  const double* T, const double* Y, double* jac, double* wdot, double* Tdot,
                  void* stream);
+
+/* Which Jacobian qss_jacobian computes is fixed when the artefact is built:
+ * the exact one above (default), or the simplified ones of Section 3.3.1
+ * (constant-QSS: the second term of Eq. JQSS dropped; zero-QSS: that term
+ * dropped and the QSS concentrations set to zero inside the Jacobian), each
+ * with the temperature column analytic or by the central difference of
+ * Section 3.3.2 (step h = 2^(e-20) for T in [2^e, 2^(e+1))).  The row of T
+ * follows from the species rows by the chain rule in every variant. */
+
+/* Central finite-difference Jacobian of f = (wdot, Tdot), the reference of
+ * Eq. (frobErr): column j = (f(phi + h e_j) - f(phi - h e_j)) / (2h), with the
+ * absolute step h = dC (mol/m^3) for the concentration columns and h = dT (K)
+ * for the temperature column.  Same layout and arrays as qss_jacobian; costs
+ * 2(N+1) source-term evaluations per cell.  Errors: QSS_ERR_INVALID_ARG for
+ * null arrays or steps that are not finite and positive. */
+int qss_jacobian_fd(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
+                    const double* T, const double* Y, double dC, double dT, double* jac,
+                    void* stream);
 
 /* The same as qss_jacobian for HOST arrays with ld = ncells.  The batch is
  * processed in chunks of `chunk` cells (0 = automatic) through two device

@@ -13,6 +13,12 @@ Parity status of each function (see the test files named beside them):
                                      binary128 rerun (tests/test_oracle_*.py)
   be_step ......................... pinned: closed-form linear case, mass
                                      invariant, Newton residual
+  eval_variant (constant-QSS, zero-QSS, FD T column)
+                                    pinned: complex step at fixed C_Q (the
+                                     definition of the simplified Jacobians),
+                                     complex step of the T column
+  jac_fd / jac_fd_errbound ........ pinned: first- and second-order
+                                     convergence to the complex-step Jacobian
   qss_groups / tarjan ............. pinned: the paper's Fig. 2 example graph
 """
 from __future__ import annotations
@@ -63,6 +69,12 @@ def lib():
                                               ctypes.c_double, _dp, ctypes.c_int]
         L.oracle_jac_fd.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int]
+        L.oracle_jac_fd_errbound.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        L.oracle_eval_variant.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, ctypes.c_int,
+                                          ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int]
+        L.oracle_jac_cs_fixed_cq.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, _dp,
+                                             ctypes.c_double, _dp, ctypes.c_int]
         L.oracle_qss_residual.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, _dp, _dp,
                                           ctypes.c_int]
         L.oracle_qss_newton_q128.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp,
@@ -237,6 +249,44 @@ class OracleMech:
                                  _p(J), nthreads)
         if nf:
             raise RuntimeError("finite differences failed")
+        return J
+
+    def jac_fd_errbound(self, rho, T, Y, dC, dT, central=True, nthreads=0):
+        """``jac_fd`` in the running-error type: (J, absolute rounding bound)."""
+        rho, T, Y, ld = self._state(rho, T, Y)
+        J = np.zeros((self.n * self.n, ld)); E = np.zeros_like(J)
+        nf = lib().oracle_jac_fd_errbound(self.h, ld, ld, _p(rho), _p(T), _p(Y), dC, dT,
+                                          2 if central else 1, _p(J), _p(E), nthreads)
+        if nf:
+            raise RuntimeError("finite differences failed")
+        return J, E * 2.0 ** -53
+
+    JAC_VARIANTS = {"exact": 0, "const_qss": 1, "zero_qss": 2}
+
+    def eval_variant(self, rho, T, Y, jac_variant="exact", t_column="analytic", nthreads=0):
+        """The Jacobian of a simplified construction (Section 3.3.1) and/or
+        with the finite-difference T column (Section 3.3.2), with running
+        error bounds: {"wdot", "Tdot", "jac", "jac_err"} (bounds absolute)."""
+        rho, T, Y, ld = self._state(rho, T, Y)
+        w = np.zeros((self.N, ld)); td = np.zeros(ld)
+        J = np.zeros((self.n * self.n, ld)); E = np.zeros_like(J)
+        nf = lib().oracle_eval_variant(self.h, ld, ld, _p(rho), _p(T), _p(Y),
+                                       self.JAC_VARIANTS[jac_variant], 1 if t_column == "fd" else 0,
+                                       _p(w), _p(td), _p(J), _p(E), nthreads)
+        if nf:
+            raise RuntimeError(f"oracle evaluation failed in {nf} cells")
+        return {"wdot": w, "Tdot": td, "jac": J, "jac_err": E * 2.0 ** -53}
+
+    def jac_cs_fixed_cq(self, rho, T, Y, cq, hrel=1e-30, nthreads=0):
+        """Complex-step Jacobian of (wdot, Tdot) with the QSS concentrations
+        held at the given values cq [Q][ld] (no QSS solve)."""
+        rho, T, Y, ld = self._state(rho, T, Y)
+        cq = _f64(cq if self.Q else np.zeros((1, ld)))
+        J = np.zeros((self.n * self.n, ld))
+        nf = lib().oracle_jac_cs_fixed_cq(self.h, ld, ld, _p(rho), _p(T), _p(Y), _p(cq), hrel, _p(J),
+                                          nthreads)
+        if nf:
+            raise RuntimeError("complex-step failed")
         return J
 
     def qss_residual(self, rho, T, Y, nthreads=0):

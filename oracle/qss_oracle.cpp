@@ -107,6 +107,9 @@ inline RE slog10(const RE& x) {
   double v = std::log10(x.v);
   return RE(v, x.e / (std::fabs(x.v) * 2.302585092994045684) + std::fabs(v));
 }
+inline double errof(double) { return 0.0; }
+inline double errof(const RE& x) { return x.e; }
+
 template <class S> S sq(const S& x) { return x * x; }
 template <class S> S ipow(const S& x, int n) {
   S r = S(1.0);
@@ -376,9 +379,18 @@ S side_product_deriv(const Side& s, int N, const std::vector<S>& C, int k) {
   return found ? p : S(0.0);
 }
 
+// Jacobian variants (Section 3.3.1): JV_EXACT is Eq. (JQSS) in full;
+// JV_CONST_QSS drops its second term (C_Q held at the solved values);
+// JV_ZERO_QSS drops it and sets C_Q = 0 inside the Jacobian.  t_fd replaces
+// the temperature column of the species rows by the central difference of
+// Section 3.3.2 with h = 2^(e-20), T in [2^e, 2^(e+1)).  The temperature row
+// is always the derivative of Tdot through the species rows in use.
+enum { JV_EXACT = 0, JV_CONST_QSS = 1, JV_ZERO_QSS = 2 };
+
 template <class S>
 bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool ordered_qss,
-               CellOut<S>& out) {
+               CellOut<S>& out, int jvar = JV_EXACT, bool t_fd = false,
+               const S* cq_given = nullptr) {
   const int N = m.N, Q = m.Q, n = N + 1;
   std::vector<S> C(phi, phi + N);
   S T = phi[N];
@@ -419,7 +431,10 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
     }
   }
   std::vector<S> CQ(Q, S(0.0));
-  if (ordered_qss) {
+  if (cq_given) {
+    // C_Q supplied by the caller: omega(C, T, C_Q) without the QSS solve
+    for (int q = 0; q < Q; ++q) CQ[q] = cq_given[q];
+  } else if (ordered_qss) {
     // resolution in the condensed order: singletons by division, groups by
     // Gaussian elimination with partial pivoting
     for (const auto& g : m.groups) {
@@ -485,8 +500,8 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
   std::vector<S> dQdCQ(m.M * (Q > 0 ? Q : 1), S(0.0));
   for (int j = 0; j < m.M; ++j) {
     const Reaction& r = m.rx[j];
-    S cl = r.qss_l >= 0 ? CQ[r.qss_l] : S(1.0);
-    S cr = r.qss_r >= 0 ? CQ[r.qss_r] : S(1.0);
+    S cl = r.qss_l >= 0 ? (jvar == JV_ZERO_QSS ? S(0.0) : CQ[r.qss_l]) : S(1.0);
+    S cr = r.qss_r >= 0 ? (jvar == JV_ZERO_QSS ? S(0.0) : CQ[r.qss_r]) : S(1.0);
     S kf = rk[j].kf, kb = rk[j].kb;
     S dkf_dT = rk[j].dkf_dT, dkb_dT = rk[j].dkb_dT;
     S Mfac = S(1.0);
@@ -505,8 +520,8 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
     if (r.qss_r >= 0) dQdCQ[j * Q + r.qss_r] = dQdCQ[j * Q + r.qss_r] - Mfac * kb * pb[j];
   }
   // R = d omega_Q / d phi |_{C_Q}  (Q x n);  A = d omega_Q / d C_Q
-  std::vector<S> X;
-  if (Q > 0) {
+  std::vector<S> X(Q * n, S(0.0));
+  if (Q > 0 && jvar == JV_EXACT) {
     std::vector<S> Rm(Q * n, S(0.0));
     for (int j = 0; j < m.M; ++j) {
       const Reaction& r = m.rx[j];
@@ -523,7 +538,6 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
     }
     // X = dC_Q/dphi = -A^{-1} R  (dense partial-pivot solve)
     std::vector<S> a2 = A;
-    X.assign(Q * n, S(0.0));
     for (int i = 0; i < Q * n; ++i) X[i] = -Rm[i];
     if (!gauss_solve(Q, a2, n, X)) return false;
   }
@@ -546,6 +560,20 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
         for (int c = 0; c < n; ++c) J[row * n + c] = J[row * n + c] + sgn * sd.nu[i] * dQ[c];
       }
     }
+  }
+  if (t_fd) {
+    // central difference in T of the full QSS evaluation
+    int e2 = 0;
+    std::frexp(re(T), &e2);                 // T = f 2^e2, f in [0.5, 1)
+    const double h = std::ldexp(1.0, e2 - 21);
+    std::vector<S> pp(phi, phi + n), pm(phi, phi + n);
+    pp[N] = pp[N] + h;
+    pm[N] = pm[N] - h;
+    CellOut<S> op, om;
+    if (!eval_cell(m, pp.data(), false, ordered_qss, op) ||
+        !eval_cell(m, pm.data(), false, ordered_qss, om))
+      return false;
+    for (int i = 0; i < N; ++i) J[i * n + N] = (op.wdot[i] - om.wdot[i]) / (2.0 * h);
   }
   // temperature row: Tdot = -T Su / Scv
   for (int c = 0; c < N; ++c) {
@@ -601,6 +629,45 @@ int eval_batch(const Mech* m, int64_t ncells, int64_t ld, const double* rho, con
     if (Tdot) Tdot[c] = re(o.Tdot);
     if (cq) for (int q = 0; q < m->Q; ++q) cq[q * ld + c] = re(o.CQ[q]);
     if (jac) for (int e = 0; e < n * n; ++e) jac[e * ld + c] = re(o.J[e]);
+  }
+  return nfail;
+}
+
+template <class S>
+int jac_fd_batch(const Mech* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                 const double* Y, double dC, double dT, int scheme, double* jac, double* jac_err,
+                 int nthreads) {
+  const int n = m->N + 1;
+  int nfail = 0;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads_or_default(nthreads)) reduction(+ : nfail)
+  for (int64_t c = 0; c < ncells; ++c) {
+    std::vector<S> phi;
+    cell_phi(*m, c, ld, rho, T, Y, phi);
+    CellOut<S> o0;
+    if (!eval_cell(*m, phi.data(), false, true, o0)) { nfail++; continue; }
+    for (int j = 0; j < n; ++j) {
+      double hj = (j < m->N) ? dC : dT;
+      std::vector<S> pp = phi, pm = phi;
+      pp[j] = pp[j] + hj;
+      pm[j] = pm[j] - hj;
+      CellOut<S> op, om;
+      bool ok = eval_cell(*m, pp.data(), false, true, op);
+      if (scheme == 2) ok = ok && eval_cell(*m, pm.data(), false, true, om);
+      if (!ok) { nfail++; break; }
+      for (int i = 0; i <= m->N; ++i) {
+        S fp = i < m->N ? op.wdot[i] : op.Tdot;
+        S f0 = i < m->N ? o0.wdot[i] : o0.Tdot;
+        S d;
+        if (scheme == 2) {
+          S fm = i < m->N ? om.wdot[i] : om.Tdot;
+          d = (fp - fm) / (2.0 * hj);
+        } else {
+          d = (fp - f0) / hj;
+        }
+        jac[(i * n + j) * ld + c] = re(d);
+        if (jac_err) jac_err[(i * n + j) * ld + c] = errof(d);
+      }
+    }
   }
   return nfail;
 }
@@ -785,39 +852,71 @@ int oracle_jac_complex_step(void* h, int64_t ncells, int64_t ld, const double* r
 }
 
 // Finite-difference Jacobian: central (scheme=2) or one-sided forward (scheme=1)
-// with absolute step dC for concentrations and dT for temperature.
+// with absolute step dC for concentrations and dT for temperature.  With
+// jac_err given, the evaluation runs in the running-error type and jac_err
+// receives the first-order rounding bound of each entry (units of u).
 int oracle_jac_fd(void* h, int64_t ncells, int64_t ld, const double* rho, const double* T,
                   const double* Y, double dC, double dT, int scheme, double* jac, int nthreads) {
+  return jac_fd_batch<double>((Mech*)h, ncells, ld, rho, T, Y, dC, dT, scheme, jac, nullptr,
+                              nthreads);
+}
+
+int oracle_jac_fd_errbound(void* h, int64_t ncells, int64_t ld, const double* rho,
+                           const double* T, const double* Y, double dC, double dT, int scheme,
+                           double* jac, double* jac_err, int nthreads) {
+  return jac_fd_batch<RE>((Mech*)h, ncells, ld, rho, T, Y, dC, dT, scheme, jac, jac_err, nthreads);
+}
+
+// A Jacobian variant (jvar: 0 exact, 1 constant-QSS, 2 zero-QSS; t_fd: FD
+// temperature column), evaluated in the running-error type: values in jac and
+// first-order rounding bounds in jac_err (units of u; may be NULL).  wdot and
+// Tdot are the exact source term in every variant.
+int oracle_eval_variant(void* h, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                        const double* Y, int jvar, int t_fd, double* wdot, double* Tdot,
+                        double* jac, double* jac_err, int nthreads) {
+  Mech* m = (Mech*)h;
+  const int n = m->N + 1;
+  if (jvar < JV_EXACT || jvar > JV_ZERO_QSS) return -1;
+  int nfail = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads_or_default(nthreads)) reduction(+ : nfail)
+  for (int64_t c = 0; c < ncells; ++c) {
+    std::vector<RE> phi;
+    cell_phi(*m, c, ld, rho, T, Y, phi);
+    CellOut<RE> o;
+    if (!eval_cell(*m, phi.data(), true, true, o, jvar, t_fd != 0)) { nfail++; continue; }
+    if (wdot) for (int k = 0; k < m->N; ++k) wdot[k * ld + c] = o.wdot[k].v;
+    if (Tdot) Tdot[c] = o.Tdot.v;
+    for (int e = 0; e < n * n; ++e) {
+      jac[e * ld + c] = o.J[e].v;
+      if (jac_err) jac_err[e * ld + c] = o.J[e].e;
+    }
+  }
+  return nfail;
+}
+
+// Complex-step Jacobian of f = (wdot, Tdot) at FIXED QSS concentrations
+// cq[q * ld + c] (no QSS solve): d f(phi; C_Q) / d phi, the definition of the
+// constant-QSS (C_Q = solved values) and zero-QSS (C_Q = 0) Jacobians.
+int oracle_jac_cs_fixed_cq(void* h, int64_t ncells, int64_t ld, const double* rho,
+                           const double* T, const double* Y, const double* cq, double hrel,
+                           double* jac, int nthreads) {
   Mech* m = (Mech*)h;
   const int n = m->N + 1;
   int nfail = 0;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads_or_default(nthreads)) reduction(+ : nfail)
   for (int64_t c = 0; c < ncells; ++c) {
-    std::vector<double> phi;
+    std::vector<cplx> phi;
     cell_phi(*m, c, ld, rho, T, Y, phi);
-    CellOut<double> o0;
-    if (!eval_cell(*m, phi.data(), false, true, o0)) { nfail++; continue; }
+    std::vector<cplx> q(m->Q > 0 ? m->Q : 1);
+    for (int k = 0; k < m->Q; ++k) q[k] = cplx(cq[k * ld + c], 0.0);
     for (int j = 0; j < n; ++j) {
-      double hj = (j < m->N) ? dC : dT;
-      std::vector<double> pp = phi, pm = phi;
-      pp[j] += hj;
-      pm[j] -= hj;
-      CellOut<double> op, om;
-      bool ok = eval_cell(*m, pp.data(), false, true, op);
-      if (scheme == 2) ok = ok && eval_cell(*m, pm.data(), false, true, om);
-      if (!ok) { nfail++; break; }
-      for (int i = 0; i <= m->N; ++i) {
-        double fp = i < m->N ? op.wdot[i] : op.Tdot;
-        double f0 = i < m->N ? o0.wdot[i] : o0.Tdot;
-        double d;
-        if (scheme == 2) {
-          double fm = i < m->N ? om.wdot[i] : om.Tdot;
-          d = (fp - fm) / (2.0 * hj);
-        } else {
-          d = (fp - f0) / hj;
-        }
-        jac[(i * n + j) * ld + c] = d;
-      }
+      double hj = hrel * std::max(std::fabs(phi[j].real()), 1.0);
+      std::vector<cplx> p = phi;
+      p[j] = cplx(p[j].real(), hj);
+      CellOut<cplx> o;
+      if (!eval_cell(*m, p.data(), false, true, o, JV_EXACT, false, q.data())) { nfail++; break; }
+      for (int i = 0; i < m->N; ++i) jac[(i * n + j) * ld + c] = o.wdot[i].imag() / hj;
+      jac[(m->N * n + j) * ld + c] = o.Tdot.imag() / hj;
     }
   }
   return nfail;

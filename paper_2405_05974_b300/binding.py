@@ -71,6 +71,8 @@ def lib():
                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                      _vp, _vp]
         L.qss_jacobian_host.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]
         L.qss_implicit_step.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
                                         ctypes.POINTER(NewtonOpts), _vp, _vp, _vp]
@@ -192,6 +194,14 @@ class Mechanism:
         check(lib().qss_jacobian(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
                                  _ptr(Tdot), _stream(stream)))
         return jac, wdot, Tdot
+
+    def jacobian_fd(self, rho, T, Y, dC, dT, jac=None, ncells=None, stream=None):
+        """Central finite-difference Jacobian (absolute steps dC, dT)."""
+        nc, ld = self._check_state(rho, T, Y, ncells)
+        jac = self._out(jac, (self.n * self.n, ld), T)
+        check(lib().qss_jacobian_fd(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), float(dC), float(dT),
+                                    _ptr(jac), _stream(stream)))
+        return jac
 
     def jacobian_host(self, rho, T, Y, jac=None, wdot=None, Tdot=None, chunk=0):
         """Host (CPU, ideally pinned) float64 tensors; synchronous."""

@@ -12,9 +12,10 @@ struct qss_mech_s {
   int device = 0;
   CUdevice dev = 0;
   CUcontext ctx = nullptr;
-  CUmodule mod = nullptr;          // mech.cubin: wdot and Jacobian kernels
+  CUmodule mod = nullptr;          // jac.cubin: analytic Jacobian kernel
+  CUmodule mod_wdot = nullptr;     // wdot.cubin: source term, FD Jacobian
   CUmodule mod_newton = nullptr;   // newton.cubin: implicit-step kernels
-  CUfunction f_wdot = nullptr, f_jac = nullptr;
+  CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   int upd_threads[2] = {128, 128};   // block size of the update kernels (their launch bound)

@@ -1,0 +1,43 @@
+// The analytic Jacobian kernel around a generated mechanism body (one thread
+// per cell; the layout is in qss_cells.cuh).  It has a translation unit and a
+// cubin of its own: the generated Jacobian is by far the longest compile, and
+// it is redone only when this file or the mechanism changes.
+#pragma once
+
+#include "qss_cells.cuh"
+
+// Blocks per SM the register allocation must allow for the Jacobian kernel
+// (1: up to 255 registers; 2: <= 255 at 128 threads; 3: <= 168; 4: <= 128).
+// Chosen per mechanism by the autotuner from timed variants.
+#ifndef QSS_MINBLOCKS
+#define QSS_MINBLOCKS 1
+#endif
+
+// f = (wdot, Tdot) and J.  State from (rho, T, Y) or, in list mode (phi and
+// list given), of the t-th cell of the list: s = list[t] for t < *nact, state
+// phi[k * ld + s] = (C_1..C_N, T), outputs written at column t.  In list mode
+// thread 0 also clears *nact_next, the counter the following Newton update
+// fills.
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
+qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
+               const double* __restrict__ T, const double* __restrict__ Y,
+               double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot,
+               const double* __restrict__ phi, const int* __restrict__ list,
+               const int* __restrict__ nact, int* __restrict__ nact_next) {
+  const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  double C[QSS_N];
+  double Tc;
+  if (phi) {
+    if (c == 0) *nact_next = 0;
+    if (c >= *nact) return;
+    const long long s = list[c];
+#pragma unroll
+    for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
+    Tc = phi[QSS_N * ld + s];
+  } else {
+    if (c >= ncells) return;
+    qss_unpack(c, ld, rho, Y, C);
+    Tc = __ldg(T + c);
+  }
+  qss_eval_jac(C, Tc, wdot ? wdot + c : nullptr, Tdot ? Tdot + c : nullptr, jac + c, ld, ld);
+}

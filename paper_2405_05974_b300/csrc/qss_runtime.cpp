@@ -16,6 +16,7 @@
 #include <fstream>
 #include <mutex>
 #include <sstream>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -109,21 +110,29 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   int rc = ctx_for_device(device, &m->dev, &m->ctx);
   if (rc) { delete m; return rc; }
   m->device = device;
-  CUresult r = drv().cuModuleLoad(&m->mod, (dir + "/mech.cubin").c_str());
-  if (r != CUDA_SUCCESS) {
-    drv().cuDevicePrimaryCtxRelease(m->dev);
-    delete m;
-    return cu_fail(r, "drv().cuModuleLoad(mech.cubin)");
-  }
-  const char* need[] = {"qss_wdot_kernel", "qss_jac_kernel"};
-  CUfunction* slot[] = {&m->f_wdot, &m->f_jac};
-  for (int i = 0; i < 2; ++i) {
-    r = drv().cuModuleGetFunction(slot[i], m->mod, need[i]);
+  // required kernels: the analytic Jacobian (jac.cubin) and the source term
+  // with the finite-difference Jacobian (wdot.cubin)
+  struct Need { CUmodule* mod; const char* file; const char* fn; CUfunction* slot; };
+  const Need need[] = {{&m->mod, "jac.cubin", "qss_jac_kernel", &m->f_jac},
+                       {&m->mod_wdot, "wdot.cubin", "qss_wdot_kernel", &m->f_wdot},
+                       {&m->mod_wdot, "wdot.cubin", "qss_jac_fd_kernel", &m->f_jac_fd}};
+  for (const Need& nd : need) {
+    CUresult r = CUDA_SUCCESS;
+    if (!*nd.mod) r = drv().cuModuleLoad(nd.mod, (dir + "/" + nd.file).c_str());
+    int code = 0;
+    std::string msg;
     if (r != CUDA_SUCCESS) {
-      drv().cuModuleUnload(m->mod);
+      code = cu_fail(r, (std::string("drv().cuModuleLoad(") + nd.file + ")").c_str());
+      *nd.mod = nullptr;
+    } else if (drv().cuModuleGetFunction(nd.slot, *nd.mod, nd.fn) != CUDA_SUCCESS) {
+      code = fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + nd.fn);
+    }
+    if (code) {
+      if (m->mod) drv().cuModuleUnload(m->mod);
+      if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
       drv().cuDevicePrimaryCtxRelease(m->dev);
       delete m;
-      return fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + need[i]);
+      return code;
     }
   }
   // optional kernels (implicit step), in newton.cubin
@@ -155,6 +164,7 @@ void qss_mech_free(qss_mech_t m) {
   }
   if (m->newton_scratch) drv().cuMemFree(m->newton_scratch);
   if (m->mod) drv().cuModuleUnload(m->mod);
+  if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
   if (m->mod_newton) drv().cuModuleUnload(m->mod_newton);
   drv().cuDevicePrimaryCtxRelease(m->dev);
   delete m;
@@ -200,6 +210,20 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   int* none = nullptr;
   void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &list, &none};
   return launch_cells(m, m->f_jac, ncells, m->block, args, (CUstream)stream, 0);
+}
+
+int qss_jacobian_fd(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho,
+                    const double* T, const double* Y, double dC, double dT, double* jac,
+                    void* stream) {
+  int rc = check_cells(m, ncells, ld);
+  if (rc) return rc;
+  if (!(dC > 0.0) || !(dT > 0.0) || !std::isfinite(dC) || !std::isfinite(dT))
+    return fail(QSS_ERR_INVALID_ARG, "finite-difference steps must be finite and > 0");
+  if (ncells == 0) return QSS_OK;
+  if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
+  long long nc = ncells, l = ld;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &dC, &dT, &jac};
+  return launch_cells(m, m->f_jac_fd, ncells, m->block, args, (CUstream)stream, 0);
 }
 
 static int copy2d(void* dst, bool dst_host, size_t dpitch, const void* src, bool src_host,

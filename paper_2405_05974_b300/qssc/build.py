@@ -2,14 +2,17 @@
 
     build_mechanism(mech_dict) -> artefact directory
 
-The directory holds ``mech_body.inc`` (the generated code), ``mech.cubin``
-(sm_103a: device math, the generated body and the wdot/Jacobian kernels),
-``newton.cubin`` (the implicit-step kernels, which need only the mechanism's
-sizes and molar masses), ``meta.txt`` (read by the C runtime) and
-``meta.json`` (op counts, registers, spills).  Artefact directories are keyed
-by the mechanism, the generator and the templates; each cubin is also cached
-by the hash of its source, headers and flags under ``build/cubins``, so a
-change to the Newton kernels does not recompile the generated body.
+The directory holds the generated code (``mech_sizes.inc``: sizes and
+constants; ``mech_wdot.inc``: the source term; ``mech_jac.inc``: the
+Jacobian), three sm_103a cubins compiled in parallel from three translation
+units -- ``jac.cubin`` (the analytic Jacobian kernel), ``wdot.cubin`` (the
+source-term and finite-difference Jacobian kernels) and ``newton.cubin`` (the
+implicit-step kernels, which need only the sizes and molar masses) --
+``meta.txt`` (read by the C runtime) and ``meta.json`` (op counts, registers,
+spills).  Artefact directories are keyed by the mechanism, the generator, the
+options and the templates; each cubin is also cached by the hash of its
+source, headers and flags under ``build/cubins``, so a change to one kernel
+template does not recompile the others' generated code.
 """
 from __future__ import annotations
 
@@ -19,7 +22,9 @@ import os
 import re
 import shutil
 import subprocess
+import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 from . import emit, mech as qmech, model as qmodel
 
@@ -29,7 +34,9 @@ REPO = os.path.dirname(PKG)
 DEFAULT_ROOT = os.path.join(REPO, "build", "mech")
 NVCC = os.environ.get("QSS_NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_kernels.cuh", "qss_newton.cuh"]
+TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_cells.cuh", "qss_jac_kernel.cuh",
+             "qss_wdot_kernels.cuh", "qss_newton.cuh"]
+ARTEFACT_FILES = ("jac.cubin", "wdot.cubin", "newton.cubin", "meta.txt", "meta.json")
 COMPILER_VERSION = "1"
 
 
@@ -68,7 +75,8 @@ def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: s
     cached_log = os.path.join(CUBIN_CACHE, key + ".log")
     if not os.path.exists(cached):
         os.makedirs(CUBIN_CACHE, exist_ok=True)
-        work = cached + ".d%d" % os.getpid()
+        tag = "%d_%d" % (os.getpid(), threading.get_ident())
+        work = cached + ".d" + tag
         os.makedirs(work, exist_ok=True)
         for name, text in headers.items():
             if not os.path.exists(os.path.join(CSRC, name)):
@@ -77,7 +85,7 @@ def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: s
         with open(os.path.join(work, "tu.cu"), "w") as f:
             f.write(tu_src)
         cmd = [NVCC, "-cubin", *ARCH, "-O3", "-lineinfo", "-Xptxas", "-v", *flags, "-I", CSRC,
-               "-I", work, "-o", cached + ".tmp", os.path.join(work, "tu.cu")]
+               "-I", work, "-o", cached + ".tmp" + tag, os.path.join(work, "tu.cu")]
         p = subprocess.run(cmd, capture_output=True, text=True)
         log = " ".join(cmd) + "\n" + p.stdout + p.stderr
         shutil.rmtree(work, ignore_errors=True)
@@ -85,47 +93,72 @@ def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: s
             raise RuntimeError(f"nvcc failed:\n{log[-4000:]}")
         with open(cached_log, "w") as f:
             f.write(log)
-        os.replace(cached + ".tmp", cached)
+        os.replace(cached + ".tmp" + tag, cached)
     shutil.copyfile(cached, out_path)
     shutil.copyfile(cached_log, log_path)
     return open(log_path).read()
 
 
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
-                    force: bool = False, verbose: bool = False) -> str:
-    key = artefact_key(mech, block, defines)
+                    force: bool = False, verbose: bool = False, jac_variant: str = "exact",
+                    t_column: str = "analytic") -> str:
+    """Generate, compile and cache the artefact of one mechanism.
+
+    ``jac_variant`` / ``t_column`` select the Jacobian that qss_jac_kernel
+    computes (``model.build_model``); ``defines`` are extra preprocessor
+    definitions of the kernel templates (e.g. ``QSS_MINBLOCKS=2``)."""
+    variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
+    key = artefact_key(mech, block, tuple(defines) + variant)
     out = os.path.join(root, f"{mech.get('name', 'mech')}_{key}")
-    if not force and os.path.exists(os.path.join(out, "mech.cubin")) and \
-            os.path.exists(os.path.join(out, "meta.txt")):
+    if not force and all(os.path.exists(os.path.join(out, f)) for f in ARTEFACT_FILES):
         return out
     t0 = time.time()
     ir = qmech.parse(mech)
-    model = qmodel.build_model(ir)
+    model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
     src, meta = emit.emit_mechanism_source(model)
     tmp = out + ".tmp%d" % os.getpid()
     os.makedirs(tmp, exist_ok=True)
-    with open(os.path.join(tmp, "mech_body.inc"), "w") as f:
-        f.write(src)
-    # sizes and constants only (for the Newton kernels' translation unit)
-    sizes = src[:src.index("__device__ __forceinline__ void qss_eval_wdot")]
-    hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES if os.path.exists(os.path.join(CSRC, t))}
+    # sizes and constants / the source term / the Jacobian, one file each
+    iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
+    ij = src.index("__device__ __forceinline__ void qss_eval_jac")
+    parts = {"mech_sizes.inc": src[:iw], "mech_wdot.inc": src[iw:ij], "mech_jac.inc": src[ij:]}
+    for name, text in parts.items():
+        with open(os.path.join(tmp, name), "w") as f:
+            f.write(text)
+    hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES}
     flags = [f"-DQSS_BLOCK={block}", *[f"-D{d}" for d in defines]]
     t1 = time.time()
-    tu_mech = '#include "qss_device.cuh"\n#include "mech_body.inc"\n#include "qss_kernels.cuh"\n'
     common = {k: hdr[k] for k in ("qss_device.cuh", "qss_exp_table.inc")}
-    log = _compile_cubin(tu_mech, {**common, "qss_kernels.cuh": hdr["qss_kernels.cuh"], "mech_body.inc": src},
-                         flags, os.path.join(tmp, "mech.cubin"), os.path.join(tmp, "build.log"))
-    t2 = time.time()
-    tu_newton = '#include "qss_device.cuh"\n#include "mech_sizes.inc"\n#include "qss_newton.cuh"\n'
-    log_n = _compile_cubin(tu_newton, {**common, "qss_newton.cuh": hdr["qss_newton.cuh"],
-                                       "mech_sizes.inc": sizes}, flags,
-                           os.path.join(tmp, "newton.cubin"), os.path.join(tmp, "build_newton.log"))
-    meta["kernels"] = {**_parse_ptxas(log), **_parse_ptxas(log_n)}
+    cells = {"qss_cells.cuh": hdr["qss_cells.cuh"], "mech_sizes.inc": parts["mech_sizes.inc"]}
+    pre = '#include "qss_device.cuh"\n#include "mech_sizes.inc"\n'
+    units = {
+        "jac": (pre + '#include "mech_jac.inc"\n#include "qss_jac_kernel.cuh"\n',
+                {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"],
+                 "qss_jac_kernel.cuh": hdr["qss_jac_kernel.cuh"]}),
+        "wdot": (pre + '#include "mech_wdot.inc"\n#include "qss_wdot_kernels.cuh"\n',
+                 {**common, **cells, "mech_wdot.inc": parts["mech_wdot.inc"],
+                  "qss_wdot_kernels.cuh": hdr["qss_wdot_kernels.cuh"]}),
+        "newton": (pre + '#include "qss_newton.cuh"\n',
+                   {**common, "mech_sizes.inc": parts["mech_sizes.inc"],
+                    "qss_newton.cuh": hdr["qss_newton.cuh"]}),
+    }
+    logs, secs = {}, {}
+
+    def compile_unit(name):
+        t = time.time()
+        tu, headers = units[name]
+        logs[name] = _compile_cubin(tu, headers, flags, os.path.join(tmp, f"{name}.cubin"),
+                                    os.path.join(tmp, f"build_{name}.log"))
+        secs[name] = round(time.time() - t, 3)
+
+    with ThreadPoolExecutor(len(units)) as ex:
+        for f in [ex.submit(compile_unit, u) for u in units]:
+            f.result()
+    meta["kernels"] = {k: v for name in units for k, v in _parse_ptxas(logs[name]).items()}
     meta["block"] = block
     meta["defines"] = list(defines)
     meta["codegen_s"] = round(t1 - t0, 3)
-    meta["nvcc_s"] = round(t2 - t1, 3)
-    meta["nvcc_newton_s"] = round(time.time() - t2, 3)
+    meta["nvcc_s"] = secs
     meta["artefact_key"] = key
     with open(os.path.join(tmp, "meta.json"), "w") as f:
         json.dump(meta, f, indent=1)
@@ -138,8 +171,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         shutil.rmtree(out)
     os.replace(tmp, out)
     if verbose:
-        print(f"built {out}: codegen {meta['codegen_s']}s nvcc {meta['nvcc_s']}s + {meta['nvcc_newton_s']}s "
-              f"{meta['kernels']}")
+        print(f"built {out}: codegen {meta['codegen_s']}s nvcc {secs} {meta['kernels']}")
     return out
 
 

@@ -225,6 +225,15 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
     g = model.g
     inputs = {model.C[k]: f"C{k}" for k in range(N)}
     inputs[model.T] = "T"
+    fd_prologue = []
+    if model.fd_vars is not None:
+        for v, name in zip(model.fd_vars, ("Tp", "Tm", "inv2h")):
+            inputs[v] = name
+        # h = 2^(e - 20) for T in [2^e, 2^(e+1)): T +- h and 1/(2h) are exact
+        fd_prologue = [
+            "  const double qss_p2 = __longlong_as_double(__double_as_longlong(T) & 0x7ff0000000000000LL);",
+            "  const double qss_h = qss_p2 * 0x1p-20;",
+            "  const double Tp = T + qss_h, Tm = T - qss_h, inv2h = 0x1p19 / qss_p2;"]
     em = Emitter(model, inputs)
     out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
     out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
@@ -257,10 +266,11 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
         "__device__ __forceinline__ void qss_eval_jac(const double* __restrict__ C, const double T,",
         "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
         "    const long long wstride, const long long jstride) {",
-        *unpack, *body_j, "}", ""])
+        *unpack, *fd_prologue, *body_j, "}", ""])
     meta = {
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
+        "jac_variant": model.jac_variant, "t_column": model.t_column,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
         "fp64_instr_wdot": fp64_instructions(cnt_w), "fp64_instr_jac": fp64_instructions(cnt_j),

@@ -285,7 +285,9 @@ class Graph:
         elif op == LOG:
             r = self.log(s(a[0]))
         elif op == SELECT:
-            r = self.select(a[0], s(a[1]), s(a[2]))
+            cx, cc = self.args[a[0]]
+            cond = self.lt(s(cx), cc) if self.deps[cx] & mask else a[0]
+            r = self.select(cond, s(a[1]), s(a[2]))
         elif op == FACT:
             r = self.fact(s(a[0]), s(a[1]))
         else:

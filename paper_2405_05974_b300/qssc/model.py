@@ -19,6 +19,8 @@ Builds, on one hash-consed DAG (``expr.Graph``):
   dependence on C enters as one more chain-rule level (d[M]_j/dC_k is the
   collision efficiency), which keeps the dense third-body contributions to a
   rank-one update per row;
+* the simplified Jacobians of Section 3.3.1 (constant-QSS and zero-QSS) and
+  the finite-difference temperature column of Section 3.3.2 as build options;
 * the temperature row from Tdot = -T sum_k (h_k/RT - 1) w_k / sum_k C_k (c_p,k/R - 1)
   (constant volume), differentiated with the production rates as
   placeholders and closed with the rows of J.
@@ -55,10 +57,21 @@ class Model:
     cq_value: List[int]
     stats: dict = field(default_factory=dict)
     parts: dict = field(default_factory=dict)
+    fd_vars: tuple = None           # (T + h, T - h, 1/(2h)) inputs of the FD T column
+    jac_variant: str = "exact"
+    t_column: str = "analytic"
+
+
+JAC_VARIANTS = ("exact", "const_qss", "zero_qss")
+T_COLUMNS = ("analytic", "fd")
 
 
 class _Builder:
-    def __init__(self, ir: MechIR):
+    def __init__(self, ir: MechIR, jac_variant="exact", t_column="analytic"):
+        if jac_variant not in JAC_VARIANTS or t_column not in T_COLUMNS:
+            raise ValueError(f"unknown Jacobian variant {jac_variant!r} / T column {t_column!r}")
+        self.jac_variant = jac_variant
+        self.t_column = t_column
         self.ir = ir
         g = self.g = Graph()
         N, Q = ir.N, ir.Q
@@ -308,13 +321,30 @@ class _Builder:
                     X[m][c] = sol[m]
         P = [[g.d(omega[i], self.CQ[m]) for m in range(Q)] for i in range(N)]
         J = [[None] * n for _ in range(n)]
+        zero_q = {v: g.ZERO for v in self.CQ}
         for i in range(N):
             for c in range(n):
                 acc = Gm[i][c]
-                for m in range(Q):
-                    if P[i][m] != g.ZERO and X[m][c] != g.ZERO:
-                        acc = g.add(acc, g.mul(P[i][m], X[m][c]))
+                if self.jac_variant == "exact":
+                    for m in range(Q):
+                        if P[i][m] != g.ZERO and X[m][c] != g.ZERO:
+                            acc = g.add(acc, g.mul(P[i][m], X[m][c]))
+                elif self.jac_variant == "zero_qss" and Q:
+                    acc = g.subs(acc, zero_q)
                 J[i][c] = acc
+        fd_vars = None
+        if self.t_column == "fd":
+            # Section 3.3.2: dw/dT by a central difference of the production
+            # rates at T + h and T - h (h an exact power of two, so that both
+            # shifted temperatures and 1/(2h) are exact); the full QSS
+            # evaluation, C_Q included, is repeated at each temperature.
+            fd_vars = (g.var("Tp"), g.var("Tm"), g.var("inv2h"))
+            cq_full = {self.CQ[m]: cqv[m] for m in range(Q)}
+            for i in range(N):
+                full = g.subs(omega[i], cq_full) if Q else omega[i]
+                up = g.subs(full, {self.T: fd_vars[0]})
+                dn = g.subs(full, {self.T: fd_vars[1]})
+                J[i][N] = g.mul(g.sub(up, dn), fd_vars[2])
         # ---- temperature equation and row ------------------------------------
         Wv = [g.var(f"W{i}") for i in range(N)]
         Su = g.sum([g.mul(g.sub(self.thermo(k, "hRT"), g.ONE), Wv[k]) for k in range(N)])
@@ -330,7 +360,8 @@ class _Builder:
                     acc = g.add(acc, g.mul(dW, J[i][c]))
             J[N][c] = acc
         model = Model(ir=ir, g=g, C=self.C, T=self.T, wdot=omega[:N], Tdot=Tdot_ph, jac=J,
-                      bind=self.bind, groups=groups, cq_value=cqv)
+                      bind=self.bind, groups=groups, cq_value=cqv, fd_vars=fd_vars,
+                      jac_variant=self.jac_variant, t_column=self.t_column)
         model.parts = {"G": Gm, "X": X, "P": P, "A": A}
         model.stats = {"nodes": len(g.op), "n_third_body_tables": len(Mkeys),
                        "groups": [len(c) for c in groups]}
@@ -376,5 +407,12 @@ class _Builder:
         return {comp[i]: x[i] for i in range(s)}, fac
 
 
-def build_model(ir: MechIR) -> Model:
-    return _Builder(ir).build()
+def build_model(ir: MechIR, jac_variant: str = "exact", t_column: str = "analytic") -> Model:
+    """``jac_variant``: "exact" (Eq. JQSS with the chain rule through C_Q),
+    "const_qss" (the second term of Eq. JQSS dropped: C_Q held at its solved
+    value) or "zero_qss" (that term dropped and C_Q set to zero inside the
+    Jacobian), Section 3.3.1.  ``t_column``: "analytic" or "fd" (central
+    difference in T, Section 3.3.2).  The temperature row always follows from
+    the species rows by the chain rule; wdot and Tdot are exact in every
+    variant."""
+    return _Builder(ir, jac_variant, t_column).build()

@@ -105,8 +105,44 @@ def test_compiler_rejects_quadratic_qss_coupling():
 
 def test_artefact_build_tiny():
     art = qbuild.build_mechanism(workloads.mechanism("tiny"))
-    assert os.path.exists(os.path.join(art, "mech.cubin"))
+    for f in ("jac.cubin", "wdot.cubin", "newton.cubin", "meta.txt", "meta.json"):
+        assert os.path.exists(os.path.join(art, f)), f
     meta = qbuild.load_meta(art)
     assert meta["N"] == 9 and meta["Q"] == 3 and meta["M"] == 30
     assert meta["flops_jac"] > meta["flops_wdot"] > 0
     assert "qss_jac_kernel" in meta["kernels"]
+
+
+@pytest.mark.parametrize("variant,tcol", [("const_qss", "analytic"), ("zero_qss", "analytic"), ("exact", "fd")])
+def test_jacobian_variant_models_match_oracle_on_cpu(variant, tcol):
+    """The compiler's symbolic variant models, evaluated on the CPU by the DAG
+    interpreter, agree with the oracle's implementation of the same variant
+    (the FD temperature column uses the compiler's exact power-of-two step)."""
+    import math
+    import numpy as np
+    import oracle
+    from paper_2405_05974_b300 import mechgen
+    from paper_2405_05974_b300.qssc import model as qmodel
+
+    m = workloads.mechanism("tiny")
+    ir = qmech.parse(m)
+    mod = qmodel.build_model(ir, jac_variant=variant, t_column=tcol)
+    om = oracle.OracleMech(m)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["tiny"], 3)
+    ref = om.eval_variant(rho, T, Y, variant, tcol)
+    C = om.conc(rho, Y)
+    n = ir.N + 1
+    for c in range(3):
+        env = {mod.C[k]: float(C[k, c]) for k in range(ir.N)}
+        env[mod.T] = float(T[c])
+        if mod.fd_vars is not None:
+            _, e = math.frexp(T[c])
+            h = math.ldexp(1.0, e - 21)
+            env[mod.fd_vars[0]] = T[c] + h
+            env[mod.fd_vars[1]] = T[c] - h
+            env[mod.fd_vars[2]] = 0.5 / h
+        outs = [mod.jac[i][j] for i in range(n) for j in range(n)]
+        got = np.array(mod.g.evaluate(outs, env, fns=mod.bind))
+        want = ref["jac"][:, c]
+        tol = 1e-9 * np.abs(want) + 1e-20 + 64 * ref["jac_err"][:, c]
+        assert np.all(np.abs(got - want) <= tol), np.argwhere(np.abs(got - want) > tol)[:5]

@@ -316,6 +316,95 @@ def test_running_error_bound_holds(key, n):
     assert np.all(np.abs(o["Tdot"] - q["Tdot"]) <= eb["Tdot"] + 1e-300)
 
 
+# ---------------------------------------------------------------------------
+# Simplified Jacobians (Section 3.3.1) and the FD temperature column (3.3.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("key,n", [("tiny", 64), ("hydrocarbon", 16)])
+def test_constant_qss_jacobian_is_derivative_at_fixed_cq(key, n):
+    """The constant-QSS Jacobian is d f(phi; C_Q) / d phi with C_Q held at its
+    solved values: the complex step through the explicit rate expressions with
+    C_Q frozen (no QSS solve) must agree with the hand-written partials, every
+    row including that of T."""
+    m, (rho, T, Y) = _states(key, n)
+    om = oracle.OracleMech(m)
+    cq = om.eval(rho, T, Y, jac=False, cq=True)["cq"]
+    v = om.eval_variant(rho, T, Y, "const_qss")
+    Jcs = om.jac_cs_fixed_cq(rho, T, Y, cq)
+    ok = np.abs(v["jac"] - Jcs) <= 1e-12 * np.abs(Jcs) + 2.0 * v["jac_err"] + 1e-300
+    assert ok.all(), np.argwhere(~ok)[:5]
+    # and it is not the exact Jacobian (the dropped term is not zero)
+    Jex = om.eval(rho, T, Y)["jac"]
+    assert np.abs(v["jac"] - Jex).max() > 1e-6 * np.abs(Jex).max()
+
+
+@pytest.mark.parametrize("key,n", [("tiny", 64), ("hydrocarbon", 16)])
+def test_zero_qss_jacobian_species_rows(key, n):
+    """The zero-QSS Jacobian's species rows are d omega(phi; C_Q = 0) / d phi
+    (complex step with the QSS concentrations frozen at zero); its source term
+    stays the exact one."""
+    m, (rho, T, Y) = _states(key, n)
+    om = oracle.OracleMech(m)
+    v = om.eval_variant(rho, T, Y, "zero_qss")
+    Jcs = om.jac_cs_fixed_cq(rho, T, Y, np.zeros((om.Q, T.shape[0])))
+    N, nn = om.N, om.n
+    a = v["jac"].reshape(nn, nn, -1)[:N]
+    b = Jcs.reshape(nn, nn, -1)[:N]
+    e = v["jac_err"].reshape(nn, nn, -1)[:N]
+    ok = np.abs(a - b) <= 1e-12 * np.abs(b) + 2.0 * e + 1e-300
+    assert ok.all(), np.argwhere(~ok)[:5]
+    ref = om.eval(rho, T, Y, jac=False)
+    assert np.array_equal(v["wdot"], ref["wdot"]) and np.array_equal(v["Tdot"], ref["Tdot"])
+
+
+def test_variants_coincide_without_qss_species():
+    """With no QSS species the second term of Eq. JQSS is absent: all three
+    constructions give the same Jacobian, bit for bit."""
+    na = [3.5, 1e-4, 0, 0, 0, -1000.0, 2.0]
+    nb = [3.2, -2e-4, 0, 0, 0, 500.0, 1.0]
+    m = _ab_mech(2.0e8, 0.5, 30000.0, na, nb)
+    om = oracle.OracleMech(m)
+    rho, T, Y = state_from_C(m, [[1.5, 0.2], [0.25, 0.9], [1.0, 1.0]], [1300.0, 1700.0])
+    Js = [om.eval_variant(rho, T, Y, v)["jac"] for v in ("exact", "const_qss", "zero_qss")]
+    assert np.array_equal(Js[0], Js[1]) and np.array_equal(Js[0], Js[2])
+    assert np.array_equal(Js[0], om.eval(rho, T, Y)["jac"])
+
+
+@pytest.mark.parametrize("key,n", [("tiny", 64), ("hydrocarbon", 16)])
+def test_fd_temperature_column(key, n):
+    """Section 3.3.2 reading: the species rows' T column by a central
+    difference with h = 2^(e-20) (T in [2^e, 2^(e+1))).  It agrees with the
+    complex-step T column to the difference's truncation and rounding error;
+    the concentration columns are those of the analytic Jacobian."""
+    m, (rho, T, Y) = _states(key, n)
+    om = oracle.OracleMech(m)
+    v = om.eval_variant(rho, T, Y, "exact", "fd")
+    J = om.eval(rho, T, Y)["jac"]
+    Jcs = om.jac_complex_step(rho, T, Y)
+    N, nn = om.N, om.n
+    a, b, c = (x.reshape(nn, nn, -1) for x in (v["jac"], J, Jcs))
+    e = v["jac_err"].reshape(nn, nn, -1)
+    assert np.array_equal(a[:N, :N], b[:N, :N])
+    d = np.abs(a[:, N] - c[:, N])
+    ok = d <= 1e-7 * np.abs(c[:, N]) + 4.0 * e[:, N] + 1e-300
+    assert ok.all(), (np.argwhere(~ok)[:5], d.max())
+    # the step is small: the FD column is far closer than a 1 % step would be
+    assert np.median(d / (np.abs(c[:, N]) + 1e-300)) < 1e-8
+
+
+def test_fd_errbound_values_match_plain_fd():
+    """The running-error FD performs the same FP64 operations as the plain
+    one (identical values); its bounds are finite and nonnegative.  (The
+    running-error type itself is pinned against binary128 in
+    test_running_error_bound_holds.)"""
+    m, (rho, T, Y) = _states("tiny", 32)
+    om = oracle.OracleMech(m)
+    J = om.jac_fd(rho, T, Y, dC=1e-4, dT=1e-4)
+    Jb, E = om.jac_fd_errbound(rho, T, Y, dC=1e-4, dT=1e-4)
+    assert np.array_equal(J, Jb)
+    assert np.all(E >= 0) and np.all(np.isfinite(E))
+
+
 def test_jacobian_central_fd_second_order():
     m, (rho, T, Y) = _states("tiny", 16)
     om = oracle.OracleMech(m)
