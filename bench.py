@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-implicit", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--implicit-ncells", type=int, default=0)
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -453,7 +454,8 @@ def main():
         variants = variants_bench(key, gm, r, t, y)
     implicit = None
     if not a.no_implicit and key == "hydrocarbon":
-        implicit = implicit_bench(gm, mech, workloads.NCELLS["implicit"], workloads.IMPLICIT_DT)
+        implicit = implicit_bench(gm, mech, a.implicit_ncells or workloads.NCELLS["implicit"],
+                                  workloads.IMPLICIT_DT)
     serving = None
     if not a.no_serve and key == "hydrocarbon" and rank == 0:
         from paper_2405_05974_b300 import binding as _b

@@ -141,7 +141,7 @@ class OracleMech:
             for i, (s, nu) in enumerate(r["products"].items()):
                 rsp[4 * j + i] = idx[s]; rnu[4 * j + i] = nu
             nr[j] = len(r["products"])
-            rev[j] = 1 if r["reversible"] else 0
+            rev[j] = (1 if r["reversible"] else 0) | (0 if r.get("forward", True) else 2)
             arr[3 * j:3 * j + 3] = (r["A"], r["b"], r["Ea"])
             if r.get("third_body"):
                 kind[j] = 1

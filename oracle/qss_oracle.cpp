@@ -125,7 +125,8 @@ struct Side {
 
 struct Reaction {
   Side lhs, rhs;
-  bool reversible;
+  bool reversible;            // reverse direction active
+  bool forward = true;        // forward direction active (false: reverse-only)
   double A, b, Ea;            // CHEMKIN units (cm-mol-s, cal/mol) as given
   int kind;                   // 0 plain, 1 third body, 2 Troe falloff
   double A0, b0, Ea0;         // low-pressure limit (Troe)
@@ -398,7 +399,16 @@ bool eval_cell(const Mech& m, const S* phi /*[N+1] = C, T*/, bool want_jac, bool
   std::vector<Thermo<S>> th(N + Q);
   for (int s = 0; s < N + Q; ++s) th[s] = nasa(m, s, T, lnT);
   std::vector<Rate<S>> rk(m.M);
-  for (int j = 0; j < m.M; ++j) rk[j] = rate_constants(m, m.rx[j], T, lnT, C, th);
+  for (int j = 0; j < m.M; ++j) {
+    rk[j] = rate_constants(m, m.rx[j], T, lnT, C, th);
+    if (!m.rx[j].forward) {
+      // reverse-only reaction (one-sided linearization): k_b = k_f / K_c is
+      // kept, the forward term is removed
+      rk[j].kf = S(0.0);
+      rk[j].dkf_dT = S(0.0);
+      rk[j].dkf_dM = S(0.0);
+    }
+  }
 
   // transported-only parts of the forward / reverse terms
   std::vector<S> pf(m.M), pb(m.M), qfp(m.M), qbp(m.M);
@@ -709,7 +719,10 @@ void* oracle_mech_create(int N, int Q, int M, const double* W, const double* nas
       r.rhs.nu.push_back(rnu[j * 4 + i]);
       if (rsp[j * 4 + i] >= N) r.qss_r = rsp[j * 4 + i] - N;
     }
-    r.reversible = reversible[j] != 0;
+    // reversible[j]: bit 0 = reverse direction active, bit 1 = forward
+    // direction removed (reverse-only reaction)
+    r.reversible = (reversible[j] & 1) != 0;
+    r.forward = (reversible[j] & 2) == 0;
     r.kind = kind[j];
     r.A = arr[j * 3]; r.b = arr[j * 3 + 1]; r.Ea = arr[j * 3 + 2];
     r.A0 = low[j * 3]; r.b0 = low[j * 3 + 1]; r.Ea0 = low[j * 3 + 2];
@@ -727,14 +740,21 @@ void* oracle_mech_create(int N, int Q, int M, const double* W, const double* nas
       r.Ea0_over_R = 0.0;
     }
   }
-  // QSS dependency digraph: m needs n when a reaction has n on one side and m
-  // on the other side (forward: n reactant; reverse if reversible: n product).
+  // QSS dependency digraph: m needs n when an active direction's rate is
+  // proportional to C_n (n its one QSS reactant) and m is a QSS species of
+  // the reaction's other side.
   std::vector<std::vector<int>> adj(Q);
   for (int j = 0; j < M; ++j) {
     const Reaction& r = m->rx[j];
-    if (r.qss_l >= 0 && r.qss_r >= 0 && r.qss_l != r.qss_r) {
-      adj[r.qss_r].push_back(r.qss_l);
-      if (r.reversible) adj[r.qss_l].push_back(r.qss_r);
+    for (int dir = 0; dir < 2; ++dir) {
+      if (dir == 0 ? !r.forward : !r.reversible) continue;
+      const Side& in = dir == 0 ? r.lhs : r.rhs;
+      const Side& other = dir == 0 ? r.rhs : r.lhs;
+      int n = -1;
+      for (int v : in.sp) if (v >= N) n = v - N;
+      if (n < 0) continue;
+      for (int v : other.sp)
+        if (v >= N && v - N != n) adj[v - N].push_back(n);
     }
   }
   for (auto& a : adj) {

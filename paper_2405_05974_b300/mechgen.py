@@ -534,6 +534,70 @@ def _assign_groups(rng, sizes, qss_ids, link):
 # states
 # ---------------------------------------------------------------------------
 
+def add_quadratic_couplings(mech: dict, n_couplings: int, seed: int) -> dict:
+    """A copy of ``mech`` with ``n_couplings`` extra reactions whose rates are
+    products of QSS concentrations (Section 2.2's quadratic couplings), as a
+    synthetic stand-in for QSS mechanisms that need linearization.
+
+    Kinds, in turn: q_a + q_b <=> X + Y (forward coupled), X + Y <=> q_a + q_b
+    (reverse coupled), 2 q_a -> X (irreversible, forward coupled), and
+    q_a + q_b <=> q_c + q_d (both directions coupled).  Reversible reactions
+    are atom balanced (products found among species of the same total
+    composition); where no balanced partner exists the reaction is made
+    irreversible, which needs no equilibrium constant.  Rate parameters are
+    drawn like the others' (bimolecular)."""
+    import copy
+    rng = np.random.default_rng(seed)
+    out = copy.deepcopy(mech)
+    sp = out["species"]
+    comp = {x["name"]: tuple(x["composition"].get(e, 0) for e in ELEMENTS) for x in sp}
+    qss = [x["name"] for x in sp if x["qss"]]
+    tr = [x["name"] for x in sp if not x["qss"]]
+    pairs_tr = {}
+    for i, a in enumerate(tr):
+        for b_ in tr[i:]:
+            pairs_tr.setdefault(tuple(u + v for u, v in zip(comp[a], comp[b_])), []).append((a, b_))
+    pairs_q = {}
+    for i, a in enumerate(qss):
+        for b_ in qss[i + 1:]:
+            pairs_q.setdefault(tuple(u + v for u, v in zip(comp[a], comp[b_])), []).append((a, b_))
+
+    def side(names):
+        d = {}
+        for x in names:
+            d[x] = d.get(x, 0) + 1
+        return d
+
+    added = 0
+    tries = 0
+    while added < n_couplings and tries < 1000 * max(n_couplings, 1):
+        tries += 1
+        kind = added % 4
+        qa, qb = (str(x) for x in rng.choice(qss, size=2, replace=False))
+        key = tuple(u + v for u, v in zip(comp[qa], comp[qb]))
+        if kind == 2:
+            lhs, rhs, rev = [qa, qa], [str(rng.choice(tr))], False
+        elif kind == 3:
+            cand = [p for p in pairs_q.get(key, []) if set(p) != {qa, qb}]
+            if not cand:
+                continue
+            lhs, rhs, rev = [qa, qb], list(cand[int(rng.integers(len(cand)))]), True
+        else:
+            cand = pairs_tr.get(key, [])
+            if cand:
+                prod, rev = list(cand[int(rng.integers(len(cand)))]), True
+            else:
+                prod, rev = [str(x) for x in rng.choice(tr, size=2, replace=False)], False
+            lhs, rhs = ([qa, qb], prod) if (kind == 0 or not rev) else (prod, [qa, qb])
+        a_ref, b, ea = _arrhenius(rng)
+        out["reactions"].append({"reactants": side(lhs), "products": side(rhs), "reversible": rev,
+                                 "A": _chemkin_A(a_ref, b, 2), "b": b, "Ea": ea, "third_body": None,
+                                 "falloff": None, "duplicate": False})
+        added += 1
+    out["name"] = f"{mech.get('name', 'mech')}_quad{added}"
+    return out
+
+
 def transported_species(mech):
     return [s for s in mech["species"] if not s["qss"]]
 

@@ -3,8 +3,10 @@
 Reads the mechanism dictionary (see ``mechgen``), orders species as
 transported (0..N-1) then QSS (N..N+Q-1), converts rate parameters to SI
 (CHEMKIN cm-mol-s -> m-mol-s by (1e-6)^(order-1); cal/mol -> J/mol), and
-checks the linearity condition of the QSS relations (Section 2.2): every
-reaction side holds at most one QSS species, with coefficient one.
+checks the linearity condition of the QSS relations (Section 2.2): the
+reactant side of every active reaction direction holds at most one QSS
+species, with coefficient one (``qssc.linearize`` removes the couplings that
+break it).  A reaction may be reverse-only (``"forward": false``).
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ class Rxn:
     troe: Tuple[float, float, float, float] = (0.0, 1.0, 1.0, 1.0)
     qss_l: int = -1
     qss_r: int = -1
+    forward: bool = True         # False: reverse-only (one-sided linearization)
 
 
 @dataclass
@@ -73,13 +76,18 @@ def parse(mech: dict) -> MechIR:
             raise MechanismError(f"reaction {j}: unknown species {e}") from None
         if any(nu <= 0 for _, nu in lhs + rhs):
             raise MechanismError(f"reaction {j}: stoichiometric coefficients must be positive")
+        forward = bool(r.get("forward", True))
+        reversible = bool(r["reversible"])
+        if not forward and not reversible:
+            raise MechanismError(f"reaction {j}: both directions removed")
         ql = [(s, nu) for s, nu in lhs if s >= N]
         qr = [(s, nu) for s, nu in rhs if s >= N]
-        for side, lab in ((ql, "left"), (qr, "right")):
-            if len(side) > 1 or (side and side[0][1] != 1):
+        # only the reactant side of an active direction enters a rate
+        for side, lab, active in ((ql, "left", forward), (qr, "right", reversible)):
+            if active and (len(side) > 1 or (side and side[0][1] != 1)):
                 raise MechanismError(
                     f"reaction {j}: quadratic QSS coupling on the {lab} side "
-                    "(linearization of the QSS relations is required first)")
+                    "(linearization of the QSS relations is required first: qssc.linearize)")
         kind = 2 if r.get("falloff") else (1 if r.get("third_body") else 0)
         order_ = sum(nu for _, nu in lhs)
         ord_inf = order_ + (1 if kind == 1 else 0)
@@ -93,9 +101,10 @@ def parse(mech: dict) -> MechIR:
                     raise MechanismError(f"reaction {j}: unknown collider {s}")
                 if ix[s] < N and float(e) != 1.0:
                     eff[ix[s]] = float(e)
-        rx = Rxn(lhs=lhs, rhs=rhs, reversible=bool(r["reversible"]), kind=kind, lnA=lnA,
+        rx = Rxn(lhs=lhs, rhs=rhs, reversible=reversible, kind=kind, lnA=lnA,
                  b=float(r["b"]), EaR=float(r["Ea"]) * CAL / R_GAS, eff=eff,
-                 qss_l=(ql[0][0] - N) if ql else -1, qss_r=(qr[0][0] - N) if qr else -1)
+                 qss_l=(ql[0][0] - N) if (ql and forward) else -1,
+                 qss_r=(qr[0][0] - N) if (qr and reversible) else -1, forward=forward)
         if kind == 2:
             lo = r["falloff"]["low"]
             if lo["A"] <= 0:

@@ -238,6 +238,8 @@ class _Builder:
             qf = g.mul(kf, pf)
             if rx.qss_l >= 0:
                 qf = g.mul(qf, self.CQ[rx.qss_l])
+            if not rx.forward:
+                qf = g.ZERO          # reverse-only: k_b = k_f / K_c is kept
             if kb is not None:
                 pb = g.prod([g.powi(self.C[s], nu) for s, nu in rx.rhs if s < N])
                 qb = g.mul(kb, pb)
