@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--implicit-ncells", type=int, default=0)
+    p.add_argument("--jac-parts", type=int, default=-1,
+                   help="Jacobian as a prefix + this many column-group kernels (default: per workload)")
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -375,7 +377,10 @@ def main():
     from paper_2405_05974_b300 import autotune, binding, mechgen
     from paper_2405_05974_b300.qssc.build import build_mechanism, load_meta
     torch.cuda.set_device(local)
-    art = autotune.artefact(mech, torch.cuda.get_device_name(local))
+    opts = workloads.build_options(key)
+    if a.jac_parts >= 0:
+        opts["jac_parts"] = a.jac_parts
+    art = autotune.artefact(mech, torch.cuda.get_device_name(local), **opts)
     meta = load_meta(art)
     gm = binding.Mechanism(art, local)
     st_cfg = workloads.STATES[key]
@@ -418,13 +423,21 @@ def main():
     kernel_ms = float(np.mean(per))
     flops_cell = meta["flops_jac"]
     achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
-    traffic = traffic_from_profile("qss_jac_kernel", key, meta["artefact_key"], ncells)
+    parts = int(meta.get("jac_parts", 0) or 0)
+    launches_per_step = 1
+    if parts >= 2:
+        # the library processes a partitioned Jacobian in chunks that fit a
+        # 1 GiB frontier buffer: one prefix and `parts` group launches each
+        fr_cells = max(32, ((1 << 30) // (8 * int(meta["frontier"]))) // 32 * 32)
+        launches_per_step = -(-ncells // fr_cells) * (parts + 1)
+    jac_kernel = "qss_jac_kernel" if parts < 2 else f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel"
+    traffic = traffic_from_profile("qss_jac_kernel", key, meta["artefact_key"], ncells) if parts < 2 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "measured live on this GPU: FP64 DFMA microbenchmark "
                            "(qss_measure_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
             "flops_per_cell": flops_cell, "fp64_instr_per_cell_est": meta.get("fp64_instr_jac"),
-            "kernel": "qss_jac_kernel", "kernel_ms": kernel_ms,
+            "kernel": jac_kernel, "kernel_ms": kernel_ms,
             "hbm_algorithmic_gbs": (8.0 * (2 + gm.N + gm.N + 1 + n * n) * ncells) / (kernel_ms * 1e-3) / 1e9}
 
     e2e = None
@@ -476,9 +489,9 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
             "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": a.steps, "clocks": clk.summary(),
+            "gpu_launches": a.steps * launches_per_step, "clocks": clk.summary(),
             "implicit": implicit, "serving": serving, "jacobian_variants": variants,
-            "kernel": {"ptxas": meta["kernels"].get("qss_jac_kernel", {}),
+            "kernel": {"ptxas": {k: v for k, v in meta["kernels"].items() if k.startswith("qss_jac")},
                        "defines": meta.get("defines", []),
                        "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}
     print(json.dumps(line), flush=True)

@@ -46,7 +46,8 @@ namespace qss {
 size_t newton_scratch_per_cell(const qss_mech_s* m, int precision) {
   (void)precision;   // both forms keep J in FP64; the FP32 factors live in registers
   const int n = m->N + 1;
-  return (size_t)n * n * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int);
+  return (size_t)n * n * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int) +
+         frontier_bytes_per_cell(m);
 }
 
 int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
@@ -92,6 +93,10 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   int* IT = ST + S;
   int* LIST[2] = {IT + S, IT + 2 * S};
   int* NACT = IT + 3 * S;   // two counters (S is a multiple of 32, so they fit in the tail)
+  // frontier of a partitioned Jacobian right after the two counters: ACT + 5 S
+  // + 2 ints is 8-byte aligned (S % 32 == 0), and the region ends within
+  // per_cell * S + 256 bytes of the scratch start
+  double* FR = frontier_bytes_per_cell(m) ? (double*)(NACT + 2) : nullptr;
   long long sld = chunk, l = ld;
   int rc;
   const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
@@ -101,15 +106,12 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
     if ((rc = launch_cells(m, m->f_newton_setup, cells, m->block, a_setup, st, 0))) return rc;
     for (int it = 0; it < o.max_iter; ++it) {
       const int cur = it & 1, nxt = cur ^ 1;
-      const double* nul = nullptr;
-      double* Fw = F;
-      double* FT = F + (size_t)m->N * S;
-      const double* phic = PHI;
       const int* lc = LIST[cur];
       const int* nc = NACT + cur;
       int* nn = NACT + nxt;
-      void* a_jac[] = {&cells, &sld, &nul, &nul, &nul, &M64, &Fw, &FT, &phic, &lc, &nc, &nn};
-      if ((rc = launch_cells(m, m->f_jac, cells, m->block, a_jac, st, 0))) return rc;
+      if ((rc = jac_launch(m, cells, sld, nullptr, nullptr, nullptr, M64, F, F + (size_t)m->N * S, PHI,
+                           lc, nc, nn, FR, (int64_t)S, st)))
+        return rc;
       int* l2 = LIST[nxt];
       void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
                        &lc, &nc, &l2, &nn, &sld, &od};

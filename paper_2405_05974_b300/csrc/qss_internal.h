@@ -19,6 +19,17 @@ struct qss_mech_s {
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   int upd_threads[2] = {128, 128};   // block size of the update kernels (their launch bound)
+  // partitioned Jacobian (jac_parts >= 2): prefix kernel + column-group kernels
+  int jac_parts = 0, frontier = 0;   // frontier: doubles per cell between them
+  CUmodule mod_prefix = nullptr;
+  CUfunction f_prefix = nullptr;
+  std::vector<CUmodule> mod_group;
+  std::vector<CUfunction> f_group;
+  // frontier scratch of the device-array path; fr_done orders its reuse
+  // across streams (recorded after each call's last group kernel)
+  CUdeviceptr fr_scratch = 0;
+  int64_t fr_cells = 0;
+  CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
   std::vector<double> W;
   std::string name, digest, dir;
@@ -40,6 +51,18 @@ std::string lib_dir();
 int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx);
 int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
                  CUstream stream, unsigned shmem);
+// wdot, Tdot and J of ncells cells, monolithic or partitioned.  State from
+// (rho, T, Y) with leading dimension ld, J SoA with ld; or, in list mode (phi,
+// list, nact given), of the listed cells with J cell-contiguous.  fr/fld: the
+// frontier scratch of a partitioned Jacobian (fld >= ncells; unused
+// otherwise).
+int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+               const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
+               const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
+               CUstream s);
+inline size_t frontier_bytes_per_cell(const qss_mech_s* m) {
+  return m->jac_parts >= 2 ? (size_t)m->frontier * sizeof(double) : 0;
+}
 // implicit step (qss_implicit.cpp)
 size_t newton_scratch_per_cell(const qss_mech_s* m, int precision);
 int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,

@@ -15,9 +15,10 @@
 
 // f = (wdot, Tdot) and J.  State from (rho, T, Y) or, in list mode (phi and
 // list given), of the t-th cell of the list: s = list[t] for t < *nact, state
-// phi[k * ld + s] = (C_1..C_N, T), outputs written at column t.  In list mode
-// thread 0 also clears *nact_next, the counter the following Newton update
-// fills.
+// phi[k * ld + s] = (C_1..C_N, T), f written at column t (wdot[k * ld + t])
+// and J written cell-contiguous, jac[t * (N+1)^2 + e] (the Newton update reads
+// one cell's matrix at a time with coalesced loads).  In list mode thread 0
+// also clears *nact_next, the counter the following Newton update fills.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
 qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                const double* __restrict__ T, const double* __restrict__ Y,
@@ -27,6 +28,8 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   double C[QSS_N];
   double Tc;
+  double* jc;
+  long long jstride;
   if (phi) {
     if (c == 0) *nact_next = 0;
     if (c >= *nact) return;
@@ -34,10 +37,15 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
 #pragma unroll
     for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
     Tc = phi[QSS_N * ld + s];
+    jc = jac + c * (QSS_NN * QSS_NN);
+    jstride = 1;
   } else {
     if (c >= ncells) return;
     qss_unpack(c, ld, rho, Y, C);
     Tc = __ldg(T + c);
+    jc = jac + c;
+    jstride = ld;
   }
-  qss_eval_jac(C, Tc, wdot ? wdot + c : nullptr, Tdot ? Tdot + c : nullptr, jac + c, ld, ld);
+  // one call site: the generated body is inlined once
+  qss_eval_jac(C, Tc, wdot ? wdot + c : nullptr, Tdot ? Tdot + c : nullptr, jc, ld, jstride);
 }

@@ -22,7 +22,8 @@
 //   update_fp64    factorisation and solve in FP64.
 //   update_fp32ir  M equilibrated by powers of two (rows, then columns),
 //                  factorisation in FP32; the solution refined with FP64
-//                  residuals g - M x (M re-read in FP64) until the correction
+//                  residuals g - M x (M from the FP64 copy in shared
+//                  memory, staged once per cell) until the correction
 //                  is below refine_tol relative, stops shrinking, or after
 //                  max_refine sweeps.
 // Rates, equilibrium constants, the QSS solve, J, M and the Newton residual
@@ -30,7 +31,8 @@
 //
 // Scratch (global memory, one chunk of `cells` cells, leading dimension sld;
 // s = cell - c0, t = position in the active list):
-//   M64[e * sld + t], e = i * NN + j     J of the t-th active cell
+//   M64[t * NN * NN + e], e = i * NN + j J of the t-th active cell, each cell's
+//                                        matrix contiguous (coalesced staging)
 //   F [k * sld + t]                       f, then g = -G, then the update x
 //   PHI, PHI0 [k * sld + s]               iterate, initial state
 //   ACT, ST, IT [s]                       active flag, status, iterations
@@ -165,8 +167,12 @@ __device__ __forceinline__ bool qss_warp_factor(R (&a)[QSS_NSLOT][QSS_NN], R (&y
       if (elim) a[sl][k] = l[sl];
       y[sl] = fma(-l[sl], py, y[sl]);
     }
+    // constant trip count (the j <= k iterations fold away once both loops
+    // are unrolled): a loop starting at k + 1 is not unrolled before the
+    // outer one, and a dynamic index would put a[][] in local memory
 #pragma unroll
-    for (int j = k + 1; j < QSS_NN; ++j) {
+    for (int j = 0; j < QSS_NN; ++j) {
+      if (j <= k) continue;
       R pj = a[0][j];
 #pragma unroll
       for (int sl = 1; sl < QSS_NSLOT; ++sl)
@@ -224,12 +230,6 @@ __device__ __forceinline__ void qss_warp_back(const R (&a)[QSS_NSLOT][QSS_NN], R
   }
 }
 
-__device__ __forceinline__ double qss_mentry(const double* __restrict__ M64, long long sld,
-                                             long long tq, int r, int j, double hq) {
-  const double m = -hq * M64[(r * QSS_NN + j) * sld + tq];
-  return (j == r) ? 1.0 + m : m;
-}
-
 template <bool FP32IR>
 __device__ __forceinline__ void qss_newton_update(
     long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
@@ -241,8 +241,8 @@ __device__ __forceinline__ void qss_newton_update(
   __shared__ int sh_piv[QSS_UPD_WARPS][QSS_NN];
   __shared__ double sh_x[QSS_UPD_WARPS][QSS_NN + 1];
   __shared__ double sh_pinv[QSS_UPD_WARPS][QSS_NN];
-  // FP32_IR: per-warp copy of the FP64 Newton matrix (padded rows)
-  __shared__ double sh_m[FP32IR ? QSS_UPD_WARPS * QSS_NN * QSS_MSTRIDE : 1];
+  // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows)
+  __shared__ double sh_m[QSS_UPD_WARPS * QSS_NN * QSS_MSTRIDE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long t0 = ((long long)blockIdx.x * QSS_UPD_WARPS + w) * 32;
   const int nact = *NACT;
@@ -277,13 +277,15 @@ __device__ __forceinline__ void qss_newton_update(
     int er[QSS_NSLOT];
     double gr[QSS_NSLOT];
     bool fin = true;
-    double* Ms = &sh_m[FP32IR ? w * QSS_NN * QSS_MSTRIDE : 0];   // this warp's copy of M = I - hq J
-    if (FP32IR) {
-      // one pass over J in global memory: consecutive entries across lanes
+    double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of M = I - hq J
+    {
+      // the cell's J is contiguous (written so by the Jacobian kernel in list
+      // mode): one coalesced pass, 256 bytes per warp load
+      const double* __restrict__ Jq = M64 + tq * (QSS_NN * QSS_NN);
 #pragma unroll 4
       for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
         const int r = e / QSS_NN, j = e - r * QSS_NN;
-        const double m = -hq * M64[e * sld + tq];
+        const double m = -hq * Jq[e];
         fin = fin && qss_finite(m);
         Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
       }
@@ -301,9 +303,7 @@ __device__ __forceinline__ void qss_newton_update(
         if (FP32IR) {
           if (live) mx = max(mx, qss_absbits(Ms[r * QSS_MSTRIDE + j]));
         } else {
-          const double m = live ? qss_mentry(M64, sld, tq, r, j, hq) : 0.0;
-          fin = fin && qss_finite(m);
-          a[sl][j] = m;
+          a[sl][j] = live ? Ms[r * QSS_MSTRIDE + j] : 0.0;
         }
       }
       if (FP32IR) {

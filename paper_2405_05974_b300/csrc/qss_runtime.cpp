@@ -71,6 +71,28 @@ int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** 
   return QSS_OK;
 }
 
+int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+               const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
+               const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
+               CUstream s) {
+  long long nc = ncells, l = ld;
+  int rc;
+  if (m->jac_parts < 2) {
+    void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
+    return launch_cells(m, m->f_jac, ncells, m->block, args, s, 0);
+  }
+  if (!fr || fld < ncells) return fail(QSS_ERR_INVALID_ARG, "frontier scratch too small");
+  long long fl = fld;
+  void* pa[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot, &fr, &fl, &phi, &list, &nact, &nact_next};
+  if ((rc = launch_cells(m, m->f_prefix, ncells, m->block, pa, s, 0))) return rc;
+  const double* frc = fr;
+  for (int i = 0; i < m->jac_parts; ++i) {
+    void* ga[] = {&nc, &frc, &fl, &jac, &l, &nact};
+    if ((rc = launch_cells(m, m->f_group[i], ncells, m->block, ga, s, 0))) return rc;
+  }
+  return QSS_OK;
+}
+
 }  // namespace qss
 
 using namespace qss;
@@ -98,38 +120,54 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "Q") ls >> m->Q;
     else if (key == "M") ls >> m->M;
     else if (key == "block") ls >> m->block;
+    else if (key == "jac_parts") ls >> m->jac_parts;
+    else if (key == "frontier") ls >> m->frontier;
     else if (key == "W") {
       double w;
       while (ls >> w) m->W.push_back(w);
     }
   }
-  if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N) {
+  if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
+      m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N)) {
     delete m;
     return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
   }
   int rc = ctx_for_device(device, &m->dev, &m->ctx);
   if (rc) { delete m; return rc; }
   m->device = device;
-  // required kernels: the analytic Jacobian (jac.cubin) and the source term
-  // with the finite-difference Jacobian (wdot.cubin)
-  struct Need { CUmodule* mod; const char* file; const char* fn; CUfunction* slot; };
-  const Need need[] = {{&m->mod, "jac.cubin", "qss_jac_kernel", &m->f_jac},
-                       {&m->mod_wdot, "wdot.cubin", "qss_wdot_kernel", &m->f_wdot},
-                       {&m->mod_wdot, "wdot.cubin", "qss_jac_fd_kernel", &m->f_jac_fd}};
+  // required kernels: the analytic Jacobian (jac.cubin, or jac_prefix.cubin
+  // and jac_g<i>.cubin when partitioned) and the source term with the
+  // finite-difference Jacobian (wdot.cubin)
+  struct Need { CUmodule* mod; std::string file; const char* fn; CUfunction* slot; };
+  std::vector<Need> need;
+  if (m->jac_parts >= 2) {
+    m->mod_group.assign(m->jac_parts, nullptr);
+    m->f_group.assign(m->jac_parts, nullptr);
+    need.push_back({&m->mod_prefix, "jac_prefix.cubin", "qss_jac_prefix_kernel", &m->f_prefix});
+    for (int i = 0; i < m->jac_parts; ++i)
+      need.push_back({&m->mod_group[i], "jac_g" + std::to_string(i) + ".cubin", "qss_jac_group_kernel",
+                      &m->f_group[i]});
+  } else {
+    need.push_back({&m->mod, "jac.cubin", "qss_jac_kernel", &m->f_jac});
+  }
+  need.push_back({&m->mod_wdot, "wdot.cubin", "qss_wdot_kernel", &m->f_wdot});
+  need.push_back({&m->mod_wdot, "wdot.cubin", "qss_jac_fd_kernel", &m->f_jac_fd});
   for (const Need& nd : need) {
     CUresult r = CUDA_SUCCESS;
     if (!*nd.mod) r = drv().cuModuleLoad(nd.mod, (dir + "/" + nd.file).c_str());
     int code = 0;
-    std::string msg;
     if (r != CUDA_SUCCESS) {
-      code = cu_fail(r, (std::string("drv().cuModuleLoad(") + nd.file + ")").c_str());
+      code = cu_fail(r, ("drv().cuModuleLoad(" + nd.file + ")").c_str());
       *nd.mod = nullptr;
     } else if (drv().cuModuleGetFunction(nd.slot, *nd.mod, nd.fn) != CUDA_SUCCESS) {
-      code = fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + nd.fn);
+      code = fail(QSS_ERR_MECH_FORMAT, std::string("artefact lacks kernel ") + nd.fn + " in " + nd.file);
     }
     if (code) {
       if (m->mod) drv().cuModuleUnload(m->mod);
       if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
+      if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
+      for (CUmodule g : m->mod_group)
+        if (g) drv().cuModuleUnload(g);
       drv().cuDevicePrimaryCtxRelease(m->dev);
       delete m;
       return code;
@@ -163,6 +201,11 @@ void qss_mech_free(qss_mech_t m) {
     if (m->st[b]) drv().cuStreamDestroy(m->st[b]);
   }
   if (m->newton_scratch) drv().cuMemFree(m->newton_scratch);
+  if (m->fr_scratch) drv().cuMemFree(m->fr_scratch);
+  if (m->fr_done) drv().cuEventDestroy(m->fr_done);
+  if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
+  for (CUmodule g : m->mod_group)
+    if (g) drv().cuModuleUnload(g);
   if (m->mod) drv().cuModuleUnload(m->mod);
   if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
   if (m->mod_newton) drv().cuModuleUnload(m->mod_newton);
@@ -204,12 +247,36 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   if (rc) return rc;
   if (ncells == 0) return QSS_OK;
   if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
-  long long nc = ncells, l = ld;
-  const double* phi = nullptr;
-  const int* list = nullptr;
-  int* none = nullptr;
-  void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &list, &none};
-  return launch_cells(m, m->f_jac, ncells, m->block, args, (CUstream)stream, 0);
+  CUstream s = (CUstream)stream;
+  if (m->jac_parts < 2)
+    return jac_launch(m, ncells, ld, rho, T, Y, jac, wdot, Tdot, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, 0, s);
+  // partitioned: chunks of cells through the handle's frontier scratch (at
+  // most 1 GiB), its reuse ordered after the previous call by an event
+  std::lock_guard<std::mutex> lock(m->mu);
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  const size_t per = frontier_bytes_per_cell(m);
+  int64_t want = std::max<int64_t>(32, (int64_t)((size_t(1) << 30) / per) / 32 * 32);
+  want = std::min<int64_t>(want, (ncells + 31) / 32 * 32);
+  if (m->fr_cells < want) {
+    if (m->fr_done) CU_TRY(drv().cuEventSynchronize(m->fr_done));
+    if (m->fr_scratch) { drv().cuMemFree(m->fr_scratch); m->fr_scratch = 0; m->fr_cells = 0; }
+    if (drv().cuMemAlloc(&m->fr_scratch, per * (size_t)want) != CUDA_SUCCESS)
+      return fail(QSS_ERR_OOM, "cannot allocate the Jacobian frontier scratch");
+    m->fr_cells = want;
+  }
+  if (!m->fr_done) CU_TRY(drv().cuEventCreate(&m->fr_done, CU_EVENT_DISABLE_TIMING));
+  else CU_TRY(drv().cuStreamWaitEvent(s, m->fr_done, 0));
+  double* fr = (double*)m->fr_scratch;
+  for (int64_t c0 = 0; c0 < ncells; c0 += m->fr_cells) {
+    const int64_t cs = std::min<int64_t>(m->fr_cells, ncells - c0);
+    if ((rc = jac_launch(m, cs, ld, rho + c0, T + c0, Y + c0, jac + c0, wdot ? wdot + c0 : nullptr,
+                         Tdot ? Tdot + c0 : nullptr, nullptr, nullptr, nullptr, nullptr, fr,
+                         m->fr_cells, s)))
+      return rc;
+  }
+  CU_TRY(drv().cuEventRecord(m->fr_done, s));
+  return QSS_OK;
 }
 
 int qss_jacobian_fd(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho,
@@ -266,7 +333,8 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
   int64_t S = chunk > 0 ? chunk : 65536;
   S = std::min<int64_t>(S, ncells);
   S = (S + 31) / 32 * 32;
-  const size_t per_cell = (size_t)(2 + N + N + 1 + n * n);
+  const size_t fpc = frontier_bytes_per_cell(m) / sizeof(double);
+  const size_t per_cell = (size_t)(2 + N + N + 1 + n * n) + fpc;
   const size_t need = per_cell * (size_t)S * sizeof(double);
   if (m->stage_bytes < need) {
     for (int b = 0; b < 2; ++b) {
@@ -299,14 +367,10 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
     if ((rc = copy2d(d_rho, false, P, rho + c0, true, hp, w, 1, s))) return rc;
     if ((rc = copy2d(d_T, false, P, T + c0, true, hp, w, 1, s))) return rc;
     if ((rc = copy2d(d_Y, false, P, Y + c0, true, hp, w, N, s))) return rc;
-    long long nc = cs, l = S;
-    double* wp = d_w;
-    double* tp = d_Td;
-    const double* phi = nullptr;
-    const int* list = nullptr;
-    int* none = nullptr;
-    void* args[] = {&nc, &l, &d_rho, &d_T, &d_Y, &d_J, &wp, &tp, &phi, &list, &list, &none};
-    if ((rc = launch_cells(m, m->f_jac, cs, m->block, args, s, 0))) return rc;
+    double* d_fr = d_J + (size_t)n * n * S;   // frontier (partitioned Jacobian only)
+    if ((rc = jac_launch(m, cs, S, d_rho, d_T, d_Y, d_J, d_w, d_Td, nullptr, nullptr, nullptr,
+                         nullptr, fpc ? d_fr : nullptr, S, s)))
+      return rc;
     if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, (size_t)n * n, s))) return rc;
     if (wdot && (rc = copy2d(wdot + c0, true, hp, d_w, false, P, w, N, s))) return rc;
     if (Tdot && (rc = copy2d(Tdot + c0, true, hp, d_Td, false, P, w, 1, s))) return rc;

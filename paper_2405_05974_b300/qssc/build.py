@@ -34,9 +34,9 @@ REPO = os.path.dirname(PKG)
 DEFAULT_ROOT = os.path.join(REPO, "build", "mech")
 NVCC = os.environ.get("QSS_NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_cells.cuh", "qss_jac_kernel.cuh",
-             "qss_wdot_kernels.cuh", "qss_newton.cuh"]
-ARTEFACT_FILES = ("jac.cubin", "wdot.cubin", "newton.cubin", "meta.txt", "meta.json")
+TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc", "qss_cells.cuh",
+             "qss_jac_kernel.cuh", "qss_jac_parts.cuh", "qss_wdot_kernels.cuh", "qss_newton.cuh"]
+ARTEFACT_FILES = ("wdot.cubin", "newton.cubin", "meta.txt", "meta.json")
 COMPILER_VERSION = "1"
 
 
@@ -99,49 +99,115 @@ def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: s
     return open(log_path).read()
 
 
+_INDEX_LOCK = threading.Lock()
+
+
+def _read_index(root: str) -> dict:
+    try:
+        with open(os.path.join(root, "index.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _write_index(root: str, fast: str, name: str):
+    """Record fast key -> artefact directory (read-modify-write under a lock;
+    concurrent processes at worst lose an entry, which costs one codegen)."""
+    with _INDEX_LOCK:
+        idx = _read_index(root)
+        if idx.get(fast) == name:
+            return
+        idx[fast] = name
+        os.makedirs(root, exist_ok=True)
+        tmp = os.path.join(root, "index.json.tmp%d_%d" % (os.getpid(), threading.get_ident()))
+        with open(tmp, "w") as f:
+            json.dump(idx, f, indent=0, sort_keys=True)
+        os.replace(tmp, os.path.join(root, "index.json"))
+
+
+def _complete(out: str) -> bool:
+    return all(os.path.exists(os.path.join(out, f)) for f in ARTEFACT_FILES) and (
+        os.path.exists(os.path.join(out, "jac.cubin")) or os.path.exists(os.path.join(out, "jac_prefix.cubin")))
+
+
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
-                    t_column: str = "analytic") -> str:
+                    t_column: str = "analytic", jac_parts: int = 0) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
-    ``jac_variant`` / ``t_column`` select the Jacobian that qss_jac_kernel
-    computes (``model.build_model``); ``defines`` are extra preprocessor
-    definitions of the kernel templates (e.g. ``QSS_MINBLOCKS=2``)."""
+    ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
+    compute (``model.build_model``); ``defines`` are extra preprocessor
+    definitions of the kernel templates (e.g. ``QSS_MINBLOCKS=2``);
+    ``jac_parts`` >= 2 splits the Jacobian into a prefix kernel and that many
+    column-group kernels (``emit.emit_partitioned_source``), each compiled in
+    its own translation unit."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
-    key = artefact_key(mech, block, tuple(defines) + variant)
-    out = os.path.join(root, f"{mech.get('name', 'mech')}_{key}")
-    if not force and all(os.path.exists(os.path.join(out, f)) for f in ARTEFACT_FILES):
-        return out
+    if jac_parts >= 2:
+        variant += (f"parts{int(jac_parts)}",)
+    # fast path: the key of (mechanism, options, generator, templates) in the
+    # index of built artefacts
+    fast = artefact_key(mech, block, tuple(defines) + variant)
+    index = _read_index(root)
+    if not force and fast in index and _complete(os.path.join(root, index[fast])):
+        return os.path.join(root, index[fast])
     t0 = time.time()
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
     src, meta = emit.emit_mechanism_source(model)
-    tmp = out + ".tmp%d" % os.getpid()
-    os.makedirs(tmp, exist_ok=True)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")
     parts = {"mech_sizes.inc": src[:iw], "mech_wdot.inc": src[iw:ij], "mech_jac.inc": src[ij:]}
-    for name, text in parts.items():
-        with open(os.path.join(tmp, name), "w") as f:
-            f.write(text)
+    if jac_parts >= 2:
+        prefix_src, group_srcs, pmeta = emit.emit_partitioned_source(model, int(jac_parts))
+        meta.update(pmeta)
+        del parts["mech_jac.inc"]
+        parts["mech_jac_prefix.inc"] = prefix_src
+        for i, gsrc in enumerate(group_srcs):
+            parts[f"mech_jac_g{i}.inc"] = gsrc
     hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES}
     flags = [f"-DQSS_BLOCK={block}", *[f"-D{d}" for d in defines]]
+    # the directory is keyed by what is compiled: the generated sources, the
+    # templates and the flags (a generator change that emits the same code
+    # keeps its artefacts)
+    hk = hashlib.sha256(json.dumps([sorted(parts.items()), sorted(hdr.items()), flags,
+                                    meta.get("jac_variant"), meta.get("t_column"), jac_parts]).encode())
+    art_name = f"{mech.get('name', 'mech')}_{hk.hexdigest()[:20]}"
+    out = os.path.join(root, art_name)
+    if not force and _complete(out):
+        _write_index(root, fast, art_name)
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    os.makedirs(tmp, exist_ok=True)
+    for pname, text in parts.items():
+        with open(os.path.join(tmp, pname), "w") as f:
+            f.write(text)
     t1 = time.time()
-    common = {k: hdr[k] for k in ("qss_device.cuh", "qss_exp_table.inc")}
+    common = {k: hdr[k] for k in ("qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc")}
     cells = {"qss_cells.cuh": hdr["qss_cells.cuh"], "mech_sizes.inc": parts["mech_sizes.inc"]}
     pre = '#include "qss_device.cuh"\n#include "mech_sizes.inc"\n'
-    units = {
-        "jac": (pre + '#include "mech_jac.inc"\n#include "qss_jac_kernel.cuh"\n',
-                {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"],
-                 "qss_jac_kernel.cuh": hdr["qss_jac_kernel.cuh"]}),
+    units = {}
+    if jac_parts >= 2:
+        jp = {"qss_jac_parts.cuh": hdr["qss_jac_parts.cuh"]}
+        units["jac_prefix"] = (pre + '#include "mech_jac_prefix.inc"\n#define QSS_JAC_PREFIX\n'
+                               '#include "qss_jac_parts.cuh"\n',
+                               {**common, **cells, **jp, "mech_jac_prefix.inc": parts["mech_jac_prefix.inc"]})
+        for i in range(int(jac_parts)):
+            nm = f"mech_jac_g{i}.inc"
+            units[f"jac_g{i}"] = (pre + f'#include "{nm}"\n#define QSS_JAC_GROUP\n#include "qss_jac_parts.cuh"\n',
+                                  {**common, **cells, **jp, nm: parts[nm]})
+    else:
+        units["jac"] = (pre + '#include "mech_jac.inc"\n#include "qss_jac_kernel.cuh"\n',
+                        {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"],
+                         "qss_jac_kernel.cuh": hdr["qss_jac_kernel.cuh"]})
+    units.update({
         "wdot": (pre + '#include "mech_wdot.inc"\n#include "qss_wdot_kernels.cuh"\n',
                  {**common, **cells, "mech_wdot.inc": parts["mech_wdot.inc"],
                   "qss_wdot_kernels.cuh": hdr["qss_wdot_kernels.cuh"]}),
         "newton": (pre + '#include "qss_newton.cuh"\n',
                    {**common, "mech_sizes.inc": parts["mech_sizes.inc"],
                     "qss_newton.cuh": hdr["qss_newton.cuh"]}),
-    }
+    })
     logs, secs = {}, {}
 
     def compile_unit(name):
@@ -151,25 +217,31 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
                                     os.path.join(tmp, f"build_{name}.log"))
         secs[name] = round(time.time() - t, 3)
 
-    with ThreadPoolExecutor(len(units)) as ex:
+    with ThreadPoolExecutor(min(len(units), os.cpu_count() or 4)) as ex:
         for f in [ex.submit(compile_unit, u) for u in units]:
             f.result()
-    meta["kernels"] = {k: v for name in units for k, v in _parse_ptxas(logs[name]).items()}
+    meta["kernels"] = {}
+    for name in units:
+        for k, v in _parse_ptxas(logs[name]).items():
+            meta["kernels"][f"{k}[{name[5:]}]" if name.startswith("jac_g") else k] = v
     meta["block"] = block
     meta["defines"] = list(defines)
     meta["codegen_s"] = round(t1 - t0, 3)
     meta["nvcc_s"] = secs
-    meta["artefact_key"] = key
+    meta["artefact_key"] = art_name.rsplit("_", 1)[1]
     with open(os.path.join(tmp, "meta.json"), "w") as f:
         json.dump(meta, f, indent=1)
     with open(os.path.join(tmp, "meta.txt"), "w") as f:
         f.write(f"name {meta['name']}\n")
         f.write(f"digest {meta['digest']}\n")
         f.write(f"N {meta['N']}\nQ {meta['Q']}\nM {meta['M']}\nblock {block}\n")
+        if jac_parts >= 2:
+            f.write(f"jac_parts {int(jac_parts)}\nfrontier {meta['frontier']}\n")
         f.write("W " + " ".join(repr(w) for w in meta["W"]) + "\n")
     if os.path.exists(out):
         shutil.rmtree(out)
     os.replace(tmp, out)
+    _write_index(root, fast, art_name)
     if verbose:
         print(f"built {out}: codegen {meta['codegen_s']}s nvcc {secs} {meta['kernels']}")
     return out

@@ -32,10 +32,11 @@ def _lit(v: float) -> str:
 
 
 class Emitter:
-    def __init__(self, model, input_names: Dict[int, str]):
+    def __init__(self, model, input_names: Dict[int, str], leaves: Dict[int, str] = None):
         self.m = model
         self.g = model.g
         self.inputs = input_names     # VAR node -> C identifier
+        self.leaves = leaves or {}    # any node -> C identifier of an already computed value
 
     def _resolve(self, i):
         g = self.g
@@ -47,7 +48,7 @@ class Emitter:
         g = self.g
         op = g.op[i]
         a = g.args[i]
-        if op in (CONST, VAR):
+        if op in (CONST, VAR) or i in self.leaves:
             return []
         if op == FACT:
             return [self._resolve(a[0])]
@@ -78,7 +79,9 @@ class Emitter:
         inline = set()
         for n in seen:
             op = g.op[n]
-            if op in (CONST, NEG, LT):
+            if n in self.leaves:
+                inline.add(n)
+            elif op in (CONST, NEG, LT):
                 inline.add(n)
             elif op == VAR:
                 inline.add(n)
@@ -113,6 +116,8 @@ class Emitter:
         def ref(n):
             n = self._resolve(n)
             op = g.op[n]
+            if n in self.leaves:
+                return self.leaves[n]
             if op == CONST:
                 v = g.val[n]
                 return _lit(v) if v >= 0 else f"({_lit(v)})"
@@ -190,6 +195,8 @@ class Emitter:
         # algorithmic count: each DAG operation once, independent of fusion
         dag = Counter()
         for n in seen:
+            if n in self.leaves:
+                continue
             op = g.op[n]
             if op in (ADD, SUB):
                 dag["add"] += 1
@@ -278,3 +285,171 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
                                                if model.jac[i][c] != g.ZERO),
     }
     return src, meta
+
+
+# ---------------------------------------------------------------------------
+# Partitioned Jacobian: a shared prefix kernel and K column-group kernels
+# ---------------------------------------------------------------------------
+_MATERIAL = (ADD, SUB, MUL, RECIP, EXP, LOG, SELECT)
+
+
+def _op_cost(g, x):
+    op = g.op[x]
+    if op == EXP:
+        return 10
+    if op == LOG:
+        return 13
+    if op == RECIP:
+        return 10
+    return 1 if op in _MATERIAL else 0
+
+
+def partition_jacobian(model, K: int, split_t: bool = True):
+    """Split the Jacobian's entries into K groups (whole concentration
+    columns, balanced by cost; the temperature column by rows when split_t)
+    and its DAG into the part needed by two or more groups (the prefix,
+    which also yields wdot and Tdot) and the parts needed by one group only.
+    Returns (groups, frontier, needs): the (row, column) entries of each
+    group, the prefix values a group kernel reads (node ids, in topological
+    order), and for each group the frontier nodes it reads.  Every operation
+    of the DAG is computed exactly once."""
+    g = model.g
+    N = model.ir.N
+    n = N + 1
+    em = Emitter(model, {})
+    res, kids = em._resolve, em._children
+    roots_w = [res(x) for x in model.wdot] + [res(model.Tdot)]
+    roots_c = [[res(model.jac[i][c]) for i in range(n)] for c in range(n)]
+    # the temperature column's entries are spread over the groups by row
+    # (its shared derivative terms then belong to the prefix); its
+    # single-group form is by far the slowest unit to compile
+    tcol = N if (split_t and K > 1) else None
+    # topological order of everything needed (children before users)
+    order, seen = [], set()
+    for r0 in roots_w + [r for col in roots_c for r in col]:
+        if r0 in seen:
+            continue
+        st = [(r0, False)]
+        while st:
+            x, done = st.pop()
+            if done:
+                order.append(x)
+                continue
+            if x in seen:
+                continue
+            seen.add(x)
+            st.append((x, True))
+            st.extend((k, False) for k in kids(x) if k not in seen)
+
+    def entry_group(i, c, col_group, ngroups):
+        return (i % ngroups) if c == tcol else col_group[c]
+
+    def masks(col_group, ngroups):
+        m = {}
+        for c in range(n):
+            for i, r in enumerate(roots_c[c]):
+                m[r] = m.get(r, 0) | (1 << entry_group(i, c, col_group, ngroups))
+        full = (1 << ngroups) - 1
+        for r in roots_w:
+            m[r] = full
+        for x in reversed(order):
+            mx = m.get(x, 0)
+            for k in kids(x):
+                m[k] = m.get(k, 0) | mx
+        return m
+
+    # balance: each column's cost when every column is its own group, then
+    # longest-first assignment to the least loaded group
+    saved = tcol
+    tcol = None
+    m1 = masks(list(range(n)), n)
+    tcol = saved
+    col_cost = [0] * n
+    for x in order:
+        mx = m1[x]
+        if mx and mx & (mx - 1) == 0:
+            col_cost[mx.bit_length() - 1] += _op_cost(g, x)
+    load = [0] * K
+    col_group = [0] * n
+    for c in sorted((c for c in range(n) if c != tcol), key=lambda c: -col_cost[c]):
+        gi = min(range(K), key=lambda i: load[i])
+        col_group[c] = gi
+        load[gi] += col_cost[c]
+    m = masks(col_group, K)
+    shared = {x for x in order if m[x] & (m[x] - 1)}
+    # frontier: shared computed values reached from a group's own nodes
+    # (through inline operations such as negation)
+    needs = []
+    frontier = set()
+    for gi in range(K):
+        need = set()
+        st = [r for c in range(n) for i, r in enumerate(roots_c[c])
+              if entry_group(i, c, col_group, K) == gi]
+        vis = set()
+        while st:
+            x = st.pop()
+            if x in vis:
+                continue
+            vis.add(x)
+            if x in shared and g.op[x] in _MATERIAL:
+                need.add(x)
+                continue
+            st.extend(kids(x))
+        needs.append(sorted(need))
+        frontier |= need
+    groups = [[(i, c) for c in range(n) for i in range(n) if entry_group(i, c, col_group, K) == gi]
+              for gi in range(K)]
+    return groups, sorted(frontier), needs
+
+
+def emit_partitioned_source(model, K: int):
+    """Sources of the partitioned Jacobian: the prefix device function
+    qss_jac_prefix(C, T, wdot, Tdot, wstride, fr, fstride) and, per group,
+    qss_jac_group(fr, fstride, jac, jstride).  The frontier array fr holds,
+    per cell, C_1..C_N and T in slots 0..N, then the prefix values the groups
+    read (slot N + 1 + i for the i-th frontier node)."""
+    ir = model.ir
+    N = ir.N
+    n = N + 1
+    groups, frontier, needs = partition_jacobian(model, K)
+    slot = {x: n + i for i, x in enumerate(frontier)}
+    inputs = {model.C[k]: f"C{k}" for k in range(N)}
+    inputs[model.T] = "T"
+    fd_prologue = []
+    if model.fd_vars is not None:
+        for v, name in zip(model.fd_vars, ("Tp", "Tm", "inv2h")):
+            inputs[v] = name
+        fd_prologue = [
+            "  const double qss_p2 = __longlong_as_double(__double_as_longlong(T) & 0x7ff0000000000000LL);",
+            "  const double qss_h = qss_p2 * 0x1p-20;",
+            "  const double Tp = T + qss_h, Tm = T - qss_h, inv2h = 0x1p19 / qss_p2;"]
+    out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
+    out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
+    out_f = [(f"fr[{slot[x]} * fstride] = {{v}};", x) for x in frontier]
+    body_p, cnt_p = Emitter(model, inputs).emit(out_w + out_t + out_f, indent="  ")
+    unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
+    store_state = [f"  fr[{k} * fstride] = C{k};" for k in range(N)] + [f"  fr[{N} * fstride] = T;"]
+    prefix = "\n".join([
+        "__device__ __forceinline__ void qss_jac_prefix(const double* __restrict__ C, const double T,",
+        "    double* __restrict__ wdot, double* __restrict__ Tdot, const long long wstride,",
+        "    double* __restrict__ fr, const long long fstride) {",
+        *unpack, *store_state, *fd_prologue, *body_p, "}", ""])
+    group_src, group_cnt = [], []
+    for gi, entries in enumerate(groups):
+        leaves = {x: f"F{slot[x]}" for x in needs[gi]}
+        out_j = [(f"jac[{i * n + c} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries]
+        body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ")
+        loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
+        loads += [f"  const double T = fr[{N} * fstride];"]
+        loads += [f"  const double F{slot[x]} = fr[{slot[x]} * fstride];" for x in needs[gi]]
+        group_src.append("\n".join([
+            f"// entry group {gi} of {K}: columns {sorted({c for _, c in entries if c != N})}"
+            + (f" and rows {sorted(i for i, c in entries if c == N)} of the T column" if any(c == N for _, c in entries) else ""),
+            "__device__ __forceinline__ void qss_jac_group(const double* __restrict__ fr,",
+            "    const long long fstride, double* __restrict__ jac, const long long jstride) {",
+            *loads, *fd_prologue, *body_g, "}", ""]))
+        group_cnt.append(cnt_g)
+    meta = {"jac_parts": K, "frontier": n + len(frontier), "groups": groups,
+            "ops_prefix": dict(cnt_p), "ops_groups": [dict(c) for c in group_cnt],
+            "flops_jac_parts": algorithmic_flops(cnt_p) + sum(algorithmic_flops(c) for c in group_cnt)}
+    return prefix, group_src, meta

@@ -42,6 +42,14 @@ STATES = {
 }
 
 NCELLS = {"tiny": 4096, "hydrocarbon": 1 << 20, "large": 1 << 20, "implicit": 1 << 20}
+# compiler options per workload: the large mechanism's Jacobian is built as a
+# prefix kernel and 8 column-group kernels (its single-kernel form takes far
+# longer to compile than its parts do in parallel)
+BUILD_OPTIONS = {"large": {"jac_parts": 8}}
+
+
+def build_options(key: str) -> dict:
+    return dict(BUILD_OPTIONS.get(key, {}))
 IMPLICIT_DT = 1.0e-6
 
 _cache = {}

@@ -29,7 +29,7 @@ _cache = {}
 def mech(key):
     if key not in _cache:
         m = workloads.mechanism(key)
-        _cache[key] = (m, binding.Mechanism(build_mechanism(m), 0), oracle.OracleMech(m))
+        _cache[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0), oracle.OracleMech(m))
     return _cache[key]
 
 

@@ -1,5 +1,5 @@
-"""The device exponential used by the generated code (table-driven, Tang's
-method) against the CUDA library exp and against exact values."""
+"""The device exponential and logarithm used by the generated code (table-driven,
+Tang-style reductions) against the CUDA library functions and exact values."""
 from decimal import Decimal, getcontext
 
 import numpy as np
@@ -50,6 +50,52 @@ def test_table_exp_out_of_fast_range():
     xd = torch.from_numpy(x).cuda()
     y = binding.selftest_math(0, xd).cpu().numpy()
     ref = binding.selftest_math(1, xd).cpu().numpy()
+    assert np.array_equal(np.isnan(y), np.isnan(ref))
+    m = ~np.isnan(ref)
+    assert np.array_equal(y[m], ref[m])
+
+
+# ---------------------------------------------------------------------------
+# table-driven log
+# ---------------------------------------------------------------------------
+
+def _log_inputs():
+    rng = np.random.default_rng(5)
+    parts = [np.exp(rng.uniform(-700.0, 700.0, 300000)), rng.uniform(200.0, 5000.0, 200000),
+             1.0 + rng.uniform(-1e-2, 1e-2, 100000), 1.0 + rng.uniform(-1e-9, 1e-9, 20000),
+             rng.uniform(1e-3, 1.0, 100000),
+             np.ldexp(1.0, np.arange(-1020, 1020)).astype(np.float64),
+             np.array([1.0, 2.0, 0.5, np.sqrt(0.5), np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0),
+                       2.2250738585072014e-308, 1.7976931348623157e308])]
+    return np.concatenate(parts)
+
+
+def test_table_log_vs_library():
+    x = _log_inputs()
+    xd = torch.from_numpy(x).cuda()
+    y = binding.selftest_math(2, xd).cpu().numpy()
+    ref = binding.selftest_math(4, xd).cpu().numpy()
+    nz = ref != 0
+    assert np.all(y[~nz] == 0)
+    e = ulp_err(y[nz], ref[nz])
+    assert e.max() <= 2.0, (e.max(), x[nz][np.argmax(e)])
+
+
+def test_table_log_vs_exact():
+    getcontext().prec = 50
+    rng = np.random.default_rng(6)
+    x = np.concatenate([np.exp(rng.uniform(-700.0, 700.0, 300)), rng.uniform(250.0, 4000.0, 300),
+                        1.0 + rng.uniform(-1e-3, 1e-3, 300)])
+    y = binding.selftest_math(2, torch.from_numpy(x).cuda()).cpu().numpy()
+    exact = np.array([float(Decimal(float(v)).ln()) for v in x])
+    assert ulp_err(y, exact).max() <= 1.5
+
+
+def test_table_log_special_arguments():
+    x = np.array([0.0, -0.0, -1.0, 5e-324, 1e-310, np.inf, -np.inf, np.nan])
+    xd = torch.from_numpy(x).cuda()
+    y = binding.selftest_math(2, xd).cpu().numpy()
+    ref = binding.selftest_math(4, xd).cpu().numpy()
     assert np.array_equal(np.isnan(y), np.isnan(ref))
     m = ~np.isnan(ref)
     assert np.array_equal(y[m], ref[m])

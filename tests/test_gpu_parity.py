@@ -20,7 +20,7 @@ _mechs = {}
 def mech(key):
     if key not in _mechs:
         m = workloads.mechanism(key)
-        _mechs[key] = (m, binding.Mechanism(build_mechanism(m), 0), oracle.OracleMech(m))
+        _mechs[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0), oracle.OracleMech(m))
     return _mechs[key]
 
 

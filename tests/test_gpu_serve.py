@@ -19,7 +19,7 @@ _m = {}
 def mech(key):
     if key not in _m:
         m = workloads.mechanism(key)
-        _m[key] = (m, binding.Mechanism(build_mechanism(m), 0))
+        _m[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0))
     return _m[key]
 
 
