@@ -21,11 +21,11 @@
 // with the matrix.  The matrix never leaves registers.
 //   update_fp64    factorisation and solve in FP64.
 //   update_fp32ir  M equilibrated by powers of two (rows, then columns),
-//                  factorisation in FP32; the solution refined with FP64
-//                  residuals g - M x (M from the FP64 copy in shared
-//                  memory, staged once per cell) until the correction
-//                  is below refine_tol relative, stops shrinking, or after
-//                  max_refine sweeps.
+//                  factorisation in FP32 as a compact loop (qss_solve_fp32ir);
+//                  the solution refined with FP64 residuals g - M x (M from
+//                  the FP64 copy in shared memory, staged once per cell)
+//                  until the correction is below refine_tol relative, stops
+//                  shrinking, or after max_refine sweeps.
 // Rates, equilibrium constants, the QSS solve, J, M and the Newton residual
 // are FP64 in both forms.
 //
@@ -55,6 +55,9 @@
 #define QSS_MSTRIDE (QSS_NN + 1)
 #define QSS_MBYTES (QSS_NN * QSS_MSTRIDE * 8)
 #define QSS_UPD_WARPS (QSS_MBYTES * 4 <= 44000 ? 4 : (QSS_MBYTES * 2 <= 44000 ? 2 : 1))
+// the FP32_IR form also keeps its FP32 factors (NN x (NN+1) floats) per warp
+#define QSS_M32BYTES (QSS_MBYTES + QSS_NN * QSS_MSTRIDE * 4 + QSS_NN * 24 + 8)
+#define QSS_UPD_WARPS32 (QSS_M32BYTES * 4 <= 44000 ? 4 : (QSS_M32BYTES * 2 <= 44000 ? 2 : 1))
 
 __device__ __forceinline__ bool qss_finite(double x) {
   return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -185,26 +188,6 @@ __device__ __forceinline__ bool qss_warp_factor(R (&a)[QSS_NSLOT][QSS_NN], R (&y
   return true;
 }
 
-// Forward substitution of a new right-hand side with the stored multipliers.
-template <class R>
-__device__ __forceinline__ void qss_warp_forward(const R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
-                                                 const int (&ord)[QSS_NSLOT],
-                                                 const int* __restrict__ piv) {
-#pragma unroll
-  for (int k = 0; k < QSS_NN; ++k) {
-    const int p = piv[k];
-    const int pl = p & 31, ps = p >> 5;
-    R py = y[0];
-#pragma unroll
-    for (int sl = 1; sl < QSS_NSLOT; ++sl)
-      if (ps == sl) py = y[sl];
-    py = qss_shfl(py, pl);
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl)
-      if (ord[sl] > k) y[sl] = fma(-a[sl][k], py, y[sl]);
-  }
-}
-
 // Back substitution (column oriented): x_k from the row of pivot order k,
 // k = NN-1 .. 0.  Lane (k & 31) keeps x_k in xo[k >> 5], so that every lane
 // ends with the entries of x whose index is lane + 32 slot.
@@ -230,6 +213,201 @@ __device__ __forceinline__ void qss_warp_back(const R (&a)[QSS_NSLOT][QSS_NN], R
   }
 }
 
+// FP32 LU with FP64 iterative refinement of one cell's Newton system M x = g,
+// M (FP64) in shared memory, row r at Ms[r * QSS_MSTRIDE]; the warp's lanes
+// own rows lane + 32 slot.  Compact by design: an unrolled FP32 elimination
+// is fetch-bound (FP32 instructions retire faster than their code streams
+// in), so the factorisation runs as a loop over pivot steps with the live
+// rows in registers shifted left by one column per step (the pivot column is
+// always entry 0, and the shift folds into the elimination FMA); L and U go
+// to shared memory (LU[r][k]: multiplier of row r at step k before its pivot
+// step, its U row from there on), and the substitutions are loops over them.
+// Scaling: rows, then columns, by powers of two (exact), so that FP32 holds
+// every entry near 1.  Returns false on a zero pivot.
+__device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, float* __restrict__ LU,
+                                                 int* __restrict__ se, int* __restrict__ piv,
+                                                 float* __restrict__ pinv, double* __restrict__ sx,
+                                                 const double (&gr)[QSS_NSLOT], double (&xo)[QSS_NSLOT],
+                                                 const int lane, const QssNewtonOpts& o) {
+  int er[QSS_NSLOT];
+  bool live[QSS_NSLOT];
+  // row exponents
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+    const int r = lane + 32 * sl;
+    live[sl] = r < QSS_NN;
+    long long mx = 0;
+    if (live[sl]) {
+#pragma unroll 4
+      for (int j = 0; j < QSS_NN; ++j) mx = max(mx, qss_absbits(Ms[r * QSS_MSTRIDE + j]));
+    }
+    const int e = qss_ilogb(__longlong_as_double(mx));
+    er[sl] = e < -1000 ? 0 : e;
+    if (live[sl]) se[r] = er[sl];
+  }
+  __syncwarp();
+  // column exponents (a lane per column)
+  double csr[QSS_NSLOT];
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+    const int c = lane + 32 * sl;
+    csr[sl] = 1.0;
+    if (c < QSS_NN) {
+      int em = -1100;
+#pragma unroll 4
+      for (int r = 0; r < QSS_NN; ++r) {
+        const double v = Ms[r * QSS_MSTRIDE + c];
+        if (qss_absbits(v) != 0) em = max(em, qss_ilogb(v) - se[r]);
+      }
+      const int ec = em < -1000 ? 0 : em;
+      se[QSS_NN + c] = ec;
+      csr[sl] = qss_pow2(-ec);
+    }
+  }
+  __syncwarp();
+  // scaled rows in FP32
+  float A[QSS_NSLOT][QSS_NN];
+  int ord[QSS_NSLOT];
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+    const int r = lane + 32 * sl;
+    ord[sl] = -1;
+#pragma unroll
+    for (int j = 0; j < QSS_NN; ++j)
+      A[sl][j] = live[sl] ? (float)(Ms[r * QSS_MSTRIDE + j] * qss_pow2(-(er[sl] + se[QSS_NN + j]))) : 0.0f;
+  }
+  // factorisation, one pivot step per iteration
+#pragma unroll 1
+  for (int k = 0; k < QSS_NN; ++k) {
+    int best = -1, brow = QSS_NN;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int key = (live[sl] && ord[sl] < 0) ? (__float_as_int(A[sl][0]) & 0x7fffffff) : -1;
+      if (key > best) { best = key; brow = lane + 32 * sl; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const int ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+      if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+    }
+    if (best <= 0) return false;
+    const int pl = brow & 31, ps = brow >> 5;
+    float p[QSS_NN];
+#pragma unroll
+    for (int j = 0; j < QSS_NN; ++j) {
+      float v = A[0][j];
+#pragma unroll
+      for (int sl = 1; sl < QSS_NSLOT; ++sl)
+        if (ps == sl) v = A[sl][j];
+      p[j] = __shfl_sync(0xffffffffu, v, pl);
+    }
+    const float inv = 1.0f / p[0];
+    if (lane == 0) { piv[k] = brow; pinv[k] = inv; }
+    if (lane == pl) {   // the pivot row's U part, columns k..NN-1
+#pragma unroll
+      for (int j = 0; j < QSS_NN; ++j)
+        if (j < QSS_NN - k) LU[brow * QSS_MSTRIDE + k + j] = p[j];
+    }
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl)
+      if (lane == pl && ps == sl) ord[sl] = k;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const bool el = live[sl] && ord[sl] < 0;
+      const float l = el ? A[sl][0] * inv : 0.0f;
+      if (el) LU[(lane + 32 * sl) * QSS_MSTRIDE + k] = l;
+#pragma unroll
+      for (int j = 0; j + 1 < QSS_NN; ++j) A[sl][j] = fmaf(-l, p[j + 1], A[sl][j + 1]);
+      A[sl][QSS_NN - 1] = 0.0f;
+    }
+  }
+  __syncwarp();
+  // refinement: r = g - M x in FP64, correction from the FP32 factors
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = 0.0;
+  double prev = 1e308;
+#pragma unroll 1
+  for (int sweep = 0; sweep <= o.max_refine; ++sweep) {
+    double res[QSS_NSLOT];
+    long long rmx = 0;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int r = lane + 32 * sl;
+      double acc = gr[sl];
+      if (sweep > 0 && live[sl]) {
+#pragma unroll 6
+        for (int j = 0; j < QSS_NN; ++j) acc = fma(-Ms[r * QSS_MSTRIDE + j], sx[j], acc);
+      }
+      res[sl] = live[sl] ? acc * qss_pow2(-er[sl]) : 0.0;
+      rmx = max(rmx, qss_absbits(res[sl]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rmx = max(rmx, __shfl_xor_sync(0xffffffffu, rmx, off));
+    if (rmx == 0) break;
+    const int es = qss_ilogb(__longlong_as_double(rmx));
+    float z[QSS_NSLOT];
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) z[sl] = (float)(res[sl] * qss_pow2(-es));
+    // forward substitution
+#pragma unroll 1
+    for (int k = 0; k < QSS_NN; ++k) {
+      const int pr = piv[k];
+      const int pl = pr & 31, ps = pr >> 5;
+      float v = z[0];
+#pragma unroll
+      for (int sl = 1; sl < QSS_NSLOT; ++sl)
+        if (ps == sl) v = z[sl];
+      const float zp = __shfl_sync(0xffffffffu, v, pl);
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl)
+        if (live[sl] && ord[sl] > k) z[sl] = fmaf(-LU[(lane + 32 * sl) * QSS_MSTRIDE + k], zp, z[sl]);
+    }
+    // back substitution, column oriented: lane (k & 31) keeps x_k
+    float d[QSS_NSLOT];
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) d[sl] = 0.0f;
+#pragma unroll 1
+    for (int k = QSS_NN - 1; k >= 0; --k) {
+      const int pr = piv[k];
+      const int pl = pr & 31, ps = pr >> 5;
+      float v = z[0];
+#pragma unroll
+      for (int sl = 1; sl < QSS_NSLOT; ++sl)
+        if (ps == sl) v = z[sl];
+      const float xk = __shfl_sync(0xffffffffu, v, pl) * pinv[k];
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl)
+        if (lane == (k & 31) && (k >> 5) == sl) d[sl] = xk;
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl)
+        if (live[sl] && ord[sl] < k) z[sl] = fmaf(-LU[(lane + 32 * sl) * QSS_MSTRIDE + k], xk, z[sl]);
+    }
+    double dmax = 0.0, xmax = 0.0;
+    __syncwarp();
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int j = lane + 32 * sl;
+      if (j < QSS_NN) {
+        const double dd = (double)d[sl] * csr[sl] * qss_pow2(es);
+        xo[sl] += dd;
+        sx[j] = xo[sl];
+        dmax = fmax(dmax, fabs(dd));
+        xmax = fmax(xmax, fabs(xo[sl]));
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+    }
+    __syncwarp();
+    if (dmax <= o.refine_tol * xmax || dmax >= 0.5 * prev) break;
+    prev = dmax;
+  }
+  return true;
+}
+
 template <bool FP32IR>
 __device__ __forceinline__ void qss_newton_update(
     long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
@@ -237,14 +415,18 @@ __device__ __forceinline__ void qss_newton_update(
     int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT, const int* __restrict__ LIST,
     const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
     const QssNewtonOpts o) {
-  using R = typename std::conditional<FP32IR, float, double>::type;
-  __shared__ int sh_piv[QSS_UPD_WARPS][QSS_NN];
-  __shared__ double sh_x[QSS_UPD_WARPS][QSS_NN + 1];
-  __shared__ double sh_pinv[QSS_UPD_WARPS][QSS_NN];
+  constexpr int W = FP32IR ? QSS_UPD_WARPS32 : QSS_UPD_WARPS;
+  __shared__ int sh_piv[W][QSS_NN];
+  __shared__ double sh_x[W][QSS_NN + 1];
+  __shared__ double sh_pinv[FP32IR ? 1 : W][QSS_NN];
   // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows)
-  __shared__ double sh_m[QSS_UPD_WARPS * QSS_NN * QSS_MSTRIDE];
+  __shared__ double sh_m[W * QSS_NN * QSS_MSTRIDE];
+  // FP32_IR: the FP32 factors, scale exponents and pivot reciprocals
+  __shared__ float sh_lu[FP32IR ? W * QSS_NN * QSS_MSTRIDE : 1];
+  __shared__ int sh_e[FP32IR ? W : 1][2 * QSS_NN];
+  __shared__ float sh_pinvf[FP32IR ? W : 1][QSS_NN];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long t0 = ((long long)blockIdx.x * QSS_UPD_WARPS + w) * 32;
+  const long long t0 = ((long long)blockIdx.x * W + w) * 32;
   const int nact = *NACT;
   if (t0 >= nact) return;
   const long long t = t0 + lane;
@@ -271,11 +453,6 @@ __device__ __forceinline__ void qss_newton_update(
     todo &= todo - 1;
     const double hq = __shfl_sync(0xffffffffu, h, q);
     const long long tq = t0 + q;
-    R a[QSS_NSLOT][QSS_NN];
-    R y[QSS_NSLOT];
-    int ord[QSS_NSLOT];
-    int er[QSS_NSLOT];
-    double gr[QSS_NSLOT];
     bool fin = true;
     double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of M = I - hq J
     {
@@ -291,121 +468,48 @@ __device__ __forceinline__ void qss_newton_update(
       }
       __syncwarp();
     }
+    double gr[QSS_NSLOT];
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int r = lane + 32 * sl;
-      const bool live = r < QSS_NN;
-      gr[sl] = live ? F[r * sld + tq] : 0.0;
-      er[sl] = 0;
-      long long mx = 0;
-#pragma unroll
-      for (int j = 0; j < QSS_NN; ++j) {
-        if (FP32IR) {
-          if (live) mx = max(mx, qss_absbits(Ms[r * QSS_MSTRIDE + j]));
-        } else {
-          a[sl][j] = live ? Ms[r * QSS_MSTRIDE + j] : 0.0;
-        }
-      }
-      if (FP32IR) {
-        const int e = qss_ilogb(__longlong_as_double(mx));
-        er[sl] = e < -1000 ? 0 : e;
-      }
-      y[sl] = FP32IR ? R(0) : (R)gr[sl];
+      gr[sl] = r < QSS_NN ? F[r * sld + tq] : 0.0;
     }
     if (!__all_sync(0xffffffffu, fin)) {
       if (lane == q) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
       failed |= 1u << q;
       continue;
     }
-    double csr[QSS_NSLOT];   // column scales of this lane's columns (lane + 32 slot)
-    if (FP32IR) {
-#pragma unroll
-      for (int sl = 0; sl < QSS_NSLOT; ++sl) csr[sl] = 1.0;
-#pragma unroll
-      for (int j = 0; j < QSS_NN; ++j) {
-        double mj[QSS_NSLOT];
-        int em = -1100;
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-          const int r = lane + 32 * sl;
-          mj[sl] = r < QSS_NN ? Ms[r * QSS_MSTRIDE + j] : 0.0;
-          if (qss_absbits(mj[sl]) != 0) em = max(em, qss_ilogb(mj[sl]) - er[sl]);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, off));
-        const int ec = em < -1000 ? 0 : em;
-        if (lane == (j & 31)) csr[j >> 5] = qss_pow2(-ec);
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) a[sl][j] = (R)(mj[sl] * qss_pow2(-(er[sl] + ec)));
-      }
-    }
-    if (!qss_warp_factor<R>(a, y, ord, sh_piv[w], sh_pinv[w], lane)) {
-      if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
-      failed |= 1u << q;
-      continue;
-    }
-    __syncwarp();
     double xo[QSS_NSLOT];   // this lane's entries of the solution (index lane + 32 slot)
-    if (!FP32IR) {
-      R xr[QSS_NSLOT];
-#pragma unroll
-      for (int sl = 0; sl < QSS_NSLOT; ++sl) xr[sl] = 0;
-      qss_warp_back<R>(a, y, ord, sh_piv[w], sh_pinv[w], xr, lane);
-#pragma unroll
-      for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = (double)xr[sl];
+    if (FP32IR) {
+      if (!qss_solve_fp32ir(Ms, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
+                            sh_x[w], gr, xo, lane, o)) {
+        if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
+        failed |= 1u << q;
+        __syncwarp();
+        continue;
+      }
     } else {
+      double a[QSS_NSLOT][QSS_NN];
+      double y[QSS_NSLOT];
+      int ord[QSS_NSLOT];
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+        const int r = lane + 32 * sl;
+        const bool live = r < QSS_NN;
+#pragma unroll
+        for (int j = 0; j < QSS_NN; ++j) a[sl][j] = live ? Ms[r * QSS_MSTRIDE + j] : 0.0;
+        y[sl] = gr[sl];
+      }
+      if (!qss_warp_factor<double>(a, y, ord, sh_piv[w], sh_pinv[w], lane)) {
+        if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
+        failed |= 1u << q;
+        __syncwarp();
+        continue;
+      }
+      __syncwarp();
 #pragma unroll
       for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = 0.0;
-      double prev = 1e308;
-#pragma unroll 1
-      for (int sweep = 0; sweep <= o.max_refine; ++sweep) {
-        // scaled residual rows: D_r (g - M x), x shared by the warp in sh_x
-        double res[QSS_NSLOT];
-        long long rmx = 0;
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-          const int r = lane + 32 * sl;
-          double acc = gr[sl];
-          if (sweep > 0 && r < QSS_NN) {
-#pragma unroll 6
-            for (int j = 0; j < QSS_NN; ++j) acc = fma(-Ms[r * QSS_MSTRIDE + j], sh_x[w][j], acc);
-          }
-          res[sl] = r < QSS_NN ? acc * qss_pow2(-er[sl]) : 0.0;
-          rmx = max(rmx, qss_absbits(res[sl]));
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) rmx = max(rmx, __shfl_xor_sync(0xffffffffu, rmx, off));
-        if (rmx == 0) break;
-        const int es = qss_ilogb(__longlong_as_double(rmx));
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) y[sl] = (float)(res[sl] * qss_pow2(-es));
-        qss_warp_forward<R>(a, y, ord, sh_piv[w]);
-        R dr[QSS_NSLOT];
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) dr[sl] = 0;
-        qss_warp_back<R>(a, y, ord, sh_piv[w], sh_pinv[w], dr, lane);
-        double dmax = 0.0, xmax = 0.0;
-        __syncwarp();
-#pragma unroll
-        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-          const int j = lane + 32 * sl;
-          if (j < QSS_NN) {
-            const double d = (double)dr[sl] * csr[sl] * qss_pow2(es);
-            xo[sl] += d;
-            sh_x[w][j] = xo[sl];
-            dmax = fmax(dmax, fabs(d));
-            xmax = fmax(xmax, fabs(xo[sl]));
-          }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
-          xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
-        }
-        __syncwarp();
-        if (dmax <= o.refine_tol * xmax || dmax >= 0.5 * prev) break;
-        prev = dmax;
-      }
+      qss_warp_back<double>(a, y, ord, sh_piv[w], sh_pinv[w], xo, lane);
     }
     // the update x of cell q back to F (column tq)
 #pragma unroll
@@ -458,7 +562,7 @@ qss_newton_update_fp64_kernel(QSS_UPDATE_PARAMS) {
                            NACT2, sld, o);
 }
 
-extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS * 32)
+extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS32 * 32)
 qss_newton_update_fp32ir_kernel(QSS_UPDATE_PARAMS) {
   qss_newton_update<true>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
                           NACT2, sld, o);
