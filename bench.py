@@ -289,6 +289,28 @@ def variants_bench(key, gm, r, t, y, ncells_fd=1 << 18):
     return out
 
 
+def implicit_capacity(gm, key, prec, ncells=65536):
+    """Cells/s of one implicit step of `ncells` cells of workload `key` (after
+    one warm-up step), the serving bench's capacity estimate."""
+    import torch
+    from paper_2405_05974_b300 import mechgen, workloads
+    m = workloads.mechanism(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    r = d(rho)
+    ms = 0.0
+    for rep in range(2):
+        t, y = d(T), d(Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        gm.implicit_step(r, t, y, 1e-6, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    return ncells / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # serving: Poisson request stream over the continuous-batching server
 # ---------------------------------------------------------------------------
@@ -334,6 +356,7 @@ def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, 
     return {"requests": len(reqs), "offered_rate_per_s": rate, "cells": int(sum(n for _, n in reqs)),
             "p50_latency_ms": st["p50_latency_us"] / 1e3, "p99_latency_ms": st["p99_latency_us"] / 1e3,
             "cells_per_s": st["cells_per_s"], "batches": st["batches"],
+            "graph_batches": st["graph_batches"], "graphs_captured": st["graphs_captured"],
             "bytes_peak": st["bytes_peak"], "wall_s": el}
 
 
@@ -426,9 +449,9 @@ def main():
     parts = int(meta.get("jac_parts", 0) or 0)
     launches_per_step = 1
     if parts >= 2:
-        # the library processes a partitioned Jacobian in chunks that fit a
-        # 1 GiB frontier buffer: one prefix and `parts` group launches each
-        fr_cells = max(32, ((1 << 30) // (8 * int(meta["frontier"]))) // 32 * 32)
+        # the library processes a partitioned Jacobian in chunks that fit its
+        # 4 GiB frontier buffer: one prefix and `parts` group launches each
+        fr_cells = max(32, ((4 << 30) // (8 * int(meta["frontier"]))) // 32 * 32)
         launches_per_step = -(-ncells // fr_cells) * (parts + 1)
     jac_kernel = "qss_jac_kernel" if parts < 2 else f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel"
     traffic = traffic_from_profile("qss_jac_kernel", key, meta["artefact_key"], ncells) if parts < 2 else None
@@ -472,14 +495,20 @@ def main():
     serving = None
     if not a.no_serve and key == "hydrocarbon" and rank == 0:
         from paper_2405_05974_b300 import binding as _b
-        mechs = {"tiny": _b.Mechanism(build_mechanism(workloads.mechanism("tiny")), local), "hydrocarbon": gm}
-        weights = [0.25, 0.75]
-        serving = {"mix": "tiny 0.25 / hydrocarbon 0.75 (the large mechanism is not in the mix: see design notes)",
+        mechs = {k: (gm if k == "hydrocarbon" else
+                     _b.Mechanism(build_mechanism(workloads.mechanism(k), **workloads.build_options(k)), local))
+                 for k in ("tiny", "hydrocarbon", "large")}
+        weights = [0.2, 0.6, 0.2]
+        serving = {"mix": "tiny 0.2 / hydrocarbon 0.6 / large 0.2 (by request)",
                    "sizes": "log-uniform 256..65536 cells", "dt": "log-uniform 1e-7..1e-5 s",
-                   "budget_bytes": 60 << 30, "load": 0.7}
+                   "budget_bytes": 60 << 30, "load": 0.7, "graphs": True,
+                   "capacity": "cells/s of one implicit step of 65536 cells per mechanism, "
+                               "combined by the mix's cell-weighted harmonic mean"}
         for prec, name in ((_b.QSS_LU_FP32_IR, "fp32ir"), (_b.QSS_LU_FP64, "fp64")):
-            cap = implicit[name]["cells_per_s"] if implicit else 2e5
+            caps = {k: implicit_capacity(mechs[k], k, prec) for k in mechs}
+            cap = 1.0 / sum(w / caps[k] for w, k in zip(weights, mechs))
             serving[name] = serve_bench(mechs, weights, prec, a.serve_seconds, cap)
+            serving[name]["capacity_cells_per_s"] = {**caps, "mix": cap}
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = cpu_baseline(mech, workloads.STATES[key], a.cpu_seconds)

@@ -112,6 +112,14 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
  * Section 3.3.2 (step h = 2^(e-20) for T in [2^e, 2^(e+1))).  The row of T
  * follows from the species rows by the chain rule in every variant. */
 
+/* A mechanism built with a partitioned Jacobian (a prefix kernel and column-
+ * group kernels exchanging per-cell values through a frontier buffer) runs
+ * qss_jacobian in chunks of cells that fit that buffer, which the handle owns
+ * and keeps.  This sets its size limit in bytes (default 4 GiB; larger chunks
+ * fill the GPU better).  No effect for a single-kernel Jacobian.  Errors:
+ * QSS_ERR_INVALID_ARG if the limit holds fewer than 32 cells. */
+int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
+
 /* Central finite-difference Jacobian of f = (wdot, Tdot), the reference of
  * Eq. (frobErr): column j = (f(phi + h e_j) - f(phi - h e_j)) / (2h), with the
  * absolute step h = dC (mol/m^3) for the concentration columns and h = dT (K)
@@ -185,13 +193,29 @@ typedef struct {
   int n_streams;                   /* concurrent batches (default 4)              */
   int64_t max_batch_cells;         /* cells per merged launch (default 262144)    */
   const qss_newton_opts* newton;   /* NULL: qss_implicit_step defaults            */
+  int graphs;                      /* 0: default = on; 1: on; -1: off (see below) */
 } qss_serve_opts;
+
+/* Graph replay.  With graphs on, a batch of C cells of mechanism m and a
+ * precision runs as one launch of a CUDA graph captured for (m, precision,
+ * bucket), bucket = the power of two >= max(C, 256): the graph's kernels
+ * (setup, max_iter x (Jacobian, Newton update), write-back) are bound to a
+ * region of the arena that the graph keeps while it is cached, the batch's
+ * inputs are copied there, and a device-side count tells the kernels how many
+ * of the bucket's cells are real.  A bucket whose graph is busy on another
+ * stream, or that does not fit next to the cached graphs, runs with direct
+ * launches; idle graphs are released, least recently used first, when the
+ * arena needs their memory.  Results are bit for bit those of direct
+ * launches. */
 
 typedef struct {
   uint64_t submitted, completed, rejected, queued, in_flight, batches, cells_completed;
   uint64_t bytes_in_use, bytes_peak;
   double p50_latency_us, p99_latency_us, mean_latency_us;  /* submit -> completion */
   double cells_per_s;   /* completed cells / (last completion - first submission) */
+  uint64_t graph_batches;    /* batches run by replaying a captured graph */
+  uint64_t graphs_captured;  /* graphs captured (a re-capture after release counts again) */
+  uint64_t graphs_cached;    /* graphs held now */
 } qss_serve_stats_t;
 
 int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts, qss_server_t* out);

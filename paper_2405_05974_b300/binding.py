@@ -40,7 +40,7 @@ class NewtonOpts(ctypes.Structure):
 
 class ServeOpts(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int), ("max_batch_cells", ctypes.c_int64),
-                ("newton", ctypes.POINTER(NewtonOpts))]
+                ("newton", ctypes.POINTER(NewtonOpts)), ("graphs", ctypes.c_int)]
 
 
 class ServeStats(ctypes.Structure):
@@ -48,7 +48,8 @@ class ServeStats(ctypes.Structure):
                                                  "in_flight", "batches", "cells_completed",
                                                  "bytes_in_use", "bytes_peak")] + \
                [(nm, ctypes.c_double) for nm in ("p50_latency_us", "p99_latency_us",
-                                                 "mean_latency_us", "cells_per_s")]
+                                                 "mean_latency_us", "cells_per_s")] + \
+               [(nm, ctypes.c_uint64) for nm in ("graph_batches", "graphs_captured", "graphs_cached")]
 
     def as_dict(self):
         return {nm: getattr(self, nm) for nm, _ in self._fields_}
@@ -71,6 +72,7 @@ def lib():
                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                       _vp, _vp]
         L.qss_jacobian_host.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]
@@ -195,6 +197,10 @@ class Mechanism:
                                  _ptr(Tdot), _stream(stream)))
         return jac, wdot, Tdot
 
+    def set_frontier_bytes(self, nbytes: int):
+        """Size limit of the partitioned Jacobian's frontier buffer."""
+        check(lib().qss_mech_set_frontier_bytes(self.h, int(nbytes)))
+
     def jacobian_fd(self, rho, T, Y, dC, dT, jac=None, ncells=None, stream=None):
         """Central finite-difference Jacobian (absolute steps dC, dT)."""
         nc, ld = self._check_state(rho, T, Y, ncells)
@@ -241,10 +247,13 @@ class Server:
     """Continuous-batching server of implicit-step requests (host arrays)."""
 
     def __init__(self, device: int = 0, budget_bytes: int = 8 << 30, n_streams: int = 4,
-                 max_batch_cells: int = 1 << 18, newton: Optional[NewtonOpts] = None):
+                 max_batch_cells: int = 1 << 18, newton: Optional[NewtonOpts] = None,
+                 graphs: bool = True):
+        """graphs: replay CUDA graphs captured per (mechanism, precision,
+        size bucket) instead of launching each batch's kernels directly."""
         self._newton = newton
         o = ServeOpts(n_streams, max_batch_cells,
-                      ctypes.pointer(newton) if newton is not None else None)
+                      ctypes.pointer(newton) if newton is not None else None, 1 if graphs else -1)
         h = _vp()
         check(lib().qss_serve_create(device, budget_bytes, ctypes.byref(o), ctypes.byref(h)))
         self.h = h

@@ -75,13 +75,14 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
 int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
-                    CUdeviceptr scratch, size_t scratch_bytes) {
+                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap) {
   if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
   const size_t per_cell = newton_scratch_per_cell(m, precision);
   int64_t chunk = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell) / 32 * 32;
   if (chunk < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
   chunk = std::min<int64_t>(chunk, (ncells + 31) / 32 * 32);
+  if (ncap && chunk < ncells) return fail(QSS_ERR_BUDGET, "a capped launch must fit one chunk");
   NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
   const size_t S = (size_t)chunk;
   double* M64 = (double*)scratch;
@@ -102,7 +103,8 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
   for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
     long long cells = std::min<int64_t>(chunk, ncells - c0), cc0 = c0;
-    void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld};
+    void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld,
+                       &ncap};
     if ((rc = launch_cells(m, m->f_newton_setup, cells, m->block, a_setup, st, 0))) return rc;
     for (int it = 0; it < o.max_iter; ++it) {
       const int cur = it & 1, nxt = cur ^ 1;
@@ -117,7 +119,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
                        &lc, &nc, &l2, &nn, &sld, &od};
       if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
     }
-    void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld};
+    void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld, &ncap};
     if ((rc = launch_cells(m, m->f_newton_finish, cells, m->block, a_fin, st, 0))) return rc;
   }
   return QSS_OK;

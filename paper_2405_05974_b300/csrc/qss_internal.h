@@ -29,6 +29,7 @@ struct qss_mech_s {
   // across streams (recorded after each call's last group kernel)
   CUdeviceptr fr_scratch = 0;
   int64_t fr_cells = 0;
+  size_t fr_budget = size_t(4) << 30;   // bytes of that buffer (qss_mech_set_frontier_bytes)
   CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
   std::vector<double> W;
@@ -71,7 +72,7 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
 int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
-                    CUdeviceptr scratch, size_t scratch_bytes);
+                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap = nullptr);
 }  // namespace qss
 
 #define CU_TRY(call)                                   \

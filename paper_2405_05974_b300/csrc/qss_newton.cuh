@@ -94,7 +94,10 @@ qss_newton_setup_kernel(long long cells, long long c0, long long ld, const doubl
                         const double* __restrict__ T, const double* __restrict__ Y,
                         double* __restrict__ PHI, double* __restrict__ PHI0, int* __restrict__ ACT,
                         int* __restrict__ ST, int* __restrict__ IT, int* __restrict__ LIST,
-                        int* __restrict__ NACT, long long sld) {
+                        int* __restrict__ NACT, long long sld, const int* __restrict__ ncap) {
+  // ncap (optional): a device-side cell count that lowers `cells`, so that a
+  // launch sequence captured for a size bucket serves any smaller batch
+  if (ncap) cells = min(cells, (long long)*ncap);
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (s == 0) { NACT[0] = (int)cells; NACT[1] = 0; }
   if (s >= cells) return;
@@ -573,7 +576,8 @@ extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_newton_finish_kernel(long long cells, long long c0, long long ld, const double* __restrict__ rho,
                          double* __restrict__ T, double* __restrict__ Y, const double* __restrict__ PHI,
                          const int* __restrict__ ST, const int* __restrict__ IT, int* __restrict__ iters,
-                         int* __restrict__ status, long long sld) {
+                         int* __restrict__ status, long long sld, const int* __restrict__ ncap) {
+  if (ncap) cells = min(cells, (long long)*ncap);
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (s >= cells) return;
   const long long c = c0 + s;

@@ -252,12 +252,20 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
     return jac_launch(m, ncells, ld, rho, T, Y, jac, wdot, Tdot, nullptr, nullptr, nullptr, nullptr,
                       nullptr, 0, s);
   // partitioned: chunks of cells through the handle's frontier scratch (at
-  // most 1 GiB), its reuse ordered after the previous call by an event
+  // most fr_budget bytes), its reuse ordered after the previous call by an
+  // event
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   const size_t per = frontier_bytes_per_cell(m);
-  int64_t want = std::max<int64_t>(32, (int64_t)((size_t(1) << 30) / per) / 32 * 32);
+  int64_t want = std::max<int64_t>(32, (int64_t)(m->fr_budget / per) / 32 * 32);
   want = std::min<int64_t>(want, (ncells + 31) / 32 * 32);
+  if (m->fr_cells > want && (int64_t)(m->fr_budget / per) < m->fr_cells) {
+    // the budget was lowered: give the larger buffer back
+    if (m->fr_done) CU_TRY(drv().cuEventSynchronize(m->fr_done));
+    drv().cuMemFree(m->fr_scratch);
+    m->fr_scratch = 0;
+    m->fr_cells = 0;
+  }
   if (m->fr_cells < want) {
     if (m->fr_done) CU_TRY(drv().cuEventSynchronize(m->fr_done));
     if (m->fr_scratch) { drv().cuMemFree(m->fr_scratch); m->fr_scratch = 0; m->fr_cells = 0; }
@@ -276,6 +284,15 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
       return rc;
   }
   CU_TRY(drv().cuEventRecord(m->fr_done, s));
+  return QSS_OK;
+}
+
+int qss_mech_set_frontier_bytes(qss_mech_t m, size_t bytes) {
+  if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
+  if (m->jac_parts >= 2 && bytes < 32 * frontier_bytes_per_cell(m))
+    return fail(QSS_ERR_INVALID_ARG, "frontier buffer smaller than 32 cells");
+  std::lock_guard<std::mutex> lock(m->mu);
+  m->fr_budget = bytes;
   return QSS_OK;
 }
 

@@ -10,7 +10,8 @@
 // n_streams streams, so batches overlap on the device.  Completion is
 // detected with an event per batch; results land in the requests' host arrays
 // (T and Y updated in place), and the latency submit -> completion is
-// recorded.  Mechanism artefacts stay loaded (their constants are in the
+// recorded.  A batch replays a CUDA graph captured for its (mechanism,
+// precision, size bucket) when one is cached and idle (see qss.h).  Mechanism artefacts stay loaded (their constants are in the
 // cubins); nothing is re-uploaded per request.
 #include <cuda.h>
 
@@ -22,6 +23,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "qss_driver.h"
@@ -49,12 +51,26 @@ struct Request {
   int rc = QSS_OK;
 };
 
+struct GraphEntry;
+
 struct Batch {
   std::vector<Request*> reqs;
   int slot = -1;
   size_t off = 0, bytes = 0;
   int64_t cells = 0;
+  GraphEntry* graph = nullptr;   // replayed graph (its own region), or direct launches
 };
+
+// A captured implicit step for (mechanism, precision, bucket): the graph and
+// the arena region its kernels are bound to.
+struct GraphEntry {
+  CUgraphExec exec = nullptr;
+  size_t off = 0, bytes = 0;
+  int64_t bucket = 0;
+  bool busy = false;
+  uint64_t last_use = 0;
+};
+using GraphKey = std::tuple<qss_mech_s*, int, int64_t>;
 
 // First-fit allocator over [0, size) of the device arena, 256-byte granules.
 class Arena {
@@ -138,26 +154,54 @@ struct qss_server_s {
   bool have_first = false;
   int fatal = QSS_OK;
   std::string fatal_msg;
+  // graph replay
+  bool graphs_on = true;
+  std::map<GraphKey, GraphEntry> graphs;
+  uint64_t use_clock = 0, graph_batches = 0, graphs_captured = 0;
 };
 
 namespace {
+
+// Device layout of a batch region of `cap` cells (ldb = cap rounded to 32):
+// rho, T, dt, Y[N] (doubles), iters, status (ints), then the Newton scratch at
+// soff and, last, the int the capped kernels read as the real cell count.
+struct Region {
+  double *rho, *T, *dt, *Y;
+  int32_t *it, *st;
+  CUdeviceptr scratch;
+  size_t scratch_bytes;
+  int* ncap;
+};
+
+Region region_of(qss_server_s* s, qss_mech_s* m, size_t off, size_t bytes, int64_t cap, int prec,
+                 bool with_count) {
+  Region g;
+  const size_t ldb = (size_t)((cap + 31) / 32 * 32);
+  size_t soff;
+  batch_bytes(m, cap, prec, &soff);
+  char* base = (char*)(s->arena_base + off);
+  g.rho = (double*)base;
+  g.T = g.rho + ldb;
+  g.dt = g.T + ldb;
+  g.Y = g.dt + ldb;
+  g.it = (int32_t*)(g.Y + ldb * m->N);
+  g.st = g.it + ldb;
+  g.scratch = s->arena_base + off + soff;
+  // a graph region carries 256 bytes more than batch_bytes: the cell count
+  g.scratch_bytes = bytes - soff - (with_count ? 256 : 0);
+  g.ncap = with_count ? (int*)(base + bytes - 256) : nullptr;
+  return g;
+}
 
 int launch_batch(qss_server_s* s, Batch* b) {
   qss_mech_s* m = b->reqs[0]->mech;
   const int prec = b->reqs[0]->precision;
   const int64_t C = b->cells;
-  const size_t ldb = (size_t)((C + 31) / 32 * 32);
+  const int64_t cap = b->graph ? b->graph->bucket : C;
+  const size_t ldb = (size_t)((cap + 31) / 32 * 32);
   CUstream st = s->streams[b->slot];
-  size_t soff;
-  batch_bytes(m, C, prec, &soff);
-  char* base = (char*)(s->arena_base + b->off);
-  double* d_rho = (double*)base;
-  double* d_T = d_rho + ldb;
-  double* d_dt = d_T + ldb;
-  double* d_Y = d_dt + ldb;
-  int32_t* d_it = (int32_t*)(d_Y + ldb * m->N);
-  int32_t* d_st = d_it + ldb;
-  CUdeviceptr scratch = s->arena_base + b->off + soff;
+  Region g = b->graph ? region_of(s, m, b->graph->off, b->graph->bytes, cap, prec, true)
+                      : region_of(s, m, b->off, b->bytes, cap, prec, false);
   // per-cell dt staged in pinned host memory owned by the slot
   if (s->pinned_cap[b->slot] < (size_t)C) {
     if (s->pinned_dt[b->slot]) drv().cuMemFreeHost(s->pinned_dt[b->slot]);
@@ -171,33 +215,39 @@ int launch_batch(qss_server_s* s, Batch* b) {
   for (Request* r : b->reqs) {
     for (int64_t i = 0; i < r->ncells; ++i) hdt[off + i] = r->dt;
     const size_t w = (size_t)r->ncells * sizeof(double);
-    CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)(d_rho + off), r->rho, w, st));
-    CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)(d_T + off), r->T, w, st));
+    CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)(g.rho + off), r->rho, w, st));
+    CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)(g.T + off), r->T, w, st));
     CUDA_MEMCPY2D c;
     std::memset(&c, 0, sizeof(c));
     c.srcMemoryType = CU_MEMORYTYPE_HOST;
     c.srcHost = r->Y;
     c.srcPitch = w;
     c.dstMemoryType = CU_MEMORYTYPE_DEVICE;
-    c.dstDevice = (CUdeviceptr)(d_Y + off);
+    c.dstDevice = (CUdeviceptr)(g.Y + off);
     c.dstPitch = ldb * sizeof(double);
     c.WidthInBytes = w;
     c.Height = m->N;
     CU_TRY(drv().cuMemcpy2DAsync(&c, st));
     off += r->ncells;
   }
-  CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)d_dt, hdt, (size_t)C * sizeof(double), st));
-  int rc = implicit_launch(m, C, (int64_t)ldb, d_dt, 1, d_rho, d_T, d_Y, prec, s->newton, d_it, d_st,
-                           st, scratch, b->bytes - soff);
-  if (rc) return rc;
+  CU_TRY(drv().cuMemcpyHtoDAsync((CUdeviceptr)g.dt, hdt, (size_t)C * sizeof(double), st));
+  if (b->graph) {
+    CU_TRY(drv().cuMemsetD32Async((CUdeviceptr)g.ncap, (unsigned)C, 1, st));
+    CU_TRY(drv().cuGraphLaunch(b->graph->exec, st));
+    s->graph_batches++;
+  } else {
+    int rc = implicit_launch(m, C, (int64_t)ldb, g.dt, 1, g.rho, g.T, g.Y, prec, s->newton, g.it, g.st,
+                             st, g.scratch, g.scratch_bytes);
+    if (rc) return rc;
+  }
   off = 0;
   for (Request* r : b->reqs) {
     const size_t w = (size_t)r->ncells * sizeof(double);
-    CU_TRY(drv().cuMemcpyDtoHAsync(r->T, (CUdeviceptr)(d_T + off), w, st));
+    CU_TRY(drv().cuMemcpyDtoHAsync(r->T, (CUdeviceptr)(g.T + off), w, st));
     CUDA_MEMCPY2D c;
     std::memset(&c, 0, sizeof(c));
     c.srcMemoryType = CU_MEMORYTYPE_DEVICE;
-    c.srcDevice = (CUdeviceptr)(d_Y + off);
+    c.srcDevice = (CUdeviceptr)(g.Y + off);
     c.srcPitch = ldb * sizeof(double);
     c.dstMemoryType = CU_MEMORYTYPE_HOST;
     c.dstHost = r->Y;
@@ -206,13 +256,72 @@ int launch_batch(qss_server_s* s, Batch* b) {
     c.Height = m->N;
     CU_TRY(drv().cuMemcpy2DAsync(&c, st));
     if (r->iters)
-      CU_TRY(drv().cuMemcpyDtoHAsync(r->iters, (CUdeviceptr)(d_it + off), r->ncells * sizeof(int32_t), st));
+      CU_TRY(drv().cuMemcpyDtoHAsync(r->iters, (CUdeviceptr)(g.it + off), r->ncells * sizeof(int32_t), st));
     if (r->status)
-      CU_TRY(drv().cuMemcpyDtoHAsync(r->status, (CUdeviceptr)(d_st + off), r->ncells * sizeof(int32_t), st));
+      CU_TRY(drv().cuMemcpyDtoHAsync(r->status, (CUdeviceptr)(g.st + off), r->ncells * sizeof(int32_t), st));
     off += r->ncells;
   }
   CU_TRY(drv().cuEventRecord(s->events[b->slot], st));
   return QSS_OK;
+}
+
+// Release idle cached graphs, least recently used first, until `bytes` can be
+// allocated from the arena (or none is left).  Returns true with *off set.
+bool arena_alloc(qss_server_s* s, size_t bytes, size_t* off) {
+  while (!s->arena->alloc(bytes, off)) {
+    auto victim = s->graphs.end();
+    for (auto it = s->graphs.begin(); it != s->graphs.end(); ++it)
+      if (!it->second.busy && (victim == s->graphs.end() || it->second.last_use < victim->second.last_use))
+        victim = it;
+    if (victim == s->graphs.end()) return false;
+    drv().cuGraphExecDestroy(victim->second.exec);
+    s->arena->release(victim->second.off, victim->second.bytes);
+    s->graphs.erase(victim);
+  }
+  return true;
+}
+
+// The cached graph for a batch of `cells` cells, captured on `st` if needed;
+// null when graphs are off, the bucket's graph is busy, or memory is short.
+GraphEntry* graph_for(qss_server_s* s, qss_mech_s* m, int prec, int64_t cells, CUstream st) {
+  if (!s->graphs_on) return nullptr;
+  int64_t bucket = 256;
+  while (bucket < cells) bucket *= 2;
+  if (bucket > s->max_batch_cells) return nullptr;
+  GraphKey key(m, prec, bucket);
+  auto it = s->graphs.find(key);
+  if (it != s->graphs.end()) {
+    if (it->second.busy) return nullptr;
+    it->second.last_use = ++s->use_clock;
+    return &it->second;
+  }
+  size_t soff;
+  const size_t bytes = batch_bytes(m, bucket, prec, &soff) + 256;   // + the cell-count int
+  size_t off;
+  if (!arena_alloc(s, bytes, &off)) return nullptr;
+  Region g = region_of(s, m, off, bytes, bucket, prec, true);
+  const size_t ldb = (size_t)((bucket + 31) / 32 * 32);
+  CUgraph graph = nullptr;
+  CUgraphExec exec = nullptr;
+  bool ok = drv().cuStreamBeginCapture(st, CU_STREAM_CAPTURE_MODE_RELAXED) == CUDA_SUCCESS;
+  int rc = ok ? implicit_launch(m, bucket, (int64_t)ldb, g.dt, 1, g.rho, g.T, g.Y, prec, s->newton,
+                                g.it, g.st, st, g.scratch, g.scratch_bytes, g.ncap)
+              : QSS_ERR_CUDA;
+  if (ok) ok = drv().cuStreamEndCapture(st, &graph) == CUDA_SUCCESS && rc == QSS_OK && graph;
+  if (ok) ok = drv().cuGraphInstantiate(&exec, graph, 0) == CUDA_SUCCESS;
+  if (graph) drv().cuGraphDestroy(graph);
+  if (!ok) {
+    s->arena->release(off, bytes);
+    return nullptr;
+  }
+  GraphEntry& e = s->graphs[key];
+  e.exec = exec;
+  e.off = off;
+  e.bytes = bytes;
+  e.bucket = bucket;
+  e.last_use = ++s->use_clock;
+  s->graphs_captured++;
+  return &e;
 }
 
 void finish_batch(qss_server_s* s, Batch* b, int rc) {
@@ -228,7 +337,10 @@ void finish_batch(qss_server_s* s, Batch* b, int rc) {
     }
   }
   s->t_last = now;
-  s->arena->release(b->off, b->bytes);
+  if (b->graph)
+    b->graph->busy = false;
+  else
+    s->arena->release(b->off, b->bytes);
   s->slot[b->slot] = nullptr;
   delete b;
 }
@@ -272,16 +384,23 @@ void scheduler(qss_server_s* s) {
           b->cells += r->ncells;
         }
       }
-      // device memory for the batch; shrink it (never below the head request)
-      // until it fits, else wait for running batches to free memory
+      // a cached (or newly captured) graph for the batch's size bucket, else
+      // device memory for direct launches: shrink the batch (never below the
+      // head request) until it fits, else wait for running batches
       size_t soff, need = 0;
       bool got = false;
-      while (true) {
-        need = batch_bytes(head->mech, b->cells, head->precision, &soff);
-        if (s->arena->alloc(need, &b->off)) { got = true; break; }
-        if (b->reqs.size() == 1) break;
-        b->cells -= b->reqs.back()->ncells;
-        b->reqs.pop_back();
+      b->graph = graph_for(s, head->mech, head->precision, b->cells, s->streams[free_slot]);
+      if (b->graph) {
+        got = true;
+        b->graph->busy = true;
+      } else {
+        while (true) {
+          need = batch_bytes(head->mech, b->cells, head->precision, &soff);
+          if (arena_alloc(s, need, &b->off)) { got = true; break; }
+          if (b->reqs.size() == 1) break;
+          b->cells -= b->reqs.back()->ncells;
+          b->reqs.pop_back();
+        }
       }
       if (!got) {
         delete b;
@@ -326,6 +445,7 @@ int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts
     if (opts->n_streams > 0) s->n_streams = opts->n_streams;
     if (opts->max_batch_cells > 0) s->max_batch_cells = opts->max_batch_cells;
     if (opts->newton) s->newton = *opts->newton;
+    if (opts->graphs < 0) s->graphs_on = false;
   }
   CUresult r = drv().cuMemAlloc(&s->arena_base, budget_bytes);
   if (r != CUDA_SUCCESS) {
@@ -424,6 +544,9 @@ int qss_serve_stats(qss_server_t s, qss_serve_stats_t* out) {
   out->cells_completed = s->cells_done;
   out->bytes_in_use = s->arena->used();
   out->bytes_peak = s->bytes_peak;
+  out->graph_batches = s->graph_batches;
+  out->graphs_captured = s->graphs_captured;
+  out->graphs_cached = s->graphs.size();
   if (!s->lat_us.empty()) {
     std::vector<double> v = s->lat_us;
     std::sort(v.begin(), v.end());
@@ -457,6 +580,7 @@ void qss_serve_destroy(qss_server_t s) {
     if (s->pinned_dt[k]) drv().cuMemFreeHost(s->pinned_dt[k]);
   }
   for (auto& kv : s->reqs) delete kv.second;
+  for (auto& kv : s->graphs) drv().cuGraphExecDestroy(kv.second.exec);
   drv().cuMemFree(s->arena_base);
   delete s->arena;
   drv().cuDevicePrimaryCtxRelease(s->dev);

@@ -132,7 +132,7 @@ def _complete(out: str) -> bool:
 
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
-                    t_column: str = "analytic", jac_parts: int = 0) -> str:
+                    t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -140,10 +140,13 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     definitions of the kernel templates (e.g. ``QSS_MINBLOCKS=2``);
     ``jac_parts`` >= 2 splits the Jacobian into a prefix kernel and that many
     column-group kernels (``emit.emit_partitioned_source``), each compiled in
-    its own translation unit."""
+    its own translation unit; ``replace_nop`` > 0 applies Alg. 2's
+    common-subexpression replacement with that operation threshold."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
         variant += (f"parts{int(jac_parts)}",)
+    if replace_nop > 0:
+        variant += (f"nop{int(replace_nop)}",)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -153,7 +156,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     t0 = time.time()
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
-    src, meta = emit.emit_mechanism_source(model)
+    src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")

@@ -32,11 +32,13 @@ def _lit(v: float) -> str:
 
 
 class Emitter:
-    def __init__(self, model, input_names: Dict[int, str], leaves: Dict[int, str] = None):
+    def __init__(self, model, input_names: Dict[int, str], leaves: Dict[int, str] = None,
+                 replace_nop: int = 0):
         self.m = model
         self.g = model.g
         self.inputs = input_names     # VAR node -> C identifier
         self.leaves = leaves or {}    # any node -> C identifier of an already computed value
+        self.replace_nop = replace_nop   # Alg. 2 threshold n_op (0: no replacement)
 
     def _resolve(self, i):
         g = self.g
@@ -109,6 +111,31 @@ class Emitter:
         for x, k in absorbed.items():
             if k == refc[x] and x not in root_set:
                 inline.add(x)
+        # Alg. 2 (common-subexpression replacement by operation count): for
+        # thresholds 1..n_op, a stored subexpression whose replacement adds
+        # (uses - 1) x (operations in its line) < threshold operations is
+        # written out inside each of its users instead of being stored.
+        replaced = set()
+        if self.replace_nop > 0:
+            order = sorted(seen)     # node ids are topological (children first)
+            nop = {}
+
+            def line_ops(n):
+                if g.op[n] in (CONST, VAR, LT, FACT) or n in self.leaves:
+                    return 0
+                own = 1 if g.op[n] != NEG else 0
+                return own + sum(nop.get(c, 0) for c in self._children(n) if c in replaced or
+                                 (c in inline and g.op[c] not in (CONST, VAR)))
+            for thr in range(1, self.replace_nop + 1):
+                for n in order:
+                    nop[n] = line_ops(n)
+                    if n in inline or n in replaced or n in root_set or n in self.leaves:
+                        continue
+                    if g.op[n] in (CONST, VAR, LT, FACT):
+                        continue
+                    if (refc[n] - 1) * nop[n] < thr:
+                        replaced.add(n)
+
         names: Dict[int, str] = {}
         lines: List[str] = []
         counts = Counter()
@@ -131,6 +158,8 @@ class Emitter:
                 return ref(g.args[n][0])
             if op == LT:
                 return f"({ref(g.args[n][0])} < {_lit(g.args[n][1])})"
+            if n in replaced:
+                return f"({expr_of(n)})"
             return names[n]
 
         def expr_of(n):
@@ -184,7 +213,7 @@ class Emitter:
                             st.append((c, False))
                     continue
                 done.add(n)
-                if n in inline:
+                if n in inline or n in replaced:
                     continue
                 names[n] = f"t{n}"
                 lines.append(f"{indent}const double t{n} = {expr_of(n)};")
@@ -225,7 +254,7 @@ def fp64_instructions(counts, exp_cost=10, log_cost=36, rcp_cost=10) -> int:
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
 
 
-def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
+def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0) -> Tuple[str, dict]:
     ir = model.ir
     N, Q = ir.N, ir.Q
     n = N + 1
@@ -241,7 +270,7 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
             "  const double qss_p2 = __longlong_as_double(__double_as_longlong(T) & 0x7ff0000000000000LL);",
             "  const double qss_h = qss_p2 * 0x1p-20;",
             "  const double Tp = T + qss_h, Tm = T - qss_h, inv2h = 0x1p19 / qss_p2;"]
-    em = Emitter(model, inputs)
+    em = Emitter(model, inputs, replace_nop=replace_nop)
     out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
     out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
     body_w, cnt_w = em.emit(out_w + out_t, indent="  ")
@@ -250,7 +279,7 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
     for c in range(n):
         for i in range(n):
             out_j.append((f"jac[{i * n + c} * jstride] = {{v}};", model.jac[i][c]))
-    em2 = Emitter(model, inputs)
+    em2 = Emitter(model, inputs, replace_nop=replace_nop)
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
     hdr = [
         f"// Generated by qssc for mechanism '{ir.name}' (digest {ir.digest}).",
@@ -277,7 +306,7 @@ def emit_mechanism_source(model, block_hint=128) -> Tuple[str, dict]:
     meta = {
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
-        "jac_variant": model.jac_variant, "t_column": model.t_column,
+        "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
         "fp64_instr_wdot": fp64_instructions(cnt_w), "fp64_instr_jac": fp64_instructions(cnt_j),

@@ -44,14 +44,19 @@ def test_partitioned_parity(key, parts, ncells):
 
 
 def test_partitioned_several_frontier_chunks():
-    """150000 hydrocarbon cells: more than the 1 GiB frontier scratch holds at
-    once (about 61000 cells), against the single-kernel Jacobian everywhere
-    and the oracle on every 499th cell."""
+    """150000 hydrocarbon cells through a frontier buffer limited to 400 MB
+    (about 34000 cells a chunk), against the single-kernel Jacobian
+    everywhere and the oracle on every 499th cell."""
     key, ncells = "hydrocarbon", 150000
     m = workloads.mechanism(key)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
     r, t, y = dev(rho), dev(T), dev(Y)
-    Jp, wp, tp = gpu_mech(key, 4).jacobian(r, t, y)
+    gp = gpu_mech(key, 4)
+    gp.set_frontier_bytes(400 << 20)
+    try:
+        Jp, wp, tp = gp.jacobian(r, t, y)
+    finally:
+        gp.set_frontier_bytes(4 << 30)
     Jm, wm, tm = gpu_mech(key, 0).jacobian(r, t, y)
     Jp, Jm = Jp.cpu().numpy(), Jm.cpu().numpy()
     idx = np.arange(0, ncells, 499)

@@ -127,3 +127,36 @@ def test_wait_timeout_then_completion():
             srv.wait(rid)            # id released
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
+def test_graph_replay_matches_direct_launches(prec):
+    """The same requests served with graph replay and with direct launches
+    give identical results; repeated sizes reuse their bucket's graph, and a
+    bucket's graph serves any batch up to its size (the real count is read on
+    the device)."""
+    sizes = [300, 300, 5000, 257, 511, 1500, 300, 4096]
+    results = {}
+    for graphs in (True, False):
+        srv = binding.Server(0, budget_bytes=2 << 30, n_streams=2, max_batch_cells=1 << 14, graphs=graphs)
+        try:
+            keep, ids = [], []
+            for i, n in enumerate(sizes):
+                key = "tiny" if i % 2 == 0 else "hydrocarbon"
+                _, gm = mech(key)
+                s = host_state(key, n, 500 + i)
+                keep.append(s)
+                ids.append(srv.submit(gm, *s, 1e-6 * (1 + i % 3), prec))
+                assert srv.wait(ids[-1]) == 0      # one at a time: no merging
+            st = srv.stats()
+        finally:
+            srv.close()
+        results[graphs] = (keep, st)
+    (kg, sg), (kd, sd) = results[True], results[False]
+    for a, b in zip(kg, kd):
+        assert np.array_equal(a[1].numpy(), b[1].numpy(), equal_nan=True)
+        assert np.array_equal(a[2].numpy(), b[2].numpy(), equal_nan=True)
+    assert sd["graph_batches"] == 0 and sd["graphs_captured"] == 0
+    assert sg["graph_batches"] == len(sizes)
+    # buckets used: tiny 512, 8192, 512, 512 and hydrocarbon 512, 2048, 4096 -> 5 graphs
+    assert sg["graphs_captured"] == 5, sg
