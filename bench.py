@@ -143,10 +143,17 @@ def max_over_ranks(pg, x):
 # ---------------------------------------------------------------------------
 # roofline inputs
 # ---------------------------------------------------------------------------
-def traffic_from_profile(kernel, workload, artefact_key, ncells):
+def cubin_digest(path):
+    import hashlib
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_from_profile(kernel, workload, cubin_key, ncells):
     """DRAM bytes per launch from the committed ncu summary of this kernel
-    (lines starting with '@'), if it was taken on the current artefact; the
-    capture's bytes per cell are scaled to the launch's cells."""
+    (lines starting with '@'), if it was taken on the same compiled kernel
+    (digest of its cubin); the capture's bytes per cell are scaled to the
+    launch's cells (the traffic is per cell: inputs, outputs and the
+    per-thread spill stack)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     if not os.path.exists(path):
         return None
@@ -156,7 +163,7 @@ def traffic_from_profile(kernel, workload, artefact_key, ncells):
             k, v = line[1:].split(":", 1)
             vals[k.strip()] = v.strip()
     try:
-        if vals.get("artefact_key") != artefact_key:
+        if vals.get("cubin_sha256") != cubin_key:
             return None
         return float(vals["dram_bytes_per_cell"]) * ncells
     except (KeyError, ValueError):
@@ -454,7 +461,8 @@ def main():
         fr_cells = max(32, ((4 << 30) // (8 * int(meta["frontier"]))) // 32 * 32)
         launches_per_step = -(-ncells // fr_cells) * (parts + 1)
     jac_kernel = "qss_jac_kernel" if parts < 2 else f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel"
-    traffic = traffic_from_profile("qss_jac_kernel", key, meta["artefact_key"], ncells) if parts < 2 else None
+    traffic = traffic_from_profile("qss_jac_kernel", key, cubin_digest(os.path.join(art, "jac.cubin")),
+                                   ncells) if parts < 2 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "measured live on this GPU: FP64 DFMA microbenchmark "

@@ -170,6 +170,39 @@ int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double*
                       void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Integration over an interval.  Advances every cell by dt_total (device
+ * array with dt_stride 1, or a scalar with dt_stride 0) at constant volume
+ * with backward-Euler substeps under local error control, the kind of
+ * stiff integration over a CFD substep the paper's Jacobian serves (Section
+ * 3.1, which drives CVODE; this is not CVODE).  Each substep of size h is a
+ * Newton-solved backward-Euler step (qss_implicit_step's solver); its local
+ * error is estimated as e = h/2 (f(phi_n+1) - f(phi_n)), with f at the last
+ * Newton iterate standing for f(phi_n+1).  A substep is accepted when the
+ * weighted RMS of e with weights rtol |phi_i| + atol_i is <= 1; the next h is
+ * h min(4, max(0.2, 0.9 / sqrt(err))) (capped by what remains of the
+ * interval).  A rejected substep retries with h max(0.2, min(0.9, 0.9 /
+ * sqrt(err))), a failed Newton solve with h / 4.  T and Y (device arrays) are
+ * updated in place; nsteps [ld] receives the accepted substeps and
+ * cell_status [ld] 0 (interval done), 1 (max_rounds substep attempts
+ * exhausted; T, Y hold the last accepted state) or 2 (h fell below h_min x
+ * dt_total).  Synchronises with the host every 8 rounds (to stop once every
+ * cell is done).  Errors: as qss_implicit_step, QSS_ERR_INVALID_ARG for bad
+ * options.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double rtol, atol_C, atol_T;   /* substep error tolerance (defaults 1e-4, 1e-10, 1e-4) */
+  double h0;                     /* first substep in s (0: 1 % of the interval)     */
+  double h_min;                  /* smallest substep / interval (default 1e-14)     */
+  int max_rounds;                /* substep attempts per cell (default 400)         */
+  qss_newton_opts newton;        /* each substep's Newton solve                      */
+} qss_integrate_opts;
+
+int qss_integrate(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt_total,
+                  int dt_stride, const double* rho, double* T, double* Y, int precision,
+                  const qss_integrate_opts* opts /* nullable */, int32_t* nsteps,
+                  int32_t* cell_status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Serving (continuous batching of implicit-step requests on one GPU).
  *
  * qss_serve_create allocates a device arena of budget_bytes (the memory

@@ -682,6 +682,47 @@ int jac_fd_batch(const Mech* m, int64_t ncells, int64_t ld, const double* rho, c
   return nfail;
 }
 
+// Newton on G(phi) = phi - phi0 - h f(phi) from phi0, the full J every
+// iteration, FP64 partial-pivot solve; stops when the weighted RMS of the
+// update is <= 1 (status 0), on an evaluation or solve failure (2) or after
+// max_iter iterations (1).  f0 = f(phi0) (the first iterate), f1 = f at the
+// last iterate evaluated.
+int be_newton(const Mech& m, const std::vector<double>& phi0, double h_dt, double rtol,
+              double atol_C, double atol_T, int max_iter, std::vector<double>& phi,
+              std::vector<double>& f0, std::vector<double>& f1, int* iters) {
+  const int N = m.N, n = N + 1;
+  phi = phi0;
+  int st = 1, it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    CellOut<double> o;
+    if (!eval_cell(m, phi.data(), true, true, o)) { st = 2; break; }
+    std::vector<double> G(n), Mx(n * n);
+    for (int i = 0; i < n; ++i) {
+      double fi = i < N ? o.wdot[i] : o.Tdot;
+      if (it == 1) f0[i] = fi;
+      f1[i] = fi;
+      G[i] = phi[i] - phi0[i] - h_dt * fi;
+      for (int j = 0; j < n; ++j) Mx[i * n + j] = (i == j ? 1.0 : 0.0) - h_dt * o.J[i * n + j];
+    }
+    std::vector<double> d(n);
+    for (int i = 0; i < n; ++i) d[i] = -G[i];
+    if (!gauss_solve(n, Mx, 1, d)) { st = 2; break; }
+    double acc = 0.0;
+    bool finite = true;
+    for (int i = 0; i < n; ++i) {
+      phi[i] += d[i];
+      double w = rtol * std::fabs(phi[i]) + (i < N ? atol_C : atol_T);
+      acc += (d[i] / w) * (d[i] / w);
+      if (!std::isfinite(phi[i])) finite = false;
+    }
+    if (!finite) { st = 2; break; }
+    if (std::sqrt(acc / n) <= 1.0) { st = 0; break; }
+  }
+  if (it > max_iter) it = max_iter;
+  *iters = it;
+  return st;
+}
+
 }  // namespace
 
 // ================================ C ABI ========================================
@@ -1071,33 +1112,72 @@ int oracle_be_step(void* h, int64_t ncells, int64_t ld, const double* dt, int dt
     double h_dt = dt[dt_stride ? c : 0];
     std::vector<double> phi0;
     cell_phi(*m, c, ld, rho, T, Y, phi0);
-    std::vector<double> phi = phi0;
-    int st = 1, it = 0;
-    for (it = 1; it <= max_iter; ++it) {
-      CellOut<double> o;
-      if (!eval_cell(*m, phi.data(), true, true, o)) { st = 2; break; }
-      std::vector<double> G(n), Mx(n * n);
-      for (int i = 0; i < n; ++i) {
-        double fi = i < N ? o.wdot[i] : o.Tdot;
-        G[i] = phi[i] - phi0[i] - h_dt * fi;
-        for (int j = 0; j < n; ++j) Mx[i * n + j] = (i == j ? 1.0 : 0.0) - h_dt * o.J[i * n + j];
-      }
-      std::vector<double> d(n);
-      for (int i = 0; i < n; ++i) d[i] = -G[i];
-      if (!gauss_solve(n, Mx, 1, d)) { st = 2; break; }
-      double acc = 0.0;
-      bool finite = true;
-      for (int i = 0; i < n; ++i) {
-        phi[i] += d[i];
-        double w = rtol * std::fabs(phi[i]) + (i < N ? atol_C : atol_T);
-        acc += (d[i] / w) * (d[i] / w);
-        if (!std::isfinite(phi[i])) finite = false;
-      }
-      if (!finite) { st = 2; break; }
-      if (std::sqrt(acc / n) <= 1.0) { st = 0; break; }
-    }
-    if (it > max_iter) it = max_iter;
+    std::vector<double> phi, f0(n), f1(n);
+    int it = 0;
+    int st = be_newton(*m, phi0, h_dt, rtol, atol_C, atol_T, max_iter, phi, f0, f1, &it);
     if (iters) iters[c] = it;
+    if (status) status[c] = st;
+    if (st != 0) nbad++;
+    T[c] = phi[N];
+    for (int k = 0; k < N; ++k) Y[k * ld + c] = phi[k] * m->W[k] / rho[c];
+  }
+  return nbad;
+}
+
+// Integration over dt_total by backward-Euler substeps with local error
+// control (each cell on its own): a substep of size h is the Newton solve
+// above from the current state; its local error is estimated as
+// e = h/2 (f(last iterate) - f(start)), err = sqrt(mean((e_i / w_i)^2)) with
+// w_i = rtol |phi_i,new| + atol_i.  Accepted when err <= 1 (next
+// h = h min(4, max(0.2, 0.9/sqrt(err))), capped by what remains); rejected:
+// h max(0.2, min(0.9, 0.9/sqrt(err))); Newton failure: h/4.  The interval is
+// done when the remainder is <= 1e-12 dt_total; a cell fails (status 2) when
+// h < h_min dt_total, and stops with status 1 after max_rounds attempts.
+int oracle_integrate(void* h, int64_t ncells, int64_t ld, const double* dt_total, int dt_stride,
+                     const double* rho, double* T, double* Y, double rtol, double atol_C,
+                     double atol_T, double h0, double h_min, int max_rounds, double n_rtol,
+                     double n_atol_C, double n_atol_T, int max_iter, int* nsteps, int* status,
+                     int nthreads) {
+  Mech* m = (Mech*)h;
+  const int N = m->N, n = N + 1;
+  int nbad = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_or_default(nthreads)) reduction(+ : nbad)
+  for (int64_t c = 0; c < ncells; ++c) {
+    const double D = dt_total[dt_stride ? c : 0];
+    std::vector<double> phi;
+    cell_phi(*m, c, ld, rho, T, Y, phi);
+    double t = 0.0, hs = std::min(h0 > 0.0 ? h0 : 0.01 * D, D);
+    int st = 1, ns = 0;
+    for (int round = 0; round < max_rounds; ++round) {
+      std::vector<double> pn, f0(n), f1(n);
+      int it = 0;
+      const int ok = be_newton(*m, phi, hs, n_rtol, n_atol_C, n_atol_T, max_iter, pn, f0, f1, &it);
+      if (ok != 0) {
+        hs *= 0.25;
+      } else {
+        double e2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double e = 0.5 * hs * (f1[i] - f0[i]);
+          const double w = rtol * std::fabs(pn[i]) + (i < N ? atol_C : atol_T);
+          e2 += (e / w) * (e / w);
+        }
+        const double err = std::sqrt(e2 / n);
+        if (err <= 1.0) {
+          phi = pn;
+          t += hs;
+          ns++;
+          const double rem = D - t;
+          if (rem <= 1e-12 * D) { st = 0; break; }
+          const double g = err > 0.0 ? 0.9 / std::sqrt(err) : 4.0;
+          hs = std::min(hs * std::min(4.0, std::max(0.2, g)), rem);
+        } else {
+          const double g = err > 0.0 ? 0.9 / std::sqrt(err) : 0.25;
+          hs = hs * (g == g ? std::min(0.9, std::max(0.2, g)) : 0.25);
+        }
+      }
+      if (hs < h_min * D) { st = 2; break; }
+    }
+    if (nsteps) nsteps[c] = ns;
     if (status) status[c] = st;
     if (st != 0) nbad++;
     T[c] = phi[N];

@@ -38,6 +38,18 @@ class NewtonOpts(ctypes.Structure):
                 ("refine_tol", ctypes.c_double)]
 
 
+class IntegrateOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol_C", ctypes.c_double), ("atol_T", ctypes.c_double),
+                ("h0", ctypes.c_double), ("h_min", ctypes.c_double), ("max_rounds", ctypes.c_int),
+                ("newton", NewtonOpts)]
+
+
+def integrate_opts(rtol=1e-4, atol_C=1e-10, atol_T=1e-4, h0=0.0, h_min=1e-14, max_rounds=400,
+                   newton: Optional["NewtonOpts"] = None) -> IntegrateOpts:
+    return IntegrateOpts(rtol, atol_C, atol_T, h0, h_min, max_rounds,
+                         newton if newton is not None else NewtonOpts(20, 1e-12, 1e-20, 1e-10, 10, 1e-8))
+
+
 class ServeOpts(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int), ("max_batch_cells", ctypes.c_int64),
                 ("newton", ctypes.POINTER(NewtonOpts)), ("graphs", ctypes.c_int)]
@@ -78,6 +90,8 @@ def lib():
         L.qss_jacobian_host.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]
         L.qss_implicit_step.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
                                         ctypes.POINTER(NewtonOpts), _vp, _vp, _vp]
+        L.qss_integrate.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                                    ctypes.POINTER(IntegrateOpts), _vp, _vp, _vp]
         L.qss_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.qss_selftest_math.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _vp, _vp, _vp]
         L.qss_serve_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ServeOpts),
@@ -221,6 +235,23 @@ class Mechanism:
         check(lib().qss_jacobian_host(self.h, nc, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
                                       _ptr(Tdot), chunk, None))
         return jac, wdot, Tdot
+
+    def integrate(self, rho, T, Y, dt_total, precision=QSS_LU_FP32_IR, ncells=None, nsteps=None,
+                  status=None, opts: Optional[IntegrateOpts] = None, stream=None):
+        """Advance (T, Y) in place over dt_total by error-controlled
+        backward-Euler substeps; returns (nsteps, status) device tensors."""
+        nc, ld = self._check_state(rho, T, Y, ncells)
+        if not isinstance(dt_total, torch.Tensor):
+            dt_total = torch.full((1,), float(dt_total), dtype=torch.float64, device=T.device)
+        stride = 1 if dt_total.numel() > 1 else 0
+        if nsteps is None:
+            nsteps = torch.empty(ld, dtype=torch.int32, device=T.device)
+        if status is None:
+            status = torch.empty(ld, dtype=torch.int32, device=T.device)
+        check(lib().qss_integrate(self.h, nc, ld, _ptr(dt_total), stride, _ptr(rho), _ptr(T), _ptr(Y),
+                                  precision, ctypes.byref(opts) if opts is not None else None,
+                                  _ptr(nsteps), _ptr(status), _stream(stream)))
+        return nsteps, status
 
     def implicit_step(self, rho, T, Y, dt, precision=QSS_LU_FP64, ncells=None, iters=None,
                       status=None, opts: Optional[NewtonOpts] = None, stream=None):

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(REPO, "include")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 LIB = os.path.join(PKG, "libqss.so")
 AUX = os.path.join(PKG, "qss_aux.cubin")
-SOURCES = ["qss_driver.cpp", "qss_runtime.cpp", "qss_implicit.cpp", "qss_probe.cpp", "qss_serve.cpp"]
+SOURCES = ["qss_driver.cpp", "qss_runtime.cpp", "qss_implicit.cpp", "qss_integrate.cpp", "qss_probe.cpp",
+           "qss_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

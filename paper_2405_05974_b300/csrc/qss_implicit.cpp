@@ -75,14 +75,16 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
 int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
-                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap) {
+                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap, double* fn0,
+                    double* fn1) {
   if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
   const size_t per_cell = newton_scratch_per_cell(m, precision);
   int64_t chunk = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell) / 32 * 32;
   if (chunk < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
   chunk = std::min<int64_t>(chunk, (ncells + 31) / 32 * 32);
-  if (ncap && chunk < ncells) return fail(QSS_ERR_BUDGET, "a capped launch must fit one chunk");
+  if ((ncap || fn0 || fn1) && chunk < ncells)
+    return fail(QSS_ERR_BUDGET, "a capped or recording launch must fit one chunk");
   NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
   const size_t S = (size_t)chunk;
   double* M64 = (double*)scratch;
@@ -116,7 +118,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
         return rc;
       int* l2 = LIST[nxt];
       void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
-                       &lc, &nc, &l2, &nn, &sld, &od};
+                       &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od};
       if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
     }
     void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld, &ncap};

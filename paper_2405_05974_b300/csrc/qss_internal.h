@@ -18,6 +18,7 @@ struct qss_mech_s {
   CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
+  CUfunction f_integ[4] = {nullptr, nullptr, nullptr, nullptr};   // init, gather, accept, finish
   int upd_threads[2] = {128, 128};   // block size of the update kernels (their launch bound)
   // partitioned Jacobian (jac_parts >= 2): prefix kernel + column-group kernels
   int jac_parts = 0, frontier = 0;   // frontier: doubles per cell between them
@@ -72,7 +73,8 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
 int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
-                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap = nullptr);
+                    CUdeviceptr scratch, size_t scratch_bytes, const int* ncap = nullptr,
+                    double* fn0 = nullptr, double* fn1 = nullptr);
 }  // namespace qss
 
 #define CU_TRY(call)                                   \

@@ -417,7 +417,7 @@ __device__ __forceinline__ void qss_newton_update(
     const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,
     int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT, const int* __restrict__ LIST,
     const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
-    const QssNewtonOpts o) {
+    double* __restrict__ FN0, double* __restrict__ FN1, const QssNewtonOpts o) {
   constexpr int W = FP32IR ? QSS_UPD_WARPS32 : QSS_UPD_WARPS;
   __shared__ int sh_piv[W][QSS_NN];
   __shared__ double sh_x[W][QSS_NN + 1];
@@ -442,7 +442,11 @@ __device__ __forceinline__ void qss_newton_update(
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < QSS_NN; ++i) {
-      const double g = -(PHI[i * sld + s] - PHI0[i * sld + s] - h * F[i * sld + t]);
+      const double f = F[i * sld + t];
+      // optional record of f: at the first iterate (phi0) and the latest
+      if (FN0 && IT[s] == 1) FN0[i * sld + s] = f;
+      if (FN1) FN1[i * sld + s] = f;
+      const double g = -(PHI[i * sld + s] - PHI0[i * sld + s] - h * f);
       F[i * sld + t] = g;
       ok = ok && qss_finite(g);
     }
@@ -557,18 +561,19 @@ __device__ __forceinline__ void qss_newton_update(
       const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,    \
       int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT,                          \
       const int* __restrict__ LIST, const int* __restrict__ NACT, int* __restrict__ LIST2,        \
-      int* __restrict__ NACT2, long long sld, QssNewtonOpts o
+      int* __restrict__ NACT2, long long sld, double* __restrict__ FN0, double* __restrict__ FN1, \
+      QssNewtonOpts o
 
 extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS * 32)
 qss_newton_update_fp64_kernel(QSS_UPDATE_PARAMS) {
   qss_newton_update<false>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
-                           NACT2, sld, o);
+                           NACT2, sld, FN0, FN1, o);
 }
 
 extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS32 * 32)
 qss_newton_update_fp32ir_kernel(QSS_UPDATE_PARAMS) {
   qss_newton_update<true>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
-                          NACT2, sld, o);
+                          NACT2, sld, FN0, FN1, o);
 }
 
 // Write the state back: T, Y (rho fixed), iterations and status.
@@ -587,4 +592,124 @@ qss_newton_finish_kernel(long long cells, long long c0, long long ld, const doub
   for (int k = 0; k < QSS_N; ++k) Y[k * ld + c] = PHI[k * sld + s] / (r * qss_inv_W[k]);
   if (iters) iters[c] = IT[s];
   if (status) status[c] = ST[s];
+}
+
+// ---------------------------------------------------------------------------
+// Integration over an interval by backward-Euler substeps with local error
+// control (qss_integrate).  Per cell s of a chunk (persistent across rounds):
+//   TT[s] time done, HH[s] next substep, DT[s] target interval,
+//   IS[s] 0 done / 1 active / 2 substep below h_min, NS[s] accepted substeps.
+// A round: gather the active cells (list A, count *CA) into a contiguous
+// batch (rho, T, Y, h), one Newton-solved backward-Euler step of the batch
+// (f recorded at phi_n and at the last iterate), then accept or reject each
+// cell's substep and build the next active list (B).
+struct QssIntegOpts {
+  double rtol, atol_C, atol_T;
+  double h_min;   // fraction of the interval
+};
+
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
+qss_integ_init_kernel(long long cells, long long c0, const double* __restrict__ dt_total,
+                      int dt_stride, double h0, double* __restrict__ TT, double* __restrict__ HH,
+                      double* __restrict__ DT, int* __restrict__ IS, int* __restrict__ NS,
+                      int* __restrict__ LA, int* __restrict__ CA) {
+  const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  if (s == 0) *CA = (int)cells;
+  if (s >= cells) return;
+  const double D = dt_total[dt_stride ? c0 + s : 0];
+  DT[s] = D;
+  TT[s] = 0.0;
+  HH[s] = fmin(h0 > 0.0 ? h0 : 0.01 * D, D);
+  IS[s] = 1;
+  NS[s] = 0;
+  LA[s] = (int)s;
+}
+
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
+qss_integ_gather_kernel(long long c0, long long ld, const double* __restrict__ rho,
+                        const double* __restrict__ T, const double* __restrict__ Y,
+                        const int* __restrict__ LA, const int* __restrict__ CA, int* __restrict__ CB,
+                        const double* __restrict__ HH, double* __restrict__ rhob,
+                        double* __restrict__ Tb, double* __restrict__ Yb, double* __restrict__ dtb,
+                        int* __restrict__ ncap, long long bld) {
+  const long long i = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  const int n = *CA;
+  if (i == 0) { *CB = 0; *ncap = n; }
+  if (i >= n) return;
+  const int s = LA[i];
+  const long long c = c0 + s;
+  rhob[i] = rho[c];
+  Tb[i] = T[c];
+#pragma unroll
+  for (int k = 0; k < QSS_N; ++k) Yb[k * bld + i] = Y[k * ld + c];
+  dtb[i] = HH[s];
+}
+
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
+qss_integ_accept_kernel(long long c0, long long ld, double* __restrict__ T, double* __restrict__ Y,
+                        const int* __restrict__ LA, const int* __restrict__ CA, int* __restrict__ LB,
+                        int* __restrict__ CB, double* __restrict__ HH, double* __restrict__ TT,
+                        const double* __restrict__ DT, int* __restrict__ IS, int* __restrict__ NS,
+                        const double* __restrict__ rhob, const double* __restrict__ Tb,
+                        const double* __restrict__ Yb, const int* __restrict__ bst,
+                        const double* __restrict__ FN0, const double* __restrict__ FN1, long long bld,
+                        QssIntegOpts o) {
+  const long long i = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  if (i >= *CA) return;
+  const int s = LA[i];
+  const long long c = c0 + s;
+  const double h = HH[s];
+  bool keep = true;
+  if (bst[i] != QSS_CELL_CONVERGED) {
+    // the Newton solve failed: a quarter of the substep
+    HH[s] = 0.25 * h;
+  } else {
+    // local error of the substep: h/2 (f(phi_n+1) - f(phi_n)), weighted RMS
+    const double r = rhob[i];
+    double e2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < QSS_NN; ++k) {
+      const double phi = k < QSS_N ? r * Yb[k * bld + i] * qss_inv_W[k] : Tb[i];
+      const double e = 0.5 * h * (FN1[k * bld + i] - FN0[k * bld + i]);
+      const double w = o.rtol * fabs(phi) + (k < QSS_N ? o.atol_C : o.atol_T);
+      const double q = e / w;
+      e2 = fma(q, q, e2);
+    }
+    const double err = sqrt(e2 / QSS_NN);
+    if (err <= 1.0) {
+      T[c] = Tb[i];
+#pragma unroll
+      for (int k = 0; k < QSS_N; ++k) Y[k * ld + c] = Yb[k * bld + i];
+      TT[s] += h;
+      NS[s] += 1;
+      const double rem = DT[s] - TT[s];
+      if (rem <= 1e-12 * DT[s]) {
+        IS[s] = 0;
+        keep = false;
+      } else {
+        const double g = err > 0.0 ? 0.9 / sqrt(err) : 4.0;
+        HH[s] = fmin(h * fmin(4.0, fmax(0.2, g)), rem);
+      }
+    } else {
+      // rejected (also for a NaN error): shrink by the error's square root
+      const double g = err > 0.0 ? 0.9 / sqrt(err) : 0.25;
+      HH[s] = h * (g == g ? fmin(0.9, fmax(0.2, g)) : 0.25);
+    }
+  }
+  if (keep && HH[s] < o.h_min * DT[s]) {
+    IS[s] = 2;
+    keep = false;
+  }
+  if (keep) LB[atomicAdd(CB, 1)] = s;
+}
+
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
+qss_integ_finish_kernel(long long cells, long long c0, const int* __restrict__ IS,
+                        const int* __restrict__ NS, int* __restrict__ nsteps, int* __restrict__ status) {
+  const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  if (s >= cells) return;
+  const long long c = c0 + s;
+  if (nsteps) nsteps[c] = NS[s];
+  // 0 reached the end, 1 substep attempts exhausted, 2 substep below h_min
+  if (status) status[c] = IS[s] == 0 ? 0 : (IS[s] == 2 ? 2 : 1);
 }

@@ -182,6 +182,11 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   for (int i = 0; i < 4; ++i)
     if (!m->mod_newton || drv().cuModuleGetFunction(oslot[i], m->mod_newton, opt[i]) != CUDA_SUCCESS)
       *oslot[i] = nullptr;
+  const char* integ[] = {"qss_integ_init_kernel", "qss_integ_gather_kernel", "qss_integ_accept_kernel",
+                         "qss_integ_finish_kernel"};
+  for (int i = 0; i < 4; ++i)
+    if (!m->mod_newton || drv().cuModuleGetFunction(&m->f_integ[i], m->mod_newton, integ[i]) != CUDA_SUCCESS)
+      m->f_integ[i] = nullptr;
   for (int i = 0; i < 2; ++i) {
     int tpb = 0;
     if (m->f_newton[i] &&

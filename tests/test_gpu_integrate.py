@@ -1,0 +1,73 @@
+"""qss_integrate (backward-Euler substeps with local error control) on the
+GPU against the oracle's integrator.
+
+Both run the same controller; a substep decision (accept/reject, err <= 1)
+can flip where err is within rounding of 1, after which the two substep
+sequences differ (both valid).  So: most cells take the same number of
+substeps with the same outcome, and on those the final states agree within
+the accumulated Newton tolerance (each substep's solution is pinned to the
+oracle's within 1e-10 relative for FP64 LU, 1e-8 for FP32 LU + refinement).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_05974_b300 import binding, mechgen, workloads
+from paper_2405_05974_b300.qssc.build import build_mechanism
+
+pytestmark = pytest.mark.gpu
+OPTS = dict(rtol=1e-3, atol_C=1e-6, atol_T=1e-3)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("key,ncells,D", [("tiny", 512, 1e-7), ("hydrocarbon", 64, 1e-8)])
+@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
+def test_integrate_matches_oracle(key, ncells, D, prec):
+    m = workloads.mechanism(key)
+    om = oracle.OracleMech(m)
+    gm = binding.Mechanism(build_mechanism(m), 0)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    t, y = dev(T), dev(Y)
+    ns, st = gm.integrate(dev(rho), t, y, D, precision=prec, opts=binding.integrate_opts(**OPTS))
+    ns, st = ns.cpu().numpy(), st.cpu().numpy()
+    To, Yo, nso, sto = om.integrate(rho, T, Y, D, **OPTS)
+    same = (st == sto) & (ns == nso)
+    assert same.mean() >= 0.9, (np.bincount(st, minlength=3), np.bincount(sto, minlength=3))
+    done = same & (st == 0)
+    assert done.mean() >= 0.7
+    W = om.W[:, None]
+    pg = np.vstack([rho[None] * y.cpu().numpy() / W, t.cpu().numpy()[None]])[:, done]
+    po = np.vstack([rho[None] * Yo / W, To[None]])[:, done]
+    rel = 1e-8 if prec == binding.QSS_LU_FP64 else 1e-6
+    atol = np.r_[np.full(om.N, 1e-12), 1e-8][:, None]
+    ok = np.abs(pg - po) <= rel * np.abs(po) + atol
+    assert ok.all(axis=0).mean() >= 0.99, np.argwhere(~ok)[:5]
+
+
+def test_integrate_rejects_bad_options():
+    m = workloads.mechanism("tiny")
+    gm = binding.Mechanism(build_mechanism(m), 0)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["tiny"], 64)
+    for bad in (dict(atol_C=0.0), dict(h_min=0.0), dict(max_rounds=0), dict(rtol=-1.0)):
+        with pytest.raises(binding.QSSError):
+            gm.integrate(dev(rho), dev(T), dev(Y), 1e-7, opts=binding.integrate_opts(**bad))
+
+
+def test_integrate_reaches_where_one_step_fails():
+    """Cells whose single backward-Euler step over the interval does not
+    converge reach the end of it by substeps."""
+    key, ncells, D = "tiny", 512, 1e-7
+    m = workloads.mechanism(key)
+    gm = binding.Mechanism(build_mechanism(m), 0)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    t1, y1 = dev(T), dev(Y)
+    _, st1 = gm.implicit_step(dev(rho), t1, y1, D * 10)
+    t2, y2 = dev(T), dev(Y)
+    _, st2 = gm.integrate(dev(rho), t2, y2, D * 10, opts=binding.integrate_opts(**OPTS))
+    st1, st2 = st1.cpu().numpy(), st2.cpu().numpy()
+    rescued = (st1 != 0) & (st2 == 0)
+    assert rescued.sum() > 0, (np.bincount(st1), np.bincount(st2, minlength=3))
