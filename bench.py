@@ -135,7 +135,7 @@ def max_over_ranks(pg, x):
     if pg is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
@@ -192,9 +192,19 @@ def cpu_baseline(mech, states_cfg, seconds, ncells_cap=1 << 20):
             break
         chunk = min(chunk * 2, 8192)
     el = time.perf_counter() - t0 - gen_s
+    # one host thread on a short sample, for the per-core rate
+    cfg = type(states_cfg)(**{**states_cfg.__dict__, "seed": states_cfg.seed + 99})
+    rho, T, Y = mechgen.generate_states(mech, cfg, 256)
+    n1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < min(2.0, seconds / 4):
+        om.eval(rho, T, Y, jac=True, nthreads=1)
+        n1 += 256
+    single = n1 / (time.perf_counter() - t1)
     return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": single,
             "sample": f"{done} seeded cells of the workload, wdot+Tdot+Jacobian, "
-                      f"{el:.1f} s on {cores} host threads (input generation excluded)"}
+                      f"{el:.1f} s on {cores} host threads (input generation excluded); "
+                      f"single_core_value: {n1} cells on one thread"}
 
 
 # ---------------------------------------------------------------------------
