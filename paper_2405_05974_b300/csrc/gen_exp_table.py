@@ -2,7 +2,7 @@
 
 Tang's method (P. T. P. Tang, "Table-driven implementation of the exponential
 function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989) with a
-128-entry table: x = (128 k + j) ln2/128 + r, exp(x) = 2^k 2^(j/128) exp(r).
+256-entry table: x = (256 k + j) ln2/256 + r, exp(x) = 2^k 2^(j/256) exp(r).
 Values are computed here in 60-digit decimal arithmetic and rounded once to
 binary64.
 
@@ -13,7 +13,7 @@ import os
 from decimal import Decimal, getcontext
 
 getcontext().prec = 60
-L = 128
+L = 256
 LN2 = Decimal(2).ln()
 
 
@@ -36,11 +36,11 @@ def main():
     inv = to_double(L / LN2)
     here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "qss_exp_table.inc"), "w") as f:
-        f.write("// Generated by gen_exp_table.py: 2^(j/128), j = 0..127, and the split of ln2/128.\n")
+        f.write("// Generated by gen_exp_table.py: 2^(j/256), j = 0..255, and the split of ln2/256.\n")
         f.write(f"#define QSS_EXP_INV_STEP {inv!r}\n")
         f.write(f"#define QSS_EXP_STEP_HI {hi!r}\n")
         f.write(f"#define QSS_EXP_STEP_LO {lo!r}\n")
-        f.write("__device__ const double qss_exp2_tab[128] = {\n")
+        f.write("__device__ const double qss_exp2_tab[256] = {\n")
         for i in range(0, L, 4):
             f.write("  " + ", ".join(repr(v) for v in tab[i:i + 4]) + ",\n")
         f.write("};\n")

@@ -14,14 +14,14 @@
 
 __device__ __forceinline__ double qss_rcp(double x) { return __drcp_rn(x); }
 
-// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989), 128 entries:
-//   x = (128 k + j) ln2/128 + r,  |r| <= ln2/256,
-//   exp(x) = 2^k * 2^(j/128) * (1 + q),  q = r + r^2/2 + ... + r^5/120.
-// n = 128 k + j is obtained by adding 1.5 * 2^52 (its low word is then n);
-// ln2/128 is split so that n * hi is exact.  The truncation error of the
-// polynomial is below 6e-19 relative; the result is within a few ulp of
+// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989), 256 entries:
+//   x = (256 k + j) ln2/256 + r,  |r| <= ln2/512,
+//   exp(x) = 2^k * 2^(j/256) * (1 + q),  q = r + r^2/2 + r^3/6 + r^4/24.
+// n = 256 k + j is obtained by adding 1.5 * 2^52 (its low word is then n);
+// ln2/256 is split so that n * hi is exact.  The truncation error of the
+// polynomial is below 4e-17 relative; the result is within about one ulp of
 // exp(x).  |x| >= 708 and NaN take the library exp (subnormal and overflowing
-// results, never reached by the workloads' arguments).  10 FP64 instructions.
+// results, never reached by the workloads' arguments).  9 FP64 instructions.
 __device__ __forceinline__ double qss_exp_table(double x) {
   const int hx = __double2hiint(x) & 0x7fffffff;
   if (hx >= 0x40862000) return exp(x);
@@ -31,14 +31,13 @@ __device__ __forceinline__ double qss_exp_table(double x) {
   const double nd = t - shifter;
   double r = fma(-nd, QSS_EXP_STEP_HI, x);
   r = fma(-nd, QSS_EXP_STEP_LO, r);
-  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
+  double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   p = fma(p, r, 0.5);
   p = fma(p, r, 1.0);
   const double q = p * r;
-  const double tj = __ldg(&qss_exp2_tab[n & 127]);
+  const double tj = __ldg(&qss_exp2_tab[n & 255]);
   const double res = fma(tj, q, tj);
-  const int scale = (int)((unsigned)(n >> 7) << 20);   // k in the exponent field
+  const int scale = (int)((unsigned)(n >> 8) << 20);   // k in the exponent field
   return __hiloint2double(__double2hiint(res) + scale, __double2loint(res));
 }
 

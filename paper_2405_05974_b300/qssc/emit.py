@@ -248,7 +248,7 @@ def algorithmic_flops(counts) -> int:
     return counts["dag_flops"]
 
 
-def fp64_instructions(counts, exp_cost=10, log_cost=36, rcp_cost=10) -> int:
+def fp64_instructions(counts, exp_cost=9, log_cost=13, rcp_cost=10) -> int:
     """Estimated FP64-pipe instructions per cell of the emitted code."""
     return (counts["add"] + counts["mul"] + counts["fma"] + exp_cost * counts["exp"]
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
