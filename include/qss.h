@@ -14,6 +14,11 @@
  *   state vector and Jacobian .............. Section 3.1, Eq. (JacExptr)
  *   chain rule through C_QSS ............... Section 3.2, Eq. (JQSS)
  *   symbolic construction with CSE ......... Section 3.2.2
+ *   simplified Jacobians, FD Jacobian ...... Section 3.3.1, Eq. (frobErr); FD T column 3.3.2
+ *   implicit steps and integration ......... Section 3.1 (the stiff 0D use the Jacobian serves)
+ * The mechanism compiler (paper_2405_05974_b300.qssc) produces the artefacts
+ * this library loads; linearization of quadratic QSS couplings (Section 2.2,
+ * Alg. 1) and the Jacobian variants are compiler options.
  *
  * Conventions shared by every entry point
  *   - Units are SI: rho kg/m^3, T K, concentrations mol/m^3, wdot mol/m^3/s,

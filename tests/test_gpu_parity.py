@@ -119,10 +119,12 @@ def test_paper_sampling_protocols():
         assert_gate("jac", J, ref["jac"], eb["jac"])
 
 
-def test_full_size_sampled_cells():
-    """Hydrocarbon workload at its full size (2^20 cells, the benchmark's launch
-    configuration): a seeded sample of cells checked against the oracle."""
-    key = "hydrocarbon"
+@pytest.mark.parametrize("key", ["hydrocarbon", "large"])
+def test_full_size_sampled_cells(key):
+    """The workload at its full size (2^20 cells, the benchmark's launch
+    configuration; for the large mechanism the partitioned Jacobian in
+    several frontier chunks): a seeded sample of cells checked against the
+    oracle."""
     m, gm, om = mech(key)
     nc = workloads.NCELLS[key]
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], nc)
