@@ -497,11 +497,24 @@ def main():
             gm.jacobian_host(rh, th, yh, jac=Jh, wdot=wh, Tdot=tdh)
         el = max_over_ranks(pg, time.perf_counter() - t0)
         nchunks = -(-ncells // 65536)
+        # the host link on its own: one 2 GiB device -> pinned host copy
+        hb = torch.empty(1 << 28, dtype=torch.float64).pin_memory()
+        db = torch.empty(1 << 28, dtype=torch.float64, device="cuda")
+        hb.copy_(db)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        hb.copy_(db)
+        torch.cuda.synchronize()
+        link = hb.numel() * 8 / (time.perf_counter() - t1) / 1e9
+        del hb, db
+        d2h = 8 * (n * n + gm.N + 1) * ncells
         e2e = {"value": ncells * world * e_steps / el, "unit": UNIT,
                "h2d_bytes_per_step": 8 * (2 + gm.N) * ncells,
-               "d2h_bytes_per_step": 8 * (n * n + gm.N + 1) * ncells,
+               "d2h_bytes_per_step": d2h,
                "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
-               "gpu_launches_per_step": nchunks}
+               "gpu_launches_per_step": nchunks,
+               "d2h_gbs_achieved": d2h * e_steps / el / 1e9,
+               "host_link_d2h_gbs": link}
         del Jh
     variants = None
     if not a.no_variants and rank == 0 and key in ("tiny", "hydrocarbon"):

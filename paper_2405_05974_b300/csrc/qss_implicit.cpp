@@ -26,20 +26,33 @@ struct NewtonOptsDev {   // layout of QssNewtonOpts in qss_newton.cuh
 };
 }  // namespace qss
 
-namespace {
-int ensure_scratch(qss_mech_s* m, size_t bytes) {
-  if (m->newton_scratch_bytes >= bytes) return QSS_OK;
-  if (m->newton_scratch) {
-    drv().cuMemFree(m->newton_scratch);
-    m->newton_scratch = 0;
-    m->newton_scratch_bytes = 0;
+namespace qss {
+// The handle's Newton scratch for a call enqueued on `st`: at least `bytes`,
+// reused only after the previous call's work (on any stream) is done with it
+// -- st waits for the event the previous call recorded (the caller records
+// it again with scratch_release once its work is enqueued).
+int scratch_acquire(qss_mech_s* m, size_t bytes, CUstream st) {
+  if (m->newton_scratch_bytes < bytes) {
+    if (m->newton_done) CU_TRY(drv().cuEventSynchronize(m->newton_done));
+    if (m->newton_scratch) {
+      drv().cuMemFree(m->newton_scratch);
+      m->newton_scratch = 0;
+      m->newton_scratch_bytes = 0;
+    }
+    CUresult r = drv().cuMemAlloc(&m->newton_scratch, bytes);
+    if (r != CUDA_SUCCESS) return fail(QSS_ERR_OOM, "cannot allocate the Newton scratch");
+    m->newton_scratch_bytes = bytes;
   }
-  CUresult r = drv().cuMemAlloc(&m->newton_scratch, bytes);
-  if (r != CUDA_SUCCESS) return fail(QSS_ERR_OOM, "cannot allocate the Newton scratch");
-  m->newton_scratch_bytes = bytes;
+  if (!m->newton_done) CU_TRY(drv().cuEventCreate(&m->newton_done, CU_EVENT_DISABLE_TIMING));
+  else CU_TRY(drv().cuStreamWaitEvent(st, m->newton_done, 0));
   return QSS_OK;
 }
-}  // namespace
+
+int scratch_release(qss_mech_s* m, CUstream st) {
+  CU_TRY(drv().cuEventRecord(m->newton_done, st));
+  return QSS_OK;
+}
+}  // namespace qss
 
 namespace qss {
 
@@ -141,8 +154,10 @@ extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const
   const size_t per_cell = newton_scratch_per_cell(m, precision);
   int64_t want = std::min<int64_t>((int64_t)(kScratchBudget / per_cell), (ncells + 31) / 32 * 32);
   want = std::max<int64_t>((want + 31) / 32 * 32, 32);
-  rc = ensure_scratch(m, per_cell * (size_t)want + 256);
+  rc = scratch_acquire(m, per_cell * (size_t)want + 256, (CUstream)stream);
   if (rc) return rc;
-  return implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,
-                         (CUstream)stream, m->newton_scratch, m->newton_scratch_bytes);
+  rc = implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,
+                       (CUstream)stream, m->newton_scratch, m->newton_scratch_bytes);
+  int rr = scratch_release(m, (CUstream)stream);
+  return rc ? rc : rr;
 }

@@ -72,12 +72,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   const size_t oNewton = take(0);
   const size_t newton_bytes = newton_scratch_per_cell(m, precision) * (size_t)S + 256;
   const size_t total = off + newton_bytes;
-  if (m->newton_scratch_bytes < total) {
-    if (m->newton_scratch) { drv().cuMemFree(m->newton_scratch); m->newton_scratch = 0; m->newton_scratch_bytes = 0; }
-    if (drv().cuMemAlloc(&m->newton_scratch, total) != CUDA_SUCCESS)
-      return fail(QSS_ERR_OOM, "cannot allocate the integration scratch");
-    m->newton_scratch_bytes = total;
-  }
+  if ((rc = scratch_acquire(m, total, st))) return rc;
   char* base = (char*)m->newton_scratch;
   double* TT = (double*)(base + oTT);
   double* HH = (double*)(base + oHH);
@@ -102,7 +97,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
     int* CA = CNT;
     int* ncap = CNT + 2;
     void* a_init[] = {&cells, &cc0, &dt_total, &dt_stride, &h0, &TT, &HH, &DTv, &IS, &NS, &L[0], &CA};
-    if ((rc = launch_cells(m, m->f_integ[0], cells, m->block, a_init, st, 0))) return rc;
+    if ((rc = launch_cells(m, m->f_integ[0], cells, m->block, a_init, st, 0))) break;
     for (int round = 0; round < io.max_rounds; ++round) {
       const int a = round & 1, b = a ^ 1;
       int* LA = L[a];
@@ -110,22 +105,25 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
       int* ca = CNT + a;
       int* cb = CNT + b;
       void* a_g[] = {&cc0, &l, &rho, &T, &Y, &LA, &ca, &cb, &HH, &rhob, &Tb, &Yb, &dtb, &ncap, &bld};
-      if ((rc = launch_cells(m, m->f_integ[1], cells, m->block, a_g, st, 0))) return rc;
+      if ((rc = launch_cells(m, m->f_integ[1], cells, m->block, a_g, st, 0))) break;
       if ((rc = implicit_launch(m, cells, bld, dtb, 1, rhob, Tb, Yb, precision, o, nullptr, bst, st,
                                 newton, newton_bytes, ncap, F0, F1)))
-        return rc;
+        break;
       void* a_a[] = {&cc0, &l, &T, &Y, &LA, &ca, &LB, &cb, &HH, &TT, &DTv, &IS, &NS,
                      &rhob, &Tb, &Yb, &bst, &F0, &F1, &bld, &od};
-      if ((rc = launch_cells(m, m->f_integ[2], cells, m->block, a_a, st, 0))) return rc;
+      if ((rc = launch_cells(m, m->f_integ[2], cells, m->block, a_a, st, 0))) break;
       if ((round + 1) % kCheckEvery == 0) {
         int left = 0;
-        CU_TRY(drv().cuMemcpyDtoHAsync(&left, (CUdeviceptr)cb, sizeof(int), st));
-        CU_TRY(drv().cuStreamSynchronize(st));
+        CUresult r1 = drv().cuMemcpyDtoHAsync(&left, (CUdeviceptr)cb, sizeof(int), st);
+        if (r1 == CUDA_SUCCESS) r1 = drv().cuStreamSynchronize(st);
+        if (r1 != CUDA_SUCCESS) { rc = cu_fail(r1, "integration count read-back"); break; }
         if (left == 0) break;
       }
     }
+    if (rc) break;
     void* a_f[] = {&cells, &cc0, &IS, &NS, &nsteps, &cell_status};
-    if ((rc = launch_cells(m, m->f_integ[3], cells, m->block, a_f, st, 0))) return rc;
+    if ((rc = launch_cells(m, m->f_integ[3], cells, m->block, a_f, st, 0))) break;
   }
-  return QSS_OK;
+  int rr = scratch_release(m, st);
+  return rc ? rc : rr;
 }

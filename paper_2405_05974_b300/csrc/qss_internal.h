@@ -43,6 +43,7 @@ struct qss_mech_s {
   // implicit step: Newton matrices of one chunk of cells (grown on demand)
   CUdeviceptr newton_scratch = 0;
   size_t newton_scratch_bytes = 0;
+  CUevent newton_done = nullptr;   // recorded after each call's last use of the scratch
 };
 
 namespace qss {
@@ -65,6 +66,9 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
 inline size_t frontier_bytes_per_cell(const qss_mech_s* m) {
   return m->jac_parts >= 2 ? (size_t)m->frontier * sizeof(double) : 0;
 }
+// the handle's Newton scratch, ordered across streams (qss_implicit.cpp)
+int scratch_acquire(qss_mech_s* m, size_t bytes, CUstream st);
+int scratch_release(qss_mech_s* m, CUstream st);
 // implicit step (qss_implicit.cpp)
 size_t newton_scratch_per_cell(const qss_mech_s* m, int precision);
 int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,

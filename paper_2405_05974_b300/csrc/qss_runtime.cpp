@@ -206,6 +206,7 @@ void qss_mech_free(qss_mech_t m) {
     if (m->st[b]) drv().cuStreamDestroy(m->st[b]);
   }
   if (m->newton_scratch) drv().cuMemFree(m->newton_scratch);
+  if (m->newton_done) drv().cuEventDestroy(m->newton_done);
   if (m->fr_scratch) drv().cuMemFree(m->fr_scratch);
   if (m->fr_done) drv().cuEventDestroy(m->fr_done);
   if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
