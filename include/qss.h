@@ -295,9 +295,9 @@ int qss_measure_fp64_peak(int device, int millis, double* tflops);
 
 /* Diagnostics: evaluates the device math routines used by generated code,
  * elementwise on device arrays x[n] -> y[n] (fn 0 = table-driven exp,
- * 1 = CUDA library exp, 2 = table-driven log, 3 = reciprocal, 4 = CUDA
- * library log).  Used by the tests that compare the table-driven functions
- * with the library and with exact values.  Errors: QSS_ERR_INVALID_ARG for an
+ * 1 = CUDA library exp, 2 = table-driven log, 3 = series-refined reciprocal,
+ * 4 = CUDA library log, 5 = CUDA correctly rounded reciprocal).  Used by the
+ * tests that compare these functions with the library and with exact values.  Errors: QSS_ERR_INVALID_ARG for an
  * unknown fn or null arrays. */
 int qss_selftest_math(int device, int fn, int64_t n, const double* x, double* y, void* stream);
 

@@ -24,7 +24,7 @@ extern "C" __global__ void qss_l2_flush(double* buf, long long n, double v) {
 
 // Elementwise evaluation of the device math used by generated code, for tests:
 // fn 0 = qss_exp_table, 1 = library exp, 2 = qss_log_table, 3 = qss_rcp,
-// 4 = library log.
+// 4 = library log, 5 = library reciprocal (correctly rounded).
 extern "C" __global__ void qss_math_probe(int fn, long long n, const double* __restrict__ x,
                                           double* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,6 +36,7 @@ extern "C" __global__ void qss_math_probe(int fn, long long n, const double* __r
     case 1: r = exp(v); break;
     case 2: r = qss_log_table(v); break;
     case 4: r = log(v); break;
+    case 5: r = __drcp_rn(v); break;
     default: r = qss_rcp(v); break;
   }
   y[i] = r;

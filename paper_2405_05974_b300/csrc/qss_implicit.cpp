@@ -93,9 +93,10 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
   const size_t per_cell = newton_scratch_per_cell(m, precision);
-  int64_t chunk = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell) / 32 * 32;
-  if (chunk < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
-  chunk = std::min<int64_t>(chunk, (ncells + 31) / 32 * 32);
+  const int64_t cap = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell);
+  if (cap < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
+  int64_t chunk = std::min<int64_t>(cap / 32 * 32, (ncells + 31) / 32 * 32);
+  if (chunk < ncells && !(ncap || fn0 || fn1)) chunk = chunk_cells(m, cap);   // whole waves per chunk
   if ((ncap || fn0 || fn1) && chunk < ncells)
     return fail(QSS_ERR_BUDGET, "a capped or recording launch must fit one chunk");
   NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
@@ -152,8 +153,8 @@ extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   const size_t per_cell = newton_scratch_per_cell(m, precision);
-  int64_t want = std::min<int64_t>((int64_t)(kScratchBudget / per_cell), (ncells + 31) / 32 * 32);
-  want = std::max<int64_t>((want + 31) / 32 * 32, 32);
+  const int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(kScratchBudget / per_cell)),
+                                         (ncells + 31) / 32 * 32);
   rc = scratch_acquire(m, per_cell * (size_t)want + 256, (CUstream)stream);
   if (rc) return rc;
   rc = implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,

@@ -58,8 +58,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   CUstream st = (CUstream)stream;
   const int N = m->N, n = N + 1;
   const size_t per = integ_per_cell(m, precision);
-  int64_t S = std::min<int64_t>((int64_t)(kIntegBudget / per) / 32 * 32, (ncells + 31) / 32 * 32);
-  S = std::max<int64_t>(S, 32);
+  const int64_t S = std::min<int64_t>(chunk_cells(m, (int64_t)(kIntegBudget / per)), (ncells + 31) / 32 * 32);
   // layout (offsets in bytes, every array 256-byte aligned)
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t D = al((size_t)S * sizeof(double)), I = al((size_t)S * sizeof(int));

@@ -61,7 +61,7 @@ extern "C" int qss_measure_fp64_peak(int device, int millis, double* tflops) {
 
 extern "C" int qss_selftest_math(int device, int fn, int64_t n, const double* x, double* y,
                                  void* stream) {
-  if (n < 0 || (n > 0 && (!x || !y)) || fn < 0 || fn > 4) return fail(QSS_ERR_INVALID_ARG, "bad argument");
+  if (n < 0 || (n > 0 && (!x || !y)) || fn < 0 || fn > 5) return fail(QSS_ERR_INVALID_ARG, "bad argument");
   if (n == 0) return QSS_OK;
   CUdevice dev;
   CUcontext ctx;

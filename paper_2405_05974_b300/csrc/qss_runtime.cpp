@@ -71,6 +71,11 @@ int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** 
   return QSS_OK;
 }
 
+int64_t chunk_cells(const qss_mech_s* m, int64_t cap) {
+  if (m->wave_cells > 0 && cap >= m->wave_cells) return cap / m->wave_cells * m->wave_cells;
+  return std::max<int64_t>(32, cap / 32 * 32);
+}
+
 int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
                const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
                const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
@@ -194,6 +199,15 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
         tpb > 0)
       m->upd_threads[i] = tpb;
   }
+  // cells of one full wave of the (first) Jacobian kernel: chunked paths use
+  // multiples of it, so that no chunk ends in a partly filled wave
+  int sms = 0, per_sm = 0;
+  if (drv().cuDeviceGetAttribute(&sms, CU_DEVICE_ATTRIBUTE_MULTIPROCESSOR_COUNT, m->dev) != CUDA_SUCCESS)
+    sms = 0;
+  if (drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m->jac_parts >= 2 ? m->f_prefix : m->f_jac,
+                                                        m->block, 0) != CUDA_SUCCESS)
+    per_sm = 0;
+  m->wave_cells = (int64_t)std::max(sms, 0) * std::max(per_sm, 0) * m->block;
   *out = m;
   return QSS_OK;
 }
@@ -263,8 +277,7 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   const size_t per = frontier_bytes_per_cell(m);
-  int64_t want = std::max<int64_t>(32, (int64_t)(m->fr_budget / per) / 32 * 32);
-  want = std::min<int64_t>(want, (ncells + 31) / 32 * 32);
+  int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(m->fr_budget / per)), (ncells + 31) / 32 * 32);
   if (m->fr_cells > want && (int64_t)(m->fr_budget / per) < m->fr_cells) {
     // the budget was lowered: give the larger buffer back
     if (m->fr_done) CU_TRY(drv().cuEventSynchronize(m->fr_done));
@@ -282,8 +295,8 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   if (!m->fr_done) CU_TRY(drv().cuEventCreate(&m->fr_done, CU_EVENT_DISABLE_TIMING));
   else CU_TRY(drv().cuStreamWaitEvent(s, m->fr_done, 0));
   double* fr = (double*)m->fr_scratch;
-  for (int64_t c0 = 0; c0 < ncells; c0 += m->fr_cells) {
-    const int64_t cs = std::min<int64_t>(m->fr_cells, ncells - c0);
+  for (int64_t c0 = 0; c0 < ncells; c0 += want) {
+    const int64_t cs = std::min<int64_t>(want, ncells - c0);
     if ((rc = jac_launch(m, cs, ld, rho + c0, T + c0, Y + c0, jac + c0, wdot ? wdot + c0 : nullptr,
                          Tdot ? Tdot + c0 : nullptr, nullptr, nullptr, nullptr, nullptr, fr,
                          m->fr_cells, s)))

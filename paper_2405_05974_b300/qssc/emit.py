@@ -248,7 +248,7 @@ def algorithmic_flops(counts) -> int:
     return counts["dag_flops"]
 
 
-def fp64_instructions(counts, exp_cost=9, log_cost=13, rcp_cost=10) -> int:
+def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
     """Estimated FP64-pipe instructions per cell of the emitted code."""
     return (counts["add"] + counts["mul"] + counts["fma"] + exp_cost * counts["exp"]
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
@@ -325,11 +325,11 @@ _MATERIAL = (ADD, SUB, MUL, RECIP, EXP, LOG, SELECT)
 def _op_cost(g, x):
     op = g.op[x]
     if op == EXP:
-        return 10
+        return 8
     if op == LOG:
         return 13
     if op == RECIP:
-        return 10
+        return 3
     return 1 if op in _MATERIAL else 0
 
 

@@ -1,5 +1,6 @@
-"""The device exponential and logarithm used by the generated code (table-driven,
-Tang-style reductions) against the CUDA library functions and exact values."""
+"""The device exponential, logarithm and reciprocal used by the generated code
+(table-driven Tang-style reductions; a series-refined reciprocal) against the
+CUDA library functions and exact values."""
 from decimal import Decimal, getcontext
 
 import numpy as np
@@ -99,3 +100,36 @@ def test_table_log_special_arguments():
     assert np.array_equal(np.isnan(y), np.isnan(ref))
     m = ~np.isnan(ref)
     assert np.array_equal(y[m], ref[m])
+
+
+# ---------------------------------------------------------------------------
+# series-refined reciprocal
+# ---------------------------------------------------------------------------
+
+def test_rcp_vs_exact():
+    # numpy's 1/x is the correctly rounded reciprocal: the exact value to 1/2 ulp
+    rng = np.random.default_rng(7)
+    x = np.concatenate([np.ldexp(rng.uniform(1.0, 2.0, 400000), rng.integers(-1020, 1020, 400000)),
+                        -np.ldexp(rng.uniform(1.0, 2.0, 100000), rng.integers(-1020, 1020, 100000)),
+                        rng.uniform(200.0, 5000.0, 100000), 1.0 + rng.uniform(-1e-9, 1e-9, 20000),
+                        np.ldexp(1.0, np.arange(-1022, 1021)).astype(np.float64),
+                        np.array([1.0, 3.0, 7.0, np.nextafter(1.0, 2.0), np.nextafter(2.0, 0.0)])])
+    y = binding.selftest_math(3, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = 1.0 / x
+    e = ulp_err(y, ref)
+    assert e.max() <= 1.0, (e.max(), x[np.argmax(e)])
+    assert np.mean(y == ref) > 0.99        # nearly always the correctly rounded value
+    lib = binding.selftest_math(5, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.array_equal(lib, ref)
+
+
+def test_rcp_special_arguments():
+    x = np.array([0.0, -0.0, 5e-324, -1e-310, 2.2250738585072014e-308, 2.0 ** 1021, -(2.0 ** 1022),
+                  1.7976931348623157e308, np.inf, -np.inf, np.nan])
+    xd = torch.from_numpy(x).cuda()
+    y = binding.selftest_math(3, xd).cpu().numpy()
+    ref = binding.selftest_math(5, xd).cpu().numpy()
+    assert np.array_equal(np.isnan(y), np.isnan(ref))
+    m = ~np.isnan(ref)
+    assert np.array_equal(y[m], ref[m])
+    assert np.array_equal(np.signbit(y[m]), np.signbit(ref[m]))
