@@ -13,13 +13,12 @@
 // has converged or failed it leaves the list, so later launches cost only what
 // the remaining cells need.
 //
-// The update kernel factors one cell's matrix at a time per warp: lane r holds
-// row r (rows 32.. in a second register slot); partial pivoting picks the row
-// with the largest |a| among rows not yet pivoted (warp arg-max, lowest index
-// on ties; rows stay in place and their pivot order is recorded), pivot-row
-// entries are broadcast with shuffles, and the right-hand side is eliminated
-// with the matrix.  The matrix never leaves registers.
-//   update_fp64    factorisation and solve in FP64.
+// The update kernel solves one cell's system at a time per warp, with partial
+// pivoting (warp arg-max, lowest index on ties) and the right-hand side
+// eliminated with the matrix.
+//   update_fp64    elimination and solve in FP64, in place in shared memory,
+//                  the trailing block of each step split evenly over the
+//                  lanes (qss_smem_solve_fp64).
 //   update_fp32ir  M equilibrated by powers of two (rows, then columns),
 //                  factorisation in FP32 as a compact loop (qss_solve_fp32ir);
 //                  the solution refined with FP64 residuals g - M x (M from
@@ -50,8 +49,8 @@
 #error "the warp-cooperative Newton solver supports at most 63 transported species"
 #endif
 #define QSS_NSLOT ((QSS_NN + 31) / 32)
-// warps per update block: the FP32_IR form stages one matrix per warp in
-// shared memory (NN x (NN+1) doubles), within the 48 KB static limit
+// warps per update block: both forms stage one matrix per warp in shared
+// memory (NN x (NN+1) doubles), within the 48 KB static limit
 #define QSS_MSTRIDE (QSS_NN + 1)
 #define QSS_MBYTES (QSS_NN * QSS_MSTRIDE * 8)
 #define QSS_UPD_WARPS (QSS_MBYTES * 4 <= 44000 ? 4 : (QSS_MBYTES * 2 <= 44000 ? 2 : 1))
@@ -124,96 +123,75 @@ struct QssNewtonOpts {
   double refine_tol;
 };
 
-// Factor the rows a[slot][j] (row r = lane + 32 slot) with partial pivoting,
-// eliminating the right-hand side y[slot] with them.  On return row r holds
-// multipliers in the columns before its pivot order ord[slot] and its row of
-// U from there on; y holds the forward-substituted right-hand side; piv[k]
-// (shared) is the row pivoted at step k and pinv[k] the reciprocal of its
-// pivot.  Returns false on a zero pivot.
-template <class R>
-__device__ __forceinline__ bool qss_warp_factor(R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
-                                                int (&ord)[QSS_NSLOT], int* __restrict__ piv,
-                                                double* __restrict__ pinv, const int lane) {
-#pragma unroll
-  for (int sl = 0; sl < QSS_NSLOT; ++sl) ord[sl] = (lane + 32 * sl < QSS_NN) ? QSS_NN : -1;
-#pragma unroll
+// FP64 solve of one cell's Newton system M x = g by one warp, in place in the
+// warp's shared-memory copy of the augmented matrix [M | g] (row r at
+// Ms[r * QSS_MSTRIDE], g in column QSS_NN).  Gaussian elimination with
+// partial pivoting (largest |a| in the column, lowest row on ties) and row
+// exchanges; the pivot row is scaled by 1/pivot (unit upper triangle, so that
+// back substitution needs no division), and the trailing block of each step,
+// rows k+1.. x columns k+1..NN, is split evenly over the 32 lanes (entry e =
+// lane + 32 m of the block, its row and column advanced incrementally), so
+// every lane does ~1/32 of the n^3/3 FMAs whatever n is.  Multipliers are
+// not kept (g is eliminated with the matrix); entries left of the diagonal
+// become don't-care values and are never read.  The loops are rolled: the
+// FP64 pipe, not instruction fetch, must be the bound (a fully unrolled
+// register form of this solve was fetch-bound on B300, 74 stall cycles per
+// issue waiting for instructions).  On return column QSS_NN holds x.  Returns
+// false on an all-zero pivot column.
+__device__ __forceinline__ bool qss_smem_solve_fp64(double* __restrict__ Ms, const int lane) {
+  const unsigned FULL = 0xffffffffu;
+#pragma unroll 1
   for (int k = 0; k < QSS_NN; ++k) {
     long long best = -1;
     int brow = QSS_NN;
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const long long key = (ord[sl] == QSS_NN) ? qss_key(a[sl][k]) : -1LL;
-      if (key > best) { best = key; brow = lane + 32 * sl; }
+    for (int i = k + lane; i < QSS_NN; i += 32) {
+      const long long key = qss_key(Ms[i * QSS_MSTRIDE + k]);
+      if (key > best) { best = key; brow = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+      const long long ob = __shfl_xor_sync(FULL, best, o);
+      const int orow = __shfl_xor_sync(FULL, brow, o);
       if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
     }
     if (best <= 0) return false;
-    const int pl = brow & 31, ps = brow >> 5;
-    if (lane == 0) piv[k] = brow;
-    R pv = a[0][k], py = y[0];
-#pragma unroll
-    for (int sl = 1; sl < QSS_NSLOT; ++sl)
-      if (ps == sl) { pv = a[sl][k]; py = y[sl]; }
-    pv = qss_shfl(pv, pl);
-    py = qss_shfl(py, pl);
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl)
-      if (lane == pl && ps == sl) ord[sl] = k;
-    const R inv = R(1) / pv;
-    if (lane == 0) pinv[k] = (double)inv;
-    R l[QSS_NSLOT];
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const bool elim = ord[sl] == QSS_NN;
-      l[sl] = elim ? a[sl][k] * inv : R(0);
-      if (elim) a[sl][k] = l[sl];
-      y[sl] = fma(-l[sl], py, y[sl]);
+    double* __restrict__ rk = Ms + k * QSS_MSTRIDE;
+    if (brow != k) {   // warp-uniform
+      double* __restrict__ rp = Ms + brow * QSS_MSTRIDE;
+      for (int c = k + lane; c <= QSS_NN; c += 32) {
+        const double v = rk[c];
+        rk[c] = rp[c];
+        rp[c] = v;
+      }
+      __syncwarp();
     }
-    // constant trip count (the j <= k iterations fold away once both loops
-    // are unrolled): a loop starting at k + 1 is not unrolled before the
-    // outer one, and a dynamic index would put a[][] in local memory
-#pragma unroll
-    for (int j = 0; j < QSS_NN; ++j) {
-      if (j <= k) continue;
-      R pj = a[0][j];
-#pragma unroll
-      for (int sl = 1; sl < QSS_NSLOT; ++sl)
-        if (ps == sl) pj = a[sl][j];
-      pj = qss_shfl(pj, pl);
-#pragma unroll
-      for (int sl = 0; sl < QSS_NSLOT; ++sl) a[sl][j] = fma(-l[sl], pj, a[sl][j]);
+    const double inv = qss_rcp(rk[k]);
+    for (int c = k + 1 + lane; c <= QSS_NN; c += 32) rk[c] *= inv;
+    __syncwarp();
+    // trailing block: W = NN - k columns (k+1 .. NN), NN - 1 - k rows
+    const int W = QSS_NN - k, E = (QSS_NN - 1 - k) * W;
+    const int di = 32 / W, dj = 32 - di * W;
+    int i = k + 1 + lane / W, j = k + 1 + (lane - (lane / W) * W);
+#pragma unroll 4
+    for (int e = lane; e < E; e += 32) {
+      double* __restrict__ ri = Ms + i * QSS_MSTRIDE;
+      ri[j] = fma(-ri[k], rk[j], ri[j]);
+      i += di;
+      j += dj;
+      if (j > QSS_NN) { j -= W; ++i; }
     }
+    __syncwarp();
+  }
+  // back substitution, column oriented: x_k is final once the columns right
+  // of k have been subtracted
+#pragma unroll 1
+  for (int k = QSS_NN - 1; k > 0; --k) {
+    const double xk = Ms[k * QSS_MSTRIDE + QSS_NN];
+    for (int i = lane; i < k; i += 32)
+      Ms[i * QSS_MSTRIDE + QSS_NN] = fma(-Ms[i * QSS_MSTRIDE + k], xk, Ms[i * QSS_MSTRIDE + QSS_NN]);
+    __syncwarp();
   }
   return true;
-}
-
-// Back substitution (column oriented): x_k from the row of pivot order k,
-// k = NN-1 .. 0.  Lane (k & 31) keeps x_k in xo[k >> 5], so that every lane
-// ends with the entries of x whose index is lane + 32 slot.
-template <class R>
-__device__ __forceinline__ void qss_warp_back(const R (&a)[QSS_NSLOT][QSS_NN], R (&y)[QSS_NSLOT],
-                                              const int (&ord)[QSS_NSLOT],
-                                              const int* __restrict__ piv,
-                                              const double* __restrict__ pinv, R (&xo)[QSS_NSLOT],
-                                              const int lane) {
-#pragma unroll
-  for (int k = QSS_NN - 1; k >= 0; --k) {
-    const int p = piv[k];
-    const int pl = p & 31, ps = p >> 5;
-    R v = y[0];
-#pragma unroll
-    for (int sl = 1; sl < QSS_NSLOT; ++sl)
-      if (ps == sl) v = y[sl];
-    const R xk = qss_shfl(v, pl) * (R)pinv[k];
-    if (lane == (k & 31)) xo[k >> 5] = xk;
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl)
-      if (ord[sl] >= 0 && ord[sl] < k) y[sl] = fma(-a[sl][k], xk, y[sl]);
-  }
 }
 
 // FP32 LU with FP64 iterative refinement of one cell's Newton system M x = g,
@@ -419,12 +397,13 @@ __device__ __forceinline__ void qss_newton_update(
     const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
     double* __restrict__ FN0, double* __restrict__ FN1, const QssNewtonOpts o) {
   constexpr int W = FP32IR ? QSS_UPD_WARPS32 : QSS_UPD_WARPS;
-  __shared__ int sh_piv[W][QSS_NN];
-  __shared__ double sh_x[W][QSS_NN + 1];
-  __shared__ double sh_pinv[FP32IR ? 1 : W][QSS_NN];
-  // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows)
+  // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows; the
+  // FP64 form keeps g in the pad column and solves in place)
   __shared__ double sh_m[W * QSS_NN * QSS_MSTRIDE];
-  // FP32_IR: the FP32 factors, scale exponents and pivot reciprocals
+  // FP32_IR: pivot order, solution, the FP32 factors, scale exponents and
+  // pivot reciprocals
+  __shared__ int sh_piv[FP32IR ? W : 1][QSS_NN];
+  __shared__ double sh_x[FP32IR ? W : 1][QSS_NN + 1];
   __shared__ float sh_lu[FP32IR ? W * QSS_NN * QSS_MSTRIDE : 1];
   __shared__ int sh_e[FP32IR ? W : 1][2 * QSS_NN];
   __shared__ float sh_pinvf[FP32IR ? W : 1][QSS_NN];
@@ -461,7 +440,7 @@ __device__ __forceinline__ void qss_newton_update(
     const double hq = __shfl_sync(0xffffffffu, h, q);
     const long long tq = t0 + q;
     bool fin = true;
-    double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of M = I - hq J
+    double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of [M | g], M = I - hq J
     {
       // the cell's J is contiguous (written so by the Jacobian kernel in list
       // mode): one coalesced pass, 256 bytes per warp load
@@ -473,50 +452,38 @@ __device__ __forceinline__ void qss_newton_update(
         fin = fin && qss_finite(m);
         Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
       }
-      __syncwarp();
     }
     double gr[QSS_NSLOT];
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int r = lane + 32 * sl;
       gr[sl] = r < QSS_NN ? F[r * sld + tq] : 0.0;
+      if (!FP32IR && r < QSS_NN) Ms[r * QSS_MSTRIDE + QSS_NN] = gr[sl];
     }
+    __syncwarp();
     if (!__all_sync(0xffffffffu, fin)) {
       if (lane == q) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
       failed |= 1u << q;
       continue;
     }
     double xo[QSS_NSLOT];   // this lane's entries of the solution (index lane + 32 slot)
-    if (FP32IR) {
-      if (!qss_solve_fp32ir(Ms, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
-                            sh_x[w], gr, xo, lane, o)) {
-        if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
-        failed |= 1u << q;
-        __syncwarp();
-        continue;
-      }
+    bool solved;
+    if constexpr (FP32IR) {
+      solved = qss_solve_fp32ir(Ms, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
+                                sh_x[w], gr, xo, lane, o);
     } else {
-      double a[QSS_NSLOT][QSS_NN];
-      double y[QSS_NSLOT];
-      int ord[QSS_NSLOT];
+      solved = qss_smem_solve_fp64(Ms, lane);
 #pragma unroll
       for (int sl = 0; sl < QSS_NSLOT; ++sl) {
         const int r = lane + 32 * sl;
-        const bool live = r < QSS_NN;
-#pragma unroll
-        for (int j = 0; j < QSS_NN; ++j) a[sl][j] = live ? Ms[r * QSS_MSTRIDE + j] : 0.0;
-        y[sl] = gr[sl];
+        xo[sl] = r < QSS_NN ? Ms[r * QSS_MSTRIDE + QSS_NN] : 0.0;
       }
-      if (!qss_warp_factor<double>(a, y, ord, sh_piv[w], sh_pinv[w], lane)) {
-        if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
-        failed |= 1u << q;
-        __syncwarp();
-        continue;
-      }
+    }
+    if (!solved) {
+      if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
+      failed |= 1u << q;
       __syncwarp();
-#pragma unroll
-      for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = 0.0;
-      qss_warp_back<double>(a, y, ord, sh_piv[w], sh_pinv[w], xo, lane);
+      continue;
     }
     // the update x of cell q back to F (column tq)
 #pragma unroll
