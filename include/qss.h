@@ -27,7 +27,10 @@
  *       rho[c], T[c], Tdot[c]            c < ncells
  *       Y[k * ld + c], wdot[k * ld + c]  k < N (transported species only)
  *       jac[(i * (N+1) + j) * ld + c]    row i = d f_i, column j = d/d phi_j,
- *                                        index N stands for temperature.
+ *                                        index N stands for temperature
+ *                                        (dense artefacts; a CSR artefact
+ *                                        stores jac[p * ld + c] for the
+ *                                        entries of qss_mech_jac_pattern).
  *   - "Device" arrays are device pointers on the mechanism's device; "host"
  *     arrays are host pointers (page-locked memory gives full copy speed).
  *   - The caller owns every array; the library never frees or retains one
@@ -95,6 +98,19 @@ void qss_mech_free(qss_mech_t mech);
 int qss_mech_info(qss_mech_t mech, int* n_transported, int* n_qss, int* n_reactions,
                   const double** W_host);
 
+/* The stored Jacobian entries of a mechanism: nnz per cell, and their
+ * pattern in CSR form (row_ptr[N+2], col_idx[nnz], columns increasing within a
+ * row; the arrays stay valid until qss_mech_free).  A dense artefact stores
+ * every entry (nnz = (N+1)^2, position i (N+1) + j); an artefact built with
+ * the CSR format stores only the structural nonzeros of the generated
+ * Jacobian (entries whose expression is not identically zero: the nonzero
+ * pattern of Table memQSS, Sec. 3.2.3), entry p of row i at column
+ * col_idx[p], row_ptr[i] <= p < row_ptr[i+1].  qss_jacobian and
+ * qss_jacobian_host then write nnz rows of ld (or ncells) values instead of
+ * (N+1)^2; qss_jacobian_fd stays dense.  Any output pointer may be NULL. */
+int qss_mech_jac_pattern(qss_mech_t mech, int64_t* nnz, const int32_t** row_ptr,
+                         const int32_t** col_idx);
+
 /* Production rates (Eqs. progRates, ReacMech, with the QSS concentrations from
  * Eq. full_QSSsystem solved in SCC order).  Device arrays rho, T, Y (inputs),
  * wdot [N][ld] (output), Tdot [ld] (output, may be NULL). */
@@ -103,8 +119,9 @@ int qss_wdot(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho, con
 
 /* Analytic Jacobian, Eq. (JacExptr) with the chain rule of Eq. (JQSS), of
  * f = (wdot, Tdot) with respect to phi = (C, T), constant volume.  Device
- * arrays; jac [(N+1)^2][ld] is required, wdot [N][ld] and Tdot [ld] may be
- * NULL (they are computed anyway). */
+ * arrays; jac [nnz][ld] is required (nnz = (N+1)^2 for a dense artefact, see
+ * qss_mech_jac_pattern), wdot [N][ld] and Tdot [ld] may be NULL (they are
+ * computed anyway). */
 int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
                  const double* T, const double* Y, double* jac, double* wdot, double* Tdot,
                  void* stream);
@@ -128,7 +145,8 @@ int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 /* Central finite-difference Jacobian of f = (wdot, Tdot), the reference of
  * Eq. (frobErr): column j = (f(phi + h e_j) - f(phi - h e_j)) / (2h), with the
  * absolute step h = dC (mol/m^3) for the concentration columns and h = dT (K)
- * for the temperature column.  Same layout and arrays as qss_jacobian; costs
+ * for the temperature column.  Dense layout [(N+1)^2][ld] whatever the
+ * artefact's storage format, otherwise the same arrays as qss_jacobian; costs
  * 2(N+1) source-term evaluations per cell.  Errors: QSS_ERR_INVALID_ARG for
  * null arrays or steps that are not finite and positive. */
 int qss_jacobian_fd(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,

@@ -85,6 +85,8 @@ def lib():
         L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
+        L.qss_mech_jac_pattern.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
+                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
         L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                       _vp, _vp]
         L.qss_jacobian_host.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]
@@ -150,6 +152,13 @@ class Mechanism:
         check(lib().qss_mech_info(h, ctypes.byref(N), ctypes.byref(Q), ctypes.byref(M), ctypes.byref(W)))
         self.N, self.Q, self.M = N.value, Q.value, M.value
         self.W = [W[i] for i in range(self.N)]
+        nnz = _i64()
+        rp, ci = ctypes.POINTER(ctypes.c_int32)(), ctypes.POINTER(ctypes.c_int32)()
+        check(lib().qss_mech_jac_pattern(h, ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)))
+        # stored Jacobian entries per cell and their CSR pattern (dense: all)
+        self.jac_nnz = nnz.value
+        self.jac_row_ptr = [rp[i] for i in range(self.N + 2)]
+        self.jac_col = [ci[i] for i in range(self.jac_nnz)]
 
     @classmethod
     def from_dict(cls, mech: dict, device: int = 0, **build_kw):
@@ -202,14 +211,24 @@ class Mechanism:
     def jacobian(self, rho, T, Y, jac=None, wdot=None, Tdot=None, ncells=None, stream=None,
                  want_rates=True):
         nc, ld = self._check_state(rho, T, Y, ncells)
-        n = self.n
-        jac = self._out(jac, (n * n, ld), T)
+        jac = self._out(jac, (self.jac_nnz, ld), T)
         if want_rates:
             wdot = self._out(wdot, (self.N, ld), T)
             Tdot = self._out(Tdot, (ld,), T)
         check(lib().qss_jacobian(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
                                  _ptr(Tdot), _stream(stream)))
         return jac, wdot, Tdot
+
+    def jac_dense(self, jac):
+        """A stored Jacobian [jac_nnz][ld] as the dense [(N+1)^2][ld] array
+        (zeros off the pattern); a dense artefact's output is returned as is."""
+        n = self.n
+        if self.jac_nnz == n * n:
+            return jac
+        out = torch.zeros((n * n, jac.shape[1]), dtype=jac.dtype, device=jac.device)
+        rows = [i * n + self.jac_col[p] for i in range(n) for p in range(self.jac_row_ptr[i], self.jac_row_ptr[i + 1])]
+        out[torch.tensor(rows, device=jac.device)] = jac
+        return out
 
     def set_frontier_bytes(self, nbytes: int):
         """Size limit of the partitioned Jacobian's frontier buffer."""
@@ -229,9 +248,8 @@ class Mechanism:
             if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
                 raise ValueError(f"{nm} must be a contiguous float64 host tensor")
         nc = T.shape[0]
-        n = self.n
         if jac is None:
-            jac = torch.empty((n * n, nc), dtype=torch.float64, pin_memory=True)
+            jac = torch.empty((self.jac_nnz, nc), dtype=torch.float64, pin_memory=True)
         check(lib().qss_jacobian_host(self.h, nc, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
                                       _ptr(Tdot), chunk, None))
         return jac, wdot, Tdot

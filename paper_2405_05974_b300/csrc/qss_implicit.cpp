@@ -59,7 +59,7 @@ namespace qss {
 size_t newton_scratch_per_cell(const qss_mech_s* m, int precision) {
   (void)precision;   // both forms keep J in FP64; the FP32 factors live in registers
   const int n = m->N + 1;
-  return (size_t)n * n * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int) +
+  return (size_t)m->jac_nnz * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int) +
          frontier_bytes_per_cell(m);
 }
 
@@ -102,7 +102,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
   const size_t S = (size_t)chunk;
   double* M64 = (double*)scratch;
-  double* PHI = M64 + (size_t)n * n * S;
+  double* PHI = M64 + (size_t)m->jac_nnz * S;
   double* PHI0 = PHI + (size_t)n * S;
   double* F = PHI0 + (size_t)n * S;
   int* ACT = (int*)(F + (size_t)n * S);

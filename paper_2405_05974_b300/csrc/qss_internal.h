@@ -33,6 +33,9 @@ struct qss_mech_s {
   size_t fr_budget = size_t(4) << 30;   // bytes of that buffer (qss_mech_set_frontier_bytes)
   CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
+  // stored Jacobian entries per cell and their pattern (CSR; dense = all)
+  int64_t jac_nnz = 0;
+  std::vector<int32_t> jac_row_ptr, jac_col;
   int64_t wave_cells = 0;   // cells of one full wave of the Jacobian kernel (0: unknown)
   std::vector<double> W;
   std::string name, digest, dir;
@@ -64,6 +67,7 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
                const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
                const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
                CUstream s);
+bool jac_pattern_ok(qss_mech_s* m);
 // The chunk (in cells) for at most `cap` cells of scratch: a multiple of the
 // Jacobian kernel's wave when at least one wave fits, else of 32 (>= 32).
 int64_t chunk_cells(const qss_mech_s* m, int64_t cap);

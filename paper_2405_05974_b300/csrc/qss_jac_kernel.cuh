@@ -16,8 +16,10 @@
 // f = (wdot, Tdot) and J.  State from (rho, T, Y) or, in list mode (phi and
 // list given), of the t-th cell of the list: s = list[t] for t < *nact, state
 // phi[k * ld + s] = (C_1..C_N, T), f written at column t (wdot[k * ld + t])
-// and J written cell-contiguous, jac[t * (N+1)^2 + e] (the Newton update reads
-// one cell's matrix at a time with coalesced loads).  In list mode thread 0
+// and J written cell-contiguous, jac[t * QSS_JAC_NNZ + e] (the Newton update
+// reads one cell's matrix at a time with coalesced loads).  e is the entry's
+// storage position: i (N+1) + j for a dense artefact, its index in the CSR
+// value array for a CSR artefact (QSS_JAC_NNZ entries per cell either way).  In list mode thread 0
 // also clears *nact_next, the counter the following Newton update fills.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
 qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
@@ -37,7 +39,7 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
 #pragma unroll
     for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
     Tc = phi[QSS_N * ld + s];
-    jc = jac + c * (QSS_NN * QSS_NN);
+    jc = jac + c * QSS_JAC_NNZ;
     jstride = 1;
   } else {
     if (c >= ncells) return;

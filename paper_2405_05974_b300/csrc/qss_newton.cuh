@@ -30,7 +30,8 @@
 //
 // Scratch (global memory, one chunk of `cells` cells, leading dimension sld;
 // s = cell - c0, t = position in the active list):
-//   M64[t * NN * NN + e], e = i * NN + j J of the t-th active cell, each cell's
+//   M64[t * QSS_JAC_NNZ + e]              J of the t-th active cell (e = i NN + j,
+//                                        or the CSR position), each cell's
 //                                        matrix contiguous (coalesced staging)
 //   F [k * sld + t]                       f, then g = -G, then the update x
 //   PHI, PHI0 [k * sld + s]               iterate, initial state
@@ -444,7 +445,25 @@ __device__ __forceinline__ void qss_newton_update(
     {
       // the cell's J is contiguous (written so by the Jacobian kernel in list
       // mode): one coalesced pass, 256 bytes per warp load
-      const double* __restrict__ Jq = M64 + tq * (QSS_NN * QSS_NN);
+      const double* __restrict__ Jq = M64 + tq * QSS_JAC_NNZ;
+#ifdef QSS_JAC_CSR
+      // CSR values: M = I first, then M[i][j] += -hq J_ij at the stored
+      // positions (each position once; 1 + m and 0 + m round as the dense
+      // form's 1 + m and m)
+      for (int e = lane; e < QSS_NN * QSS_MSTRIDE; e += 32) {
+        const int r = e / QSS_MSTRIDE;
+        Ms[e] = (e == r * (QSS_MSTRIDE + 1)) ? 1.0 : 0.0;
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int p = lane; p < QSS_JAC_NNZ; p += 32) {
+        const int rc = qss_jac_rc[p];
+        const int r = rc / QSS_NN, j = rc - r * QSS_NN;
+        const double m = -hq * Jq[p];
+        fin = fin && qss_finite(m);
+        Ms[r * QSS_MSTRIDE + j] += m;
+      }
+#else
 #pragma unroll 4
       for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
         const int r = e / QSS_NN, j = e - r * QSS_NN;
@@ -452,6 +471,7 @@ __device__ __forceinline__ void qss_newton_update(
         fin = fin && qss_finite(m);
         Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
       }
+#endif
     }
     double gr[QSS_NSLOT];
 #pragma unroll

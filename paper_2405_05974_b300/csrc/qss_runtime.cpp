@@ -98,6 +98,33 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   return QSS_OK;
 }
 
+// The stored Jacobian pattern from meta.txt: absent (older or dense
+// artefacts) means dense, which is filled in here; a CSR pattern must have
+// N + 2 row pointers from 0 to jac_nnz and strictly increasing columns in
+// range within each row.
+bool jac_pattern_ok(qss_mech_s* m) {
+  const int n = m->N + 1;
+  if (m->jac_row_ptr.empty() && m->jac_col.empty()) {
+    if (m->jac_nnz != 0 && m->jac_nnz != (int64_t)n * n) return false;
+    m->jac_nnz = (int64_t)n * n;
+    for (int i = 0; i <= n; ++i) m->jac_row_ptr.push_back(i * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) m->jac_col.push_back(j);
+    return true;
+  }
+  if ((int)m->jac_row_ptr.size() != n + 1 || m->jac_row_ptr[0] != 0 ||
+      m->jac_row_ptr[n] != m->jac_nnz || (int64_t)m->jac_col.size() != m->jac_nnz ||
+      m->jac_nnz <= 0 || m->jac_nnz > (int64_t)n * n)
+    return false;
+  for (int i = 0; i < n; ++i) {
+    if (m->jac_row_ptr[i] > m->jac_row_ptr[i + 1]) return false;
+    for (int p = m->jac_row_ptr[i]; p < m->jac_row_ptr[i + 1]; ++p)
+      if (m->jac_col[p] < 0 || m->jac_col[p] >= n || (p > m->jac_row_ptr[i] && m->jac_col[p] <= m->jac_col[p - 1]))
+        return false;
+  }
+  return true;
+}
+
 }  // namespace qss
 
 using namespace qss;
@@ -105,6 +132,14 @@ using namespace qss;
 extern "C" {
 
 const char* qss_last_error(void) { return g_err.c_str(); }
+
+int qss_mech_jac_pattern(qss_mech_t m, int64_t* nnz, const int32_t** row_ptr, const int32_t** col_idx) {
+  if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
+  if (nnz) *nnz = m->jac_nnz;
+  if (row_ptr) *row_ptr = m->jac_row_ptr.data();
+  if (col_idx) *col_idx = m->jac_col.data();
+  return QSS_OK;
+}
 
 int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   if (!artefact_dir || !out) return fail(QSS_ERR_INVALID_ARG, "null argument");
@@ -127,13 +162,19 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "block") ls >> m->block;
     else if (key == "jac_parts") ls >> m->jac_parts;
     else if (key == "frontier") ls >> m->frontier;
-    else if (key == "W") {
+    else if (key == "jac_nnz") ls >> m->jac_nnz;
+    else if (key == "jac_row_ptr" || key == "jac_col") {
+      std::vector<int32_t>& v = key == "jac_col" ? m->jac_col : m->jac_row_ptr;
+      int32_t x;
+      while (ls >> x) v.push_back(x);
+    } else if (key == "W") {
       double w;
       while (ls >> w) m->W.push_back(w);
     }
   }
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
-      m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N)) {
+      m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
+      !jac_pattern_ok(m)) {
     delete m;
     return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
   }
@@ -365,12 +406,13 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
   if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
-  const int N = m->N, n = N + 1;
+  const int N = m->N;
   int64_t S = chunk > 0 ? chunk : 65536;
   S = std::min<int64_t>(S, ncells);
   S = (S + 31) / 32 * 32;
   const size_t fpc = frontier_bytes_per_cell(m) / sizeof(double);
-  const size_t per_cell = (size_t)(2 + N + N + 1 + n * n) + fpc;
+  const size_t nnz = (size_t)m->jac_nnz;
+  const size_t per_cell = (size_t)(2 + N + N + 1) + nnz + fpc;
   const size_t need = per_cell * (size_t)S * sizeof(double);
   if (m->stage_bytes < need) {
     for (int b = 0; b < 2; ++b) {
@@ -403,11 +445,11 @@ int qss_jacobian_host(qss_mech_t m, int64_t ncells, const double* rho, const dou
     if ((rc = copy2d(d_rho, false, P, rho + c0, true, hp, w, 1, s))) return rc;
     if ((rc = copy2d(d_T, false, P, T + c0, true, hp, w, 1, s))) return rc;
     if ((rc = copy2d(d_Y, false, P, Y + c0, true, hp, w, N, s))) return rc;
-    double* d_fr = d_J + (size_t)n * n * S;   // frontier (partitioned Jacobian only)
+    double* d_fr = d_J + nnz * S;   // frontier (partitioned Jacobian only)
     if ((rc = jac_launch(m, cs, S, d_rho, d_T, d_Y, d_J, d_w, d_Td, nullptr, nullptr, nullptr,
                          nullptr, fpc ? d_fr : nullptr, S, s)))
       return rc;
-    if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, (size_t)n * n, s))) return rc;
+    if ((rc = copy2d(jac + c0, true, hp, d_J, false, P, w, nnz, s))) return rc;
     if (wdot && (rc = copy2d(wdot + c0, true, hp, d_w, false, P, w, N, s))) return rc;
     if (Tdot && (rc = copy2d(Tdot + c0, true, hp, d_Td, false, P, w, 1, s))) return rc;
   }

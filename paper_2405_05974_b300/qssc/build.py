@@ -132,7 +132,8 @@ def _complete(out: str) -> bool:
 
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
-                    t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0) -> str:
+                    t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
+                    jac_format: str = "dense") -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -141,12 +142,16 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     ``jac_parts`` >= 2 splits the Jacobian into a prefix kernel and that many
     column-group kernels (``emit.emit_partitioned_source``), each compiled in
     its own translation unit; ``replace_nop`` > 0 applies Alg. 2's
-    common-subexpression replacement with that operation threshold."""
+    common-subexpression replacement with that operation threshold;
+    ``jac_format`` "csr" makes the Jacobian kernels store only the structural
+    nonzeros, in CSR order (``emit.jac_layout``)."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
         variant += (f"parts{int(jac_parts)}",)
     if replace_nop > 0:
         variant += (f"nop{int(replace_nop)}",)
+    if jac_format != "dense":
+        variant += (jac_format,)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -156,13 +161,13 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     t0 = time.time()
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
-    src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop)
+    src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")
     parts = {"mech_sizes.inc": src[:iw], "mech_wdot.inc": src[iw:ij], "mech_jac.inc": src[ij:]}
     if jac_parts >= 2:
-        prefix_src, group_srcs, pmeta = emit.emit_partitioned_source(model, int(jac_parts))
+        prefix_src, group_srcs, pmeta = emit.emit_partitioned_source(model, int(jac_parts), jac_format)
         meta.update(pmeta)
         del parts["mech_jac.inc"]
         parts["mech_jac_prefix.inc"] = prefix_src
@@ -240,6 +245,10 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         f.write(f"N {meta['N']}\nQ {meta['Q']}\nM {meta['M']}\nblock {block}\n")
         if jac_parts >= 2:
             f.write(f"jac_parts {int(jac_parts)}\nfrontier {meta['frontier']}\n")
+        f.write(f"jac_nnz {meta['jac_stored']}\n")
+        if jac_format != "dense":
+            f.write("jac_row_ptr " + " ".join(map(str, meta["jac_row_ptr"])) + "\n")
+            f.write("jac_col " + " ".join(map(str, meta["jac_col"])) + "\n")
         f.write("W " + " ".join(repr(w) for w in meta["W"]) + "\n")
     if os.path.exists(out):
         shutil.rmtree(out)

@@ -254,11 +254,36 @@ def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
 
 
-def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0) -> Tuple[str, dict]:
+JAC_FORMATS = ("dense", "csr")
+
+
+def jac_layout(model, jac_format: str = "dense"):
+    """Storage position of each Jacobian entry (i, c) that the kernels write.
+    "dense": every entry, position i (N+1) + c.  "csr": only the structural
+    nonzeros (entries whose expression is not identically zero), in row-major
+    order, position = index in the CSR value array.  Returns (pos, row_ptr,
+    col_idx); row_ptr / col_idx describe the stored pattern in both formats."""
+    if jac_format not in JAC_FORMATS:
+        raise ValueError(f"unknown Jacobian format {jac_format!r}")
+    g = model.g
+    n = model.ir.N + 1
+    pos, row_ptr, col = {}, [0], []
+    for i in range(n):
+        for c in range(n):
+            if jac_format == "dense" or model.jac[i][c] != g.ZERO:
+                pos[(i, c)] = len(col)
+                col.append(c)
+        row_ptr.append(len(col))
+    return pos, row_ptr, col
+
+
+def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
+                          jac_format: str = "dense") -> Tuple[str, dict]:
     ir = model.ir
     N, Q = ir.N, ir.Q
     n = N + 1
     g = model.g
+    pos, row_ptr, col = jac_layout(model, jac_format)
     inputs = {model.C[k]: f"C{k}" for k in range(N)}
     inputs[model.T] = "T"
     fd_prologue = []
@@ -278,7 +303,8 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0) -> Tuple[
     out_j = []
     for c in range(n):
         for i in range(n):
-            out_j.append((f"jac[{i * n + c} * jstride] = {{v}};", model.jac[i][c]))
+            if (i, c) in pos:
+                out_j.append((f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]))
     em2 = Emitter(model, inputs, replace_nop=replace_nop)
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
     hdr = [
@@ -289,8 +315,16 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0) -> Tuple[
         f"#define QSS_N {N}",
         f"#define QSS_Q {Q}",
         f"#define QSS_NN {n}",
+        f"#define QSS_JAC_NNZ {len(col)}   // stored Jacobian entries per cell ({jac_format})",
         "",
     ]
+    if jac_format == "csr":
+        # position p of the CSR value array -> i * (N+1) + c, for kernels that
+        # need the dense matrix (the Newton update)
+        rc = [i * n + c for i in range(n) for c in col[row_ptr[i]:row_ptr[i + 1]]]
+        hdr.append("#define QSS_JAC_CSR 1")
+        hdr.append("__constant__ unsigned short qss_jac_rc[QSS_JAC_NNZ] = {" + ", ".join(map(str, rc)) + "};")
+        hdr.append("")
     unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
     hdr.append("__constant__ double qss_inv_W[QSS_N] = {" + ", ".join(_lit(1.0 / w) for w in ir.W) + "};")
     hdr.append("")
@@ -307,6 +341,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0) -> Tuple[
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
+        "jac_format": jac_format, "jac_stored": len(col), "jac_row_ptr": row_ptr, "jac_col": col,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
         "fp64_instr_wdot": fp64_instructions(cnt_w), "fp64_instr_jac": fp64_instructions(cnt_j),
@@ -431,7 +466,7 @@ def partition_jacobian(model, K: int, split_t: bool = True):
     return groups, sorted(frontier), needs
 
 
-def emit_partitioned_source(model, K: int):
+def emit_partitioned_source(model, K: int, jac_format: str = "dense"):
     """Sources of the partitioned Jacobian: the prefix device function
     qss_jac_prefix(C, T, wdot, Tdot, wstride, fr, fstride) and, per group,
     qss_jac_group(fr, fstride, jac, jstride).  The frontier array fr holds,
@@ -441,6 +476,7 @@ def emit_partitioned_source(model, K: int):
     N = ir.N
     n = N + 1
     groups, frontier, needs = partition_jacobian(model, K)
+    pos, _, _ = jac_layout(model, jac_format)
     slot = {x: n + i for i, x in enumerate(frontier)}
     inputs = {model.C[k]: f"C{k}" for k in range(N)}
     inputs[model.T] = "T"
@@ -466,7 +502,8 @@ def emit_partitioned_source(model, K: int):
     group_src, group_cnt = [], []
     for gi, entries in enumerate(groups):
         leaves = {x: f"F{slot[x]}" for x in needs[gi]}
-        out_j = [(f"jac[{i * n + c} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries]
+        out_j = [(f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries
+                 if (i, c) in pos]
         body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ")
         loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
         loads += [f"  const double T = fr[{N} * fstride];"]

@@ -146,3 +146,61 @@ def test_jacobian_variant_models_match_oracle_on_cpu(variant, tcol):
         want = ref["jac"][:, c]
         tol = 1e-9 * np.abs(want) + 1e-20 + 64 * ref["jac_err"][:, c]
         assert np.all(np.abs(got - want) <= tol), np.argwhere(np.abs(got - want) > tol)[:5]
+
+
+@pytest.mark.parametrize("key", ["tiny", "hydrocarbon"])
+def test_csr_layout_is_the_structural_pattern(key):
+    """The CSR storage order lists exactly the entries whose expression is not
+    identically zero, row by row with increasing columns; every such entry is
+    nonzero at some sampled state (the oracle's dense Jacobian), so the pattern
+    is not padded with entries that are always zero."""
+    from paper_2405_05974_b300.qssc import emit as qemit
+    m = workloads.mechanism(key)
+    ir = qmech.parse(m)
+    mod = qmodel.build_model(ir)
+    n = ir.N + 1
+    pos, row_ptr, col = qemit.jac_layout(mod, "csr")
+    assert row_ptr[0] == 0 and row_ptr[-1] == len(col) == len(pos) and len(row_ptr) == n + 1
+    for i in range(n):
+        cols = col[row_ptr[i]:row_ptr[i + 1]]
+        assert cols == sorted(set(cols))
+        for p, c in zip(range(row_ptr[i], row_ptr[i + 1]), cols):
+            assert pos[(i, c)] == p
+    nz = {(i, c) for i in range(n) for c in range(n) if mod.jac[i][c] != mod.g.ZERO}
+    assert set(pos) == nz
+    om = oracle.OracleMech(m)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], 64)
+    J = om.eval(rho, T, Y)["jac"]
+    seen = np.any(J != 0.0, axis=1).reshape(n, n)
+    assert all(seen[i, c] for i, c in nz)
+    assert not any(seen[i, c] for i in range(n) for c in range(n) if (i, c) not in nz)
+    dpos, drp, dcol = qemit.jac_layout(mod, "dense")
+    assert len(dpos) == n * n and dpos[(2, 3)] == 2 * n + 3 and drp == [i * n for i in range(n + 1)]
+
+
+def test_csr_artefact_source_and_meta():
+    """A CSR artefact stores each pattern position exactly once in the
+    generated Jacobian (and in the partitioned groups), and its meta.txt
+    carries the pattern the runtime validates."""
+    m = workloads.mechanism("tiny")
+    for parts in (0, 2):
+        art = qbuild.build_mechanism(m, jac_format="csr", jac_parts=parts)
+        meta = qbuild.load_meta(art)
+        nnz = meta["jac_stored"]
+        assert meta["jac_format"] == "csr" and nnz == meta["jac_nnz"] < (meta["N"] + 1) ** 2
+        srcs = [f for f in os.listdir(art) if f.startswith("mech_jac")]
+        stored = []
+        for f in srcs:
+            stored += [int(x) for x in re.findall(r"jac\[(\d+) \* jstride\]", open(os.path.join(art, f)).read())]
+        assert sorted(stored) == list(range(nnz))
+        sizes = open(os.path.join(art, "mech_sizes.inc")).read()
+        assert f"#define QSS_JAC_NNZ {nnz}" in sizes and "#define QSS_JAC_CSR 1" in sizes
+        n = meta["N"] + 1
+        rc = [int(x) for x in re.search(r"qss_jac_rc\[QSS_JAC_NNZ\] = \{([^}]*)\}", sizes).group(1).split(",")]
+        assert rc == [i * n + c for i in range(n) for c in meta["jac_col"][meta["jac_row_ptr"][i]:meta["jac_row_ptr"][i + 1]]]
+        txt = dict(line.split(" ", 1) for line in open(os.path.join(art, "meta.txt")).read().splitlines())
+        assert int(txt["jac_nnz"]) == nnz
+        assert [int(x) for x in txt["jac_row_ptr"].split()] == meta["jac_row_ptr"]
+        assert [int(x) for x in txt["jac_col"].split()] == meta["jac_col"]
+    dense = qbuild.load_meta(qbuild.build_mechanism(m))
+    assert dense["jac_format"] == "dense" and dense["jac_stored"] == (dense["N"] + 1) ** 2
