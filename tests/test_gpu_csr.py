@@ -41,7 +41,7 @@ def dense_rows(gm):
 @pytest.mark.parametrize("key,parts,ncells", [("tiny", 0, 3001), ("tiny", 2, 3001), ("hydrocarbon", 0, 2047)])
 def test_csr_values_equal_dense(key, parts, ncells):
     m = workloads.mechanism(key)
-    gd, gc = gpu_mech(key), gpu_mech(key, "csr", parts)
+    gd, gc = gpu_mech(key, "dense", parts), gpu_mech(key, "csr", parts)   # same kernels but the stores
     n = gd.n
     assert gd.jac_nnz == n * n and gc.jac_nnz < n * n
     assert len(gc.jac_row_ptr) == n + 1 and gc.jac_row_ptr[-1] == gc.jac_nnz
