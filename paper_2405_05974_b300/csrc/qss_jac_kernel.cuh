@@ -16,11 +16,14 @@
 // f = (wdot, Tdot) and J.  State from (rho, T, Y) or, in list mode (phi and
 // list given), of the t-th cell of the list: s = list[t] for t < *nact, state
 // phi[k * ld + s] = (C_1..C_N, T), f written at column t (wdot[k * ld + t])
-// and J written cell-contiguous, jac[t * QSS_JAC_NNZ + e] (the Newton update
-// reads one cell's matrix at a time with coalesced loads).  e is the entry's
+// and J written in groups of four cells, entry e of cell t at
+// jac[(t / 4) * 4 * QSS_JAC_NNZ + 4 e + t % 4]: a warp's store of one entry
+// fills eight whole 32-byte sectors, and the Newton update, whose warps take
+// consecutive cells, reads each sector for four cells.  e is the entry's
 // storage position: i (N+1) + j for a dense artefact, its index in the CSR
-// value array for a CSR artefact (QSS_JAC_NNZ entries per cell either way).  In list mode thread 0
-// also clears *nact_next, the counter the following Newton update fills.
+// value array for a CSR artefact (QSS_JAC_NNZ entries per cell either way).
+// In list mode thread 0 also clears *nact_next, the counter the following
+// Newton update fills.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
 qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                const double* __restrict__ T, const double* __restrict__ Y,
@@ -39,8 +42,8 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
 #pragma unroll
     for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
     Tc = phi[QSS_N * ld + s];
-    jc = jac + c * QSS_JAC_NNZ;
-    jstride = 1;
+    jc = jac + (c >> 2) * (4 * QSS_JAC_NNZ) + (c & 3);
+    jstride = 4;
   } else {
     if (c >= ncells) return;
     qss_unpack(c, ld, rho, Y, C);

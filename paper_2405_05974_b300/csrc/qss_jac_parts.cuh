@@ -56,9 +56,10 @@ qss_jac_prefix_kernel(long long ncells, long long ld, const double* __restrict__
 
 #ifdef QSS_JAC_GROUP
 // The group's Jacobian columns from the frontier of cell c.  With nact given
-// (list mode) cells c < *nact are processed and J is written cell-contiguous,
-// jac[c * QSS_JAC_NNZ + e] (the Newton update's layout); otherwise cells
-// c < ncells, jac[e * ld + c] (e: the entry's dense or CSR storage position).
+// (list mode) cells c < *nact are processed and J is written in groups of
+// four cells, jac[(c / 4) * 4 * QSS_JAC_NNZ + 4 e + c % 4] (the Newton
+// update's layout); otherwise cells c < ncells, jac[e * ld + c] (e: the
+// entry's dense or CSR storage position).
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
 qss_jac_group_kernel(long long ncells, const double* __restrict__ fr, long long fld,
                      double* __restrict__ jac, long long ld, const int* __restrict__ nact) {
@@ -67,8 +68,8 @@ qss_jac_group_kernel(long long ncells, const double* __restrict__ fr, long long 
   long long jstride;
   if (nact) {
     if (c >= *nact) return;
-    jc = jac + c * QSS_JAC_NNZ;
-    jstride = 1;
+    jc = jac + (c >> 2) * (4 * QSS_JAC_NNZ) + (c & 3);
+    jstride = 4;
   } else {
     if (c >= ncells) return;
     jc = jac + c;

@@ -13,9 +13,10 @@
 // has converged or failed it leaves the list, so later launches cost only what
 // the remaining cells need.
 //
-// The update kernel solves one cell's system at a time per warp, with partial
-// pivoting (warp arg-max, lowest index on ties) and the right-hand side
-// eliminated with the matrix.
+// The update kernel solves one cell's system at a time per warp (the warps
+// stride over the active list, so a nearly empty list costs one cell per
+// warp), with partial pivoting (warp arg-max, lowest index on ties) and the
+// right-hand side eliminated with the matrix.
 //   update_fp64    elimination and solve in FP64, in place in shared memory,
 //                  the trailing block of each step split evenly over the
 //                  lanes (qss_smem_solve_fp64).
@@ -30,10 +31,12 @@
 //
 // Scratch (global memory, one chunk of `cells` cells, leading dimension sld;
 // s = cell - c0, t = position in the active list):
-//   M64[t * QSS_JAC_NNZ + e]              J of the t-th active cell (e = i NN + j,
-//                                        or the CSR position), each cell's
-//                                        matrix contiguous (coalesced staging)
-//   F [k * sld + t]                       f, then g = -G, then the update x
+//   M64[(t/4) 4 QSS_JAC_NNZ + 4 e + t%4]  J of the t-th active cell (e = i NN + j,
+//                                        or the CSR position), four cells
+//                                        interleaved (whole-sector stores,
+//                                        sectors shared by consecutive warps)
+//   F [k * sld + t]                       f at the current iterate (written by
+//                                        the Jacobian kernel in list mode)
 //   PHI, PHI0 [k * sld + s]               iterate, initial state
 //   ACT, ST, IT [s]                       active flag, status, iterations
 //   LIST[2][sld], NACT[2]                 active lists (double-buffered)
@@ -393,11 +396,12 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
 template <bool FP32IR>
 __device__ __forceinline__ void qss_newton_update(
     long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
-    const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,
+    const double* __restrict__ PHI0, const double* __restrict__ F, const double* __restrict__ M64,
     int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT, const int* __restrict__ LIST,
     const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
     double* __restrict__ FN0, double* __restrict__ FN1, const QssNewtonOpts o) {
   constexpr int W = FP32IR ? QSS_UPD_WARPS32 : QSS_UPD_WARPS;
+  const unsigned FULL = 0xffffffffu;
   // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows; the
   // FP64 form keeps g in the pad column and solves in place)
   __shared__ double sh_m[W * QSS_NN * QSS_MSTRIDE];
@@ -409,45 +413,46 @@ __device__ __forceinline__ void qss_newton_update(
   __shared__ int sh_e[FP32IR ? W : 1][2 * QSS_NN];
   __shared__ float sh_pinvf[FP32IR ? W : 1][QSS_NN];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long t0 = ((long long)blockIdx.x * W + w) * 32;
   const int nact = *NACT;
-  if (t0 >= nact) return;
-  const long long t = t0 + lane;
-  bool mine = t < nact;
-  const int s = mine ? LIST[t] : 0;
-  double h = 0.0;
-  if (mine) {   // g = -G(phi) into F, own cell
-    h = dt[dt_stride ? c0 + s : 0];
-    IT[s] += 1;
+  const long long nwarps = (long long)gridDim.x * W;
+  double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of [M | g], M = I - h J
+  // one active cell per warp at a time, the warps striding over the list:
+  // when few cells are left (the last Newton iterations) each gets its own
+  // warp instead of queueing behind 31 others
+  for (long long tq = (long long)blockIdx.x * W + w; tq < nact; tq += nwarps) {
+    const int s = LIST[tq];
+    const double hq = dt[dt_stride ? c0 + s : 0];
+    const int it = IT[s] + 1;
+    // g = -G(phi) = -(phi - phi0 - h f), entry i on lane i % 32 (slot i / 32);
+    // f optionally recorded at the first iterate (phi0) and the latest
+    double gr[QSS_NSLOT];
     bool ok = true;
 #pragma unroll
-    for (int i = 0; i < QSS_NN; ++i) {
-      const double f = F[i * sld + t];
-      // optional record of f: at the first iterate (phi0) and the latest
-      if (FN0 && IT[s] == 1) FN0[i * sld + s] = f;
-      if (FN1) FN1[i * sld + s] = f;
-      const double g = -(PHI[i * sld + s] - PHI0[i * sld + s] - h * f);
-      F[i * sld + t] = g;
-      ok = ok && qss_finite(g);
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+      const int i = lane + 32 * sl;
+      gr[sl] = 0.0;
+      if (i < QSS_NN) {
+        const double f = F[i * sld + tq];
+        if (FN0 && it == 1) FN0[i * sld + s] = f;
+        if (FN1) FN1[i * sld + s] = f;
+        gr[sl] = -(PHI[i * sld + s] - PHI0[i * sld + s] - hq * f);
+        ok = ok && qss_finite(gr[sl]);
+      }
     }
-    if (!ok) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; mine = false; }
-  }
-  __syncwarp();
-  unsigned todo = __ballot_sync(0xffffffffu, mine);
-  unsigned failed = 0;
-  while (todo) {
-    const int q = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const double hq = __shfl_sync(0xffffffffu, h, q);
-    const long long tq = t0 + q;
+    __syncwarp();
+    if (lane == 0) IT[s] = it;
+    if (!__all_sync(FULL, ok)) {
+      if (lane == 0) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
+      continue;
+    }
     bool fin = true;
-    double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of [M | g], M = I - hq J
     {
-      // the cell's J is contiguous (written so by the Jacobian kernel in list
-      // mode): one coalesced pass, 256 bytes per warp load
-      const double* __restrict__ Jq = M64 + tq * QSS_JAC_NNZ;
+      // the cell's J, interleaved with three neighbours (the Jacobian
+      // kernel's list-mode layout): every 32-byte sector this warp loads also
+      // holds the same entry of the cells the next warps take
+      const double* __restrict__ Jq = M64 + (tq >> 2) * (4 * QSS_JAC_NNZ) + (tq & 3);
 #ifdef QSS_JAC_CSR
-      // CSR values: M = I first, then M[i][j] += -hq J_ij at the stored
+      // CSR values: M = I first, then M[i][j] += -h J_ij at the stored
       // positions (each position once; 1 + m and 0 + m round as the dense
       // form's 1 + m and m)
       for (int e = lane; e < QSS_NN * QSS_MSTRIDE; e += 32) {
@@ -459,7 +464,7 @@ __device__ __forceinline__ void qss_newton_update(
       for (int p = lane; p < QSS_JAC_NNZ; p += 32) {
         const int rc = qss_jac_rc[p];
         const int r = rc / QSS_NN, j = rc - r * QSS_NN;
-        const double m = -hq * Jq[p];
+        const double m = -hq * Jq[4 * p];
         fin = fin && qss_finite(m);
         Ms[r * QSS_MSTRIDE + j] += m;
       }
@@ -467,23 +472,22 @@ __device__ __forceinline__ void qss_newton_update(
 #pragma unroll 4
       for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
         const int r = e / QSS_NN, j = e - r * QSS_NN;
-        const double m = -hq * Jq[e];
+        const double m = -hq * Jq[4 * e];
         fin = fin && qss_finite(m);
         Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
       }
 #endif
     }
-    double gr[QSS_NSLOT];
+    if (!FP32IR) {
 #pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const int r = lane + 32 * sl;
-      gr[sl] = r < QSS_NN ? F[r * sld + tq] : 0.0;
-      if (!FP32IR && r < QSS_NN) Ms[r * QSS_MSTRIDE + QSS_NN] = gr[sl];
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+        const int r = lane + 32 * sl;
+        if (r < QSS_NN) Ms[r * QSS_MSTRIDE + QSS_NN] = gr[sl];
+      }
     }
     __syncwarp();
-    if (!__all_sync(0xffffffffu, fin)) {
-      if (lane == q) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
-      failed |= 1u << q;
+    if (!__all_sync(FULL, fin)) {
+      if (lane == 0) { ST[s] = QSS_CELL_NONFINITE; ACT[s] = 0; }
       continue;
     }
     double xo[QSS_NSLOT];   // this lane's entries of the solution (index lane + 32 slot)
@@ -499,53 +503,49 @@ __device__ __forceinline__ void qss_newton_update(
         xo[sl] = r < QSS_NN ? Ms[r * QSS_MSTRIDE + QSS_NN] : 0.0;
       }
     }
+    __syncwarp();   // the next cell overwrites this warp's shared arrays
     if (!solved) {
-      if (lane == q) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
-      failed |= 1u << q;
-      __syncwarp();
+      if (lane == 0) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
       continue;
     }
-    // the update x of cell q back to F (column tq)
+    // phi += x; weighted RMS of the update over the lanes; next list
+    double acc = 0.0;
+    bool pfin = true;
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const int j = lane + 32 * sl;
-      if (j < QSS_NN) F[j * sld + tq] = xo[sl];
+      const int i = lane + 32 * sl;
+      if (i < QSS_NN) {
+        const double x = xo[sl];
+        const double p = PHI[i * sld + s] + x;
+        PHI[i * sld + s] = p;
+        const double wgt = o.rtol * fabs(p) + (i < QSS_N ? o.atol_C : o.atol_T);
+        const double qv = x / wgt;
+        acc = fma(qv, qv, acc);
+        pfin = pfin && qss_finite(p);
+      }
     }
-    __syncwarp();
-  }
-  __syncwarp();
-  if (!mine || ((failed >> lane) & 1u)) return;
-  // own cell: update phi, convergence test, next list
-  double acc = 0.0;
-  bool fin = true;
 #pragma unroll
-  for (int i = 0; i < QSS_NN; ++i) {
-    const double x = F[i * sld + t];
-    const double p = PHI[i * sld + s] + x;
-    PHI[i * sld + s] = p;
-    const double wgt = o.rtol * fabs(p) + (i < QSS_N ? o.atol_C : o.atol_T);
-    const double qv = x / wgt;
-    acc = fma(qv, qv, acc);
-    fin = fin && qss_finite(p);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    pfin = __all_sync(FULL, pfin);
+    if (lane == 0) {
+      if (!pfin) {
+        ST[s] = QSS_CELL_NONFINITE;
+        ACT[s] = 0;
+      } else if (acc <= (double)QSS_NN) {
+        ST[s] = QSS_CELL_CONVERGED;
+        ACT[s] = 0;
+      } else if (it >= o.max_iter) {
+        ACT[s] = 0;   // status stays MAXITER
+      } else {
+        LIST2[atomicAdd(NACT2, 1)] = s;
+      }
+    }
   }
-  bool keep = false;
-  if (!fin) {
-    ST[s] = QSS_CELL_NONFINITE;
-    ACT[s] = 0;
-  } else if (acc <= (double)QSS_NN) {
-    ST[s] = QSS_CELL_CONVERGED;
-    ACT[s] = 0;
-  } else if (IT[s] >= o.max_iter) {
-    ACT[s] = 0;   // status stays MAXITER
-  } else {
-    keep = true;
-  }
-  if (keep) LIST2[atomicAdd(NACT2, 1)] = s;
 }
 
 #define QSS_UPDATE_PARAMS                                                                         \
   long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,          \
-      const double* __restrict__ PHI0, double* __restrict__ F, const double* __restrict__ M64,    \
+      const double* __restrict__ PHI0, const double* __restrict__ F, const double* __restrict__ M64, \
       int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT,                          \
       const int* __restrict__ LIST, const int* __restrict__ NACT, int* __restrict__ LIST2,        \
       int* __restrict__ NACT2, long long sld, double* __restrict__ FN0, double* __restrict__ FN1, \
