@@ -16,6 +16,7 @@ with outputs written at ``wdot[i * wstride]`` and ``jac[e * jstride]``.
 """
 from __future__ import annotations
 
+import re
 from collections import Counter
 from typing import Dict, List, Tuple
 
@@ -355,6 +356,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
 # Partitioned Jacobian: a shared prefix kernel and K column-group kernels
 # ---------------------------------------------------------------------------
 _MATERIAL = (ADD, SUB, MUL, RECIP, EXP, LOG, SELECT)
+_FRONTIER_NAME = re.compile(r"\bF\d+\b")
 
 
 def _op_cost(g, x):
@@ -507,7 +509,17 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense"):
         body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ")
         loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
         loads += [f"  const double T = fr[{N} * fstride];"]
-        loads += [f"  const double F{slot[x]} = fr[{slot[x]} * fstride];" for x in needs[gi]]
+        # each frontier value is loaded just before its first use: loaded all
+        # at the top, a group's hundreds of values go straight from the load
+        # to the spill stack
+        pending = {f"F{slot[x]}": f"  const double F{slot[x]} = fr[{slot[x]} * fstride];" for x in needs[gi]}
+        lazy = []
+        for line in body_g:
+            for nm in _FRONTIER_NAME.findall(line):
+                if nm in pending:
+                    lazy.append(pending.pop(nm))
+            lazy.append(line)
+        body_g = lazy + list(pending.values())
         group_src.append("\n".join([
             f"// entry group {gi} of {K}: columns {sorted({c for _, c in entries if c != N})}"
             + (f" and rows {sorted(i for i, c in entries if c == N)} of the T column" if any(c == N for _, c in entries) else ""),
