@@ -76,7 +76,8 @@ def lib():
         L.oracle_jac_cs_fixed_cq.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, _dp,
                                              ctypes.c_double, _dp, ctypes.c_int]
         L.oracle_integrate.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, ctypes.c_int, _dp, _dp, _dp] + \
-            [ctypes.c_double] * 5 + [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, _ip, _ip, ctypes.c_int]
+            [ctypes.c_double] * 5 + [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_int, _ip, _ip,
+                                                                               ctypes.c_int]
         L.oracle_qss_residual.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp, _dp, _dp,
                                           ctypes.c_int]
         L.oracle_qss_newton_q128.argtypes = [ctypes.c_void_p, _i64, _i64, _dp, _dp, _dp,
@@ -326,15 +327,16 @@ class OracleMech:
 
     def integrate(self, rho, T, Y, dt_total, rtol=1e-4, atol_C=1e-10, atol_T=1e-4, h0=0.0, h_min=1e-14,
                   max_rounds=400, newton_rtol=1e-12, newton_atol_C=1e-20, newton_atol_T=1e-10,
-                  max_iter=20, nthreads=0):
-        """Integration over dt_total by error-controlled backward-Euler
-        substeps; returns (T_new, Y_new, nsteps, status)."""
+                  max_iter=20, order=1, nthreads=0):
+        """Integration over dt_total by error-controlled substeps of order 1
+        (backward Euler) or 2 (variable-step BDF2); returns (T_new, Y_new,
+        nsteps, status)."""
         rho, T, Y, ld = self._state(rho, T, Y)
         T2, Y2 = T.copy(), Y.copy()
         dt = np.atleast_1d(_f64(dt_total))
         ns = np.zeros(ld, np.int32); st = np.zeros(ld, np.int32)
         lib().oracle_integrate(self.h, ld, ld, _p(dt), 1 if dt.size > 1 else 0, _p(rho), _p(T2), _p(Y2),
                                rtol, atol_C, atol_T, h0, h_min, max_rounds, newton_rtol, newton_atol_C,
-                               newton_atol_T, max_iter, _p(ns, _ip), _p(st, _ip), nthreads)
+                               newton_atol_T, max_iter, int(order), _p(ns, _ip), _p(st, _ip), nthreads)
         return T2, Y2, ns, st
 

@@ -687,11 +687,16 @@ int jac_fd_batch(const Mech* m, int64_t ncells, int64_t ld, const double* rho, c
 // update is <= 1 (status 0), on an evaluation or solve failure (2) or after
 // max_iter iterations (1).  f0 = f(phi0) (the first iterate), f1 = f at the
 // last iterate evaluated.
-int be_newton(const Mech& m, const std::vector<double>& phi0, double h_dt, double rtol,
-              double atol_C, double atol_T, int max_iter, std::vector<double>& phi,
-              std::vector<double>& f0, std::vector<double>& f1, int* iters) {
+// Newton on G(phi) = phi - cterm - gamma f(phi) from the iterate phi_init
+// (backward Euler: cterm = phi_init = phi_n, gamma = h; BDF2: cterm = the
+// combination of phi_n and phi_n-1, gamma = beta h).  f0 is f at the first
+// iterate, f1 at the last one.
+int newton_solve(const Mech& m, const std::vector<double>& phi_init, const std::vector<double>& cterm,
+                 double gamma, double rtol, double atol_C, double atol_T, int max_iter,
+                 std::vector<double>& phi, std::vector<double>& f0, std::vector<double>& f1,
+                 int* iters) {
   const int N = m.N, n = N + 1;
-  phi = phi0;
+  phi = phi_init;
   int st = 1, it = 0;
   for (it = 1; it <= max_iter; ++it) {
     CellOut<double> o;
@@ -701,8 +706,8 @@ int be_newton(const Mech& m, const std::vector<double>& phi0, double h_dt, doubl
       double fi = i < N ? o.wdot[i] : o.Tdot;
       if (it == 1) f0[i] = fi;
       f1[i] = fi;
-      G[i] = phi[i] - phi0[i] - h_dt * fi;
-      for (int j = 0; j < n; ++j) Mx[i * n + j] = (i == j ? 1.0 : 0.0) - h_dt * o.J[i * n + j];
+      G[i] = phi[i] - cterm[i] - gamma * fi;
+      for (int j = 0; j < n; ++j) Mx[i * n + j] = (i == j ? 1.0 : 0.0) - gamma * o.J[i * n + j];
     }
     std::vector<double> d(n);
     for (int i = 0; i < n; ++i) d[i] = -G[i];
@@ -721,6 +726,12 @@ int be_newton(const Mech& m, const std::vector<double>& phi0, double h_dt, doubl
   if (it > max_iter) it = max_iter;
   *iters = it;
   return st;
+}
+
+int be_newton(const Mech& m, const std::vector<double>& phi0, double h_dt, double rtol,
+              double atol_C, double atol_T, int max_iter, std::vector<double>& phi,
+              std::vector<double>& f0, std::vector<double>& f1, int* iters) {
+  return newton_solve(m, phi0, phi0, h_dt, rtol, atol_C, atol_T, max_iter, phi, f0, f1, iters);
 }
 
 }  // namespace
@@ -1124,22 +1135,37 @@ int oracle_be_step(void* h, int64_t ncells, int64_t ld, const double* dt, int dt
   return nbad;
 }
 
-// Integration over dt_total by backward-Euler substeps with local error
-// control (each cell on its own): a substep of size h is the Newton solve
-// above from the current state; its local error is estimated as
-// e = h/2 (f(last iterate) - f(start)), err = sqrt(mean((e_i / w_i)^2)) with
-// w_i = rtol |phi_i,new| + atol_i.  Accepted when err <= 1 (next
-// h = h min(4, max(0.2, 0.9/sqrt(err))), capped by what remains); rejected:
-// h max(0.2, min(0.9, 0.9/sqrt(err))); Newton failure: h/4.  The interval is
-// done when the remainder is <= 1e-12 dt_total; a cell fails (status 2) when
-// h < h_min dt_total, and stops with status 1 after max_rounds attempts.
+// Integration over dt_total by substeps with local error control (each cell
+// on its own), of order 1 (backward Euler) or 2 (variable-step BDF2 after a
+// first backward-Euler substep).  A substep of size h from phi_n is the
+// Newton solve above:
+//   order 1:  phi - phi_n - h f(phi) = 0;
+//   BDF2 (previous accepted substep h_p, w = h / h_p):
+//     phi - a1 phi_n - a2 phi_n-1 - beta h f(phi) = 0,
+//     a1 = (1+w)^2/(1+2w), a2 = -w^2/(1+2w), beta = (1+w)/(1+2w)
+//   (the quadratic through t_n-1, t_n, t_n+1 with slope f at t_n+1).
+// Local error estimates from f at the first iterate (f_n) and the last (f_n+1):
+//   order 1:  e = h/2 (f_n+1 - f_n)                       (h^2/2 times phi'');
+//   BDF2:     e = h (1+w)/(3(1+2w)) ((f_n+1 - f_n) - w (f_n - f_n-1)),
+// the formula's truncation error (1+w)^2/(6w(1+2w)) h^3 d3phi/dt3 with the
+// third derivative from the second divided difference of f over t_n-1, t_n,
+// t_n+1.  err = sqrt(mean((e_i / w_i)^2)), w_i = rtol |phi_i,new| + atol_i.
+// Accepted when err <= 1: next h = h min(g_max, max(0.2, 0.9 err^(-1/(p+1))))
+// (p the substep's order; g_max = 4 for order 1, 2 for order 2, which keeps
+// the step ratio inside BDF2's zero-stability bound 1 + sqrt 2), capped by
+// what remains; rejected: h max(0.2, min(0.9, 0.9 err^(-1/(p+1)))); Newton
+// failure: h/4.  The interval is done when the remainder is <= 1e-12
+// dt_total; a cell fails (status 2) when h < h_min dt_total, and stops with
+// status 1 after max_rounds attempts.
 int oracle_integrate(void* h, int64_t ncells, int64_t ld, const double* dt_total, int dt_stride,
                      const double* rho, double* T, double* Y, double rtol, double atol_C,
                      double atol_T, double h0, double h_min, int max_rounds, double n_rtol,
-                     double n_atol_C, double n_atol_T, int max_iter, int* nsteps, int* status,
-                     int nthreads) {
+                     double n_atol_C, double n_atol_T, int max_iter, int order, int* nsteps,
+                     int* status, int nthreads) {
   Mech* m = (Mech*)h;
   const int N = m->N, n = N + 1;
+  if (order != 1 && order != 2) return -1;
+  const double g_max = order == 2 ? 2.0 : 4.0;
   int nbad = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_or_default(nthreads)) reduction(+ : nbad)
   for (int64_t c = 0; c < ncells; ++c) {
@@ -1147,31 +1173,52 @@ int oracle_integrate(void* h, int64_t ncells, int64_t ld, const double* dt_total
     std::vector<double> phi;
     cell_phi(*m, c, ld, rho, T, Y, phi);
     double t = 0.0, hs = std::min(h0 > 0.0 ? h0 : 0.01 * D, D);
+    std::vector<double> phi_prev(n), f_prev(n), cterm(n);
+    double h_prev = 0.0;   // 0: no previous substep (the first substep is backward Euler)
     int st = 1, ns = 0;
     for (int round = 0; round < max_rounds; ++round) {
+      const bool bdf2 = order == 2 && h_prev > 0.0;
+      const double w = bdf2 ? hs / h_prev : 0.0;
+      double gamma = hs;
+      if (bdf2) {
+        const double a1 = (1.0 + w) * (1.0 + w) / (1.0 + 2.0 * w), a2 = -w * w / (1.0 + 2.0 * w);
+        for (int i = 0; i < n; ++i) cterm[i] = a1 * phi[i] + a2 * phi_prev[i];
+        gamma = (1.0 + w) / (1.0 + 2.0 * w) * hs;
+      } else {
+        cterm = phi;
+      }
       std::vector<double> pn, f0(n), f1(n);
       int it = 0;
-      const int ok = be_newton(*m, phi, hs, n_rtol, n_atol_C, n_atol_T, max_iter, pn, f0, f1, &it);
+      const int ok = newton_solve(*m, phi, cterm, gamma, n_rtol, n_atol_C, n_atol_T, max_iter, pn, f0,
+                                  f1, &it);
       if (ok != 0) {
         hs *= 0.25;
       } else {
         double e2 = 0.0;
+        const double ce = bdf2 ? hs * (1.0 + w) / (3.0 * (1.0 + 2.0 * w)) : 0.5 * hs;
         for (int i = 0; i < n; ++i) {
-          const double e = 0.5 * hs * (f1[i] - f0[i]);
-          const double w = rtol * std::fabs(pn[i]) + (i < N ? atol_C : atol_T);
-          e2 += (e / w) * (e / w);
+          const double e = bdf2 ? ce * ((f1[i] - f0[i]) - w * (f0[i] - f_prev[i])) : ce * (f1[i] - f0[i]);
+          const double wt = rtol * std::fabs(pn[i]) + (i < N ? atol_C : atol_T);
+          e2 += (e / wt) * (e / wt);
         }
         const double err = std::sqrt(e2 / n);
+        // 0.9 err^(-1/(p+1)) for the substep's order p
+        const double gr = err > 0.0 ? (bdf2 ? 0.9 / std::cbrt(err) : 0.9 / std::sqrt(err)) : 0.0;
         if (err <= 1.0) {
+          if (order == 2) {
+            phi_prev = phi;
+            f_prev = f0;
+            h_prev = hs;
+          }
           phi = pn;
           t += hs;
           ns++;
           const double rem = D - t;
           if (rem <= 1e-12 * D) { st = 0; break; }
-          const double g = err > 0.0 ? 0.9 / std::sqrt(err) : 4.0;
-          hs = std::min(hs * std::min(4.0, std::max(0.2, g)), rem);
+          const double g = err > 0.0 ? gr : g_max;
+          hs = std::min(hs * std::min(g_max, std::max(0.2, g)), rem);
         } else {
-          const double g = err > 0.0 ? 0.9 / std::sqrt(err) : 0.25;
+          const double g = err > 0.0 ? gr : 0.25;
           hs = hs * (g == g ? std::min(0.9, std::max(0.2, g)) : 0.25);
         }
       }
