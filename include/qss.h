@@ -195,16 +195,26 @@ int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double*
 /* ---------------------------------------------------------------------------
  * Integration over an interval.  Advances every cell by dt_total (device
  * array with dt_stride 1, or a scalar with dt_stride 0) at constant volume
- * with backward-Euler substeps under local error control, the kind of
- * stiff integration over a CFD substep the paper's Jacobian serves (Section
- * 3.1, which drives CVODE; this is not CVODE).  Each substep of size h is a
- * Newton-solved backward-Euler step (qss_implicit_step's solver); its local
- * error is estimated as e = h/2 (f(phi_n+1) - f(phi_n)), with f at the last
- * Newton iterate standing for f(phi_n+1).  A substep is accepted when the
- * weighted RMS of e with weights rtol |phi_i| + atol_i is <= 1; the next h is
- * h min(4, max(0.2, 0.9 / sqrt(err))) (capped by what remains of the
- * interval).  A rejected substep retries with h max(0.2, min(0.9, 0.9 /
- * sqrt(err))), a failed Newton solve with h / 4.  T and Y (device arrays) are
+ * with substeps under local error control, the kind of stiff integration
+ * over a CFD substep the paper's Jacobian serves (Section 3.1, which drives
+ * CVODE; this is not CVODE).  Each substep of size h is solved by Newton
+ * (qss_implicit_step's solver) from phi_n:
+ *   order 1: backward Euler, phi - phi_n - h f(phi) = 0, local error
+ *            e = h/2 (f(phi_n+1) - f(phi_n));
+ *   order 2: variable-step BDF2 once a substep has been accepted (the first
+ *            is backward Euler): with w = h / h_prev,
+ *            phi - a1 phi_n - a2 phi_n-1 - beta h f(phi) = 0, a1 =
+ *            (1+w)^2/(1+2w), a2 = -w^2/(1+2w), beta = (1+w)/(1+2w); local
+ *            error e = h (1+w)/(3(1+2w)) ((f(phi_n+1) - f(phi_n)) - w (f(phi_n)
+ *            - f(phi_n-1))), its truncation error with the third derivative
+ *            from divided differences of f,
+ * with f at the last Newton iterate standing for f(phi_n+1).  A substep is
+ * accepted when the weighted RMS err of e with weights rtol |phi_i| + atol_i
+ * is <= 1; the next h is h min(g_max, max(0.2, 0.9 err^(-1/(p+1)))) for a
+ * substep of order p (g_max 4 for order 1, 2 for order 2, inside BDF2's
+ * step-ratio stability bound; capped by what remains of the interval).  A
+ * rejected substep retries with h max(0.2, min(0.9, 0.9 err^(-1/(p+1)))), a
+ * failed Newton solve with h / 4.  T and Y (device arrays) are
  * updated in place; nsteps [ld] receives the accepted substeps and
  * cell_status [ld] 0 (interval done), 1 (max_rounds substep attempts
  * exhausted; T, Y hold the last accepted state) or 2 (h fell below h_min x
@@ -218,6 +228,7 @@ typedef struct {
   double h_min;                  /* smallest substep / interval (default 1e-14)     */
   int max_rounds;                /* substep attempts per cell (default 400)         */
   qss_newton_opts newton;        /* each substep's Newton solve                      */
+  int order;                     /* 1 backward Euler (default), 2 variable-step BDF2 */
 } qss_integrate_opts;
 
 int qss_integrate(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt_total,

@@ -41,13 +41,15 @@ class NewtonOpts(ctypes.Structure):
 class IntegrateOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol_C", ctypes.c_double), ("atol_T", ctypes.c_double),
                 ("h0", ctypes.c_double), ("h_min", ctypes.c_double), ("max_rounds", ctypes.c_int),
-                ("newton", NewtonOpts)]
+                ("newton", NewtonOpts), ("order", ctypes.c_int)]
 
 
 def integrate_opts(rtol=1e-4, atol_C=1e-10, atol_T=1e-4, h0=0.0, h_min=1e-14, max_rounds=400,
-                   newton: Optional["NewtonOpts"] = None) -> IntegrateOpts:
+                   newton: Optional["NewtonOpts"] = None, order=1) -> IntegrateOpts:
+    """order 1: backward-Euler substeps; 2: variable-step BDF2 substeps."""
     return IntegrateOpts(rtol, atol_C, atol_T, h0, h_min, max_rounds,
-                         newton if newton is not None else NewtonOpts(20, 1e-12, 1e-20, 1e-10, 10, 1e-8))
+                         newton if newton is not None else NewtonOpts(20, 1e-12, 1e-20, 1e-10, 10, 1e-8),
+                         order)
 
 
 class ServeOpts(ctypes.Structure):

@@ -89,15 +89,15 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
                     CUdeviceptr scratch, size_t scratch_bytes, const int* ncap, double* fn0,
-                    double* fn1) {
+                    double* fn1, const double* p0, int64_t p0ld) {
   if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
   const size_t per_cell = newton_scratch_per_cell(m, precision);
   const int64_t cap = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell);
   if (cap < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
   int64_t chunk = std::min<int64_t>(cap / 32 * 32, (ncells + 31) / 32 * 32);
-  if (chunk < ncells && !(ncap || fn0 || fn1)) chunk = chunk_cells(m, cap);   // whole waves per chunk
-  if ((ncap || fn0 || fn1) && chunk < ncells)
+  if (chunk < ncells && !(ncap || fn0 || fn1 || p0)) chunk = chunk_cells(m, cap);   // whole waves per chunk
+  if ((ncap || fn0 || fn1 || p0) && chunk < ncells)
     return fail(QSS_ERR_BUDGET, "a capped or recording launch must fit one chunk");
   NewtonOptsDev od = {o.max_iter, o.rtol, o.atol_C, o.atol_T, o.max_refine, o.refine_tol};
   const size_t S = (size_t)chunk;
@@ -114,13 +114,13 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   // + 2 ints is 8-byte aligned (S % 32 == 0), and the region ends within
   // per_cell * S + 256 bytes of the scratch start
   double* FR = frontier_bytes_per_cell(m) ? (double*)(NACT + 2) : nullptr;
-  long long sld = chunk, l = ld;
+  long long sld = chunk, l = ld, pl = p0ld;
   int rc;
   const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
   for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
     long long cells = std::min<int64_t>(chunk, ncells - c0), cc0 = c0;
     void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld,
-                       &ncap};
+                       &ncap, &p0, &pl};
     if ((rc = launch_cells(m, m->f_newton_setup, cells, m->block, a_setup, st, 0))) return rc;
     for (int it = 0; it < o.max_iter; ++it) {
       const int cur = it & 1, nxt = cur ^ 1;

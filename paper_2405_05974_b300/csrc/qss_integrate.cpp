@@ -1,9 +1,9 @@
-// Integration over an interval by backward-Euler substeps with local error
-// control: host side of qss_integrate.
+// Integration over an interval by backward-Euler or variable-step BDF2
+// substeps with local error control: host side of qss_integrate.
 //
 // Per chunk of cells: an init kernel, then rounds of (gather the active cells
-// into a contiguous batch; one Newton-solved backward-Euler substep of the
-// batch with each cell's own step h, recording f at the step's start and at
+// into a contiguous batch, with the constant term of a BDF2 substep; one
+// Newton-solved substep of the batch with each cell's own step h, recording f at the step's start and at
 // the last Newton iterate; accept or reject each substep and build the next
 // active list), then a kernel that writes the step counts and statuses.  The
 // active counts stay on the device (the Newton kernels read them), so the
@@ -27,13 +27,15 @@ constexpr int kCheckEvery = 8;                     // rounds between host checks
 struct IntegOptsDev {   // layout of QssIntegOpts in qss_newton.cuh
   double rtol, atol_C, atol_T;
   double h_min;
+  int order;
 };
 
-// per-cell bytes: persistent (TT, HH, DT; IS, NS, LA, LB), batch (rho, T, dt,
-// Y[N]; status; FN0, FN1 [n] each) and the Newton scratch of the batch
+// per-cell bytes: persistent (TT, HH, DT, HP; PP, FP [n] each; IS, NS, LA,
+// LB), batch (rho, T, dt, Y[N]; status; FN0, FN1, PC [n] each) and the Newton
+// scratch of the batch
 size_t integ_per_cell(const qss_mech_s* m, int prec) {
   const int N = m->N, n = N + 1;
-  return (size_t)(3 + 3 + N + 2 * n) * sizeof(double) + 5 * sizeof(int) +
+  return (size_t)(4 + 2 * n + 3 + N + 3 * n) * sizeof(double) + 5 * sizeof(int) +
          newton_scratch_per_cell(m, prec);
 }
 
@@ -43,14 +45,15 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
                              int dt_stride, const double* rho, double* T, double* Y, int precision,
                              const qss_integrate_opts* opts, int32_t* nsteps, int32_t* cell_status,
                              void* stream) {
-  qss_integrate_opts io = {1e-4, 1e-10, 1e-4, 0.0, 1e-14, 400, {20, 1e-12, 1e-20, 1e-10, 10, 1e-8}};
+  qss_integrate_opts io = {1e-4, 1e-10, 1e-4, 0.0, 1e-14, 400, {20, 1e-12, 1e-20, 1e-10, 10, 1e-8}, 1};
   if (opts) io = *opts;
   qss_newton_opts o;
   int rc = check_implicit_args(m, ncells, ld, dt_total, dt_stride, rho, T, Y, precision, &io.newton, &o);
   if (rc || ncells == 0) return rc;
   if (!(io.rtol >= 0) || !(io.atol_C > 0) || !(io.atol_T > 0) || !(io.h0 >= 0) ||
-      !(io.h_min > 0 && io.h_min < 1e-12) || io.max_rounds < 1)
-    return fail(QSS_ERR_INVALID_ARG, "bad integration options (atol > 0, 0 < h_min < 1e-12 required)");
+      !(io.h_min > 0 && io.h_min < 1e-12) || io.max_rounds < 1 || (io.order != 1 && io.order != 2))
+    return fail(QSS_ERR_INVALID_ARG,
+                "bad integration options (atol > 0, 0 < h_min < 1e-12, order 1 or 2 required)");
   for (int k = 0; k < 4; ++k)
     if (!m->f_integ[k]) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no integration kernels");
   std::lock_guard<std::mutex> lock(m->mu);
@@ -68,6 +71,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   const size_t oLA = take(I), oLB = take(I), oCNT = take(256);
   const size_t oRb = take(D), oTb = take(D), oDtb = take(D), oYb = take((size_t)N * D);
   const size_t oBst = take(I), oF0 = take((size_t)n * D), oF1 = take((size_t)n * D);
+  const size_t oHP = take(D), oPP = take((size_t)n * D), oFP = take((size_t)n * D), oPC = take((size_t)n * D);
   const size_t oNewton = take(0);
   const size_t newton_bytes = newton_scratch_per_cell(m, precision) * (size_t)S + 256;
   const size_t total = off + newton_bytes;
@@ -87,15 +91,21 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   int* bst = (int*)(base + oBst);
   double* F0 = (double*)(base + oF0);
   double* F1 = (double*)(base + oF1);
+  double* HP = (double*)(base + oHP);   // order 2: previous substep, phi_n-1, f_n-1, constant term
+  double* PP = (double*)(base + oPP);
+  double* FP = (double*)(base + oFP);
+  double* PC = (double*)(base + oPC);
+  const double* P0 = io.order == 2 ? PC : nullptr;
   CUdeviceptr newton = m->newton_scratch + oNewton;
-  IntegOptsDev od = {io.rtol, io.atol_C, io.atol_T, io.h_min};
-  long long bld = S, l = ld;
+  IntegOptsDev od = {io.rtol, io.atol_C, io.atol_T, io.h_min, io.order};
+  long long bld = S, l = ld, SS = S;
+  int order = io.order;
   for (int64_t c0 = 0; c0 < ncells; c0 += S) {
     long long cells = std::min<int64_t>(S, ncells - c0), cc0 = c0;
     double h0 = io.h0;
     int* CA = CNT;
     int* ncap = CNT + 2;
-    void* a_init[] = {&cells, &cc0, &dt_total, &dt_stride, &h0, &TT, &HH, &DTv, &IS, &NS, &L[0], &CA};
+    void* a_init[] = {&cells, &cc0, &dt_total, &dt_stride, &h0, &TT, &HH, &DTv, &IS, &NS, &L[0], &CA, &HP};
     if ((rc = launch_cells(m, m->f_integ[0], cells, m->block, a_init, st, 0))) break;
     for (int round = 0; round < io.max_rounds; ++round) {
       const int a = round & 1, b = a ^ 1;
@@ -103,13 +113,14 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
       int* LB = L[b];
       int* ca = CNT + a;
       int* cb = CNT + b;
-      void* a_g[] = {&cc0, &l, &rho, &T, &Y, &LA, &ca, &cb, &HH, &rhob, &Tb, &Yb, &dtb, &ncap, &bld};
+      void* a_g[] = {&cc0, &l, &rho, &T, &Y, &LA, &ca, &cb, &HH, &rhob, &Tb, &Yb, &dtb, &ncap, &bld,
+                     &HP, &PP, &PC, &SS, &order};
       if ((rc = launch_cells(m, m->f_integ[1], cells, m->block, a_g, st, 0))) break;
       if ((rc = implicit_launch(m, cells, bld, dtb, 1, rhob, Tb, Yb, precision, o, nullptr, bst, st,
-                                newton, newton_bytes, ncap, F0, F1)))
+                                newton, newton_bytes, ncap, F0, F1, P0, bld)))
         break;
       void* a_a[] = {&cc0, &l, &T, &Y, &LA, &ca, &LB, &cb, &HH, &TT, &DTv, &IS, &NS,
-                     &rhob, &Tb, &Yb, &bst, &F0, &F1, &bld, &od};
+                     &rhob, &Tb, &Yb, &bst, &F0, &F1, &bld, &od, &HP, &PP, &FP, &SS};
       if ((rc = launch_cells(m, m->f_integ[2], cells, m->block, a_a, st, 0))) break;
       if ((round + 1) % kCheckEvery == 0) {
         int left = 0;

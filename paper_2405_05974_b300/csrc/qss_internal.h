@@ -86,7 +86,8 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
                     const double* rho, double* T, double* Y, int precision,
                     const qss_newton_opts& o, int32_t* iters, int32_t* cell_status, CUstream st,
                     CUdeviceptr scratch, size_t scratch_bytes, const int* ncap = nullptr,
-                    double* fn0 = nullptr, double* fn1 = nullptr);
+                    double* fn0 = nullptr, double* fn1 = nullptr, const double* p0 = nullptr,
+                    int64_t p0ld = 0);
 }  // namespace qss
 
 #define CU_TRY(call)                                   \

@@ -97,9 +97,12 @@ qss_newton_setup_kernel(long long cells, long long c0, long long ld, const doubl
                         const double* __restrict__ T, const double* __restrict__ Y,
                         double* __restrict__ PHI, double* __restrict__ PHI0, int* __restrict__ ACT,
                         int* __restrict__ ST, int* __restrict__ IT, int* __restrict__ LIST,
-                        int* __restrict__ NACT, long long sld, const int* __restrict__ ncap) {
+                        int* __restrict__ NACT, long long sld, const int* __restrict__ ncap,
+                        const double* __restrict__ P0, long long p0ld) {
   // ncap (optional): a device-side cell count that lowers `cells`, so that a
-  // launch sequence captured for a size bucket serves any smaller batch
+  // launch sequence captured for a size bucket serves any smaller batch.
+  // P0 (optional): the constant term of G, P0[k * p0ld + c] (a multistep
+  // formula's combination of past states); otherwise it is the state.
   if (ncap) cells = min(cells, (long long)*ncap);
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (s == 0) { NACT[0] = (int)cells; NACT[1] = 0; }
@@ -110,10 +113,10 @@ qss_newton_setup_kernel(long long cells, long long c0, long long ld, const doubl
   for (int k = 0; k < QSS_N; ++k) {
     const double v = r * Y[k * ld + c] * qss_inv_W[k];
     PHI[k * sld + s] = v;
-    PHI0[k * sld + s] = v;
+    PHI0[k * sld + s] = P0 ? P0[k * p0ld + c] : v;
   }
   PHI[QSS_N * sld + s] = T[c];
-  PHI0[QSS_N * sld + s] = T[c];
+  PHI0[QSS_N * sld + s] = P0 ? P0[QSS_N * p0ld + c] : T[c];
   ACT[s] = 1;
   ST[s] = QSS_CELL_MAXITER;
   IT[s] = 0;
@@ -582,24 +585,36 @@ qss_newton_finish_kernel(long long cells, long long c0, long long ld, const doub
 }
 
 // ---------------------------------------------------------------------------
-// Integration over an interval by backward-Euler substeps with local error
-// control (qss_integrate).  Per cell s of a chunk (persistent across rounds):
+// Integration over an interval by substeps with local error control
+// (qss_integrate), backward Euler (order 1) or variable-step BDF2 (order 2,
+// after a first backward-Euler substep).  Per cell s of a chunk (persistent
+// across rounds):
 //   TT[s] time done, HH[s] next substep, DT[s] target interval,
-//   IS[s] 0 done / 1 active / 2 substep below h_min, NS[s] accepted substeps.
+//   IS[s] 0 done / 1 active / 2 substep below h_min, NS[s] accepted substeps,
+//   order 2: HP[s] previous accepted substep (0: none yet), PP[k S + s] and
+//   FP[k S + s] the state and f at its start (phi_n-1, f_n-1).
 // A round: gather the active cells (list A, count *CA) into a contiguous
-// batch (rho, T, Y, h), one Newton-solved backward-Euler step of the batch
-// (f recorded at phi_n and at the last iterate), then accept or reject each
-// cell's substep and build the next active list (B).
+// batch (rho, T, Y, Newton step gamma, constant term PC of G), one
+// Newton-solved substep of the batch (f recorded at phi_n and at the last
+// iterate), then accept or reject each cell's substep and build the next
+// active list (B).  With w = h / h_prev, BDF2 solves
+//   phi - a1 phi_n - a2 phi_n-1 - beta h f(phi) = 0,
+//   a1 = (1+w)^2/(1+2w), a2 = -w^2/(1+2w), beta = (1+w)/(1+2w),
+// and estimates its local error as h (1+w)/(3(1+2w)) ((f_n+1 - f_n) -
+// w (f_n - f_n-1)) (its truncation error with the third derivative from the
+// second divided difference of f); backward Euler's estimate is
+// h/2 (f_n+1 - f_n).
 struct QssIntegOpts {
   double rtol, atol_C, atol_T;
   double h_min;   // fraction of the interval
+  int order;      // 1 or 2
 };
 
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_integ_init_kernel(long long cells, long long c0, const double* __restrict__ dt_total,
                       int dt_stride, double h0, double* __restrict__ TT, double* __restrict__ HH,
                       double* __restrict__ DT, int* __restrict__ IS, int* __restrict__ NS,
-                      int* __restrict__ LA, int* __restrict__ CA) {
+                      int* __restrict__ LA, int* __restrict__ CA, double* __restrict__ HP) {
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (s == 0) *CA = (int)cells;
   if (s >= cells) return;
@@ -607,6 +622,7 @@ qss_integ_init_kernel(long long cells, long long c0, const double* __restrict__ 
   DT[s] = D;
   TT[s] = 0.0;
   HH[s] = fmin(h0 > 0.0 ? h0 : 0.01 * D, D);
+  HP[s] = 0.0;
   IS[s] = 1;
   NS[s] = 0;
   LA[s] = (int)s;
@@ -618,18 +634,37 @@ qss_integ_gather_kernel(long long c0, long long ld, const double* __restrict__ r
                         const int* __restrict__ LA, const int* __restrict__ CA, int* __restrict__ CB,
                         const double* __restrict__ HH, double* __restrict__ rhob,
                         double* __restrict__ Tb, double* __restrict__ Yb, double* __restrict__ dtb,
-                        int* __restrict__ ncap, long long bld) {
+                        int* __restrict__ ncap, long long bld, const double* __restrict__ HP,
+                        const double* __restrict__ PP, double* __restrict__ PC, long long S, int order) {
   const long long i = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   const int n = *CA;
   if (i == 0) { *CB = 0; *ncap = n; }
   if (i >= n) return;
   const int s = LA[i];
   const long long c = c0 + s;
-  rhob[i] = rho[c];
+  const double r = rho[c];
+  rhob[i] = r;
   Tb[i] = T[c];
 #pragma unroll
   for (int k = 0; k < QSS_N; ++k) Yb[k * bld + i] = Y[k * ld + c];
-  dtb[i] = HH[s];
+  const double h = HH[s];
+  dtb[i] = h;
+  if (order == 2) {
+    // the constant term of G: phi_n (backward Euler) or the BDF2 combination
+    const double hp = HP[s];
+    double a1 = 1.0, a2 = 0.0;
+    if (hp > 0.0) {
+      const double w = h / hp;
+      a1 = (1.0 + w) * (1.0 + w) / (1.0 + 2.0 * w);
+      a2 = -w * w / (1.0 + 2.0 * w);
+      dtb[i] = (1.0 + w) / (1.0 + 2.0 * w) * h;
+    }
+#pragma unroll
+    for (int k = 0; k < QSS_NN; ++k) {
+      const double phi = k < QSS_N ? r * Y[k * ld + c] * qss_inv_W[k] : T[c];
+      PC[k * bld + i] = hp > 0.0 ? a1 * phi + a2 * PP[k * S + s] : phi;
+    }
+  }
 }
 
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
@@ -640,30 +675,46 @@ qss_integ_accept_kernel(long long c0, long long ld, double* __restrict__ T, doub
                         const double* __restrict__ rhob, const double* __restrict__ Tb,
                         const double* __restrict__ Yb, const int* __restrict__ bst,
                         const double* __restrict__ FN0, const double* __restrict__ FN1, long long bld,
-                        QssIntegOpts o) {
+                        QssIntegOpts o, double* __restrict__ HP, double* __restrict__ PP,
+                        double* __restrict__ FP, long long S) {
   const long long i = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (i >= *CA) return;
   const int s = LA[i];
   const long long c = c0 + s;
   const double h = HH[s];
+  const double g_max = o.order == 2 ? 2.0 : 4.0;
   bool keep = true;
   if (bst[i] != QSS_CELL_CONVERGED) {
     // the Newton solve failed: a quarter of the substep
     HH[s] = 0.25 * h;
   } else {
-    // local error of the substep: h/2 (f(phi_n+1) - f(phi_n)), weighted RMS
+    const bool bdf2 = o.order == 2 && HP[s] > 0.0;
+    const double w = bdf2 ? h / HP[s] : 0.0;
+    const double ce = bdf2 ? h * (1.0 + w) / (3.0 * (1.0 + 2.0 * w)) : 0.5 * h;
+    // local error estimate, weighted RMS
     const double r = rhob[i];
     double e2 = 0.0;
 #pragma unroll
     for (int k = 0; k < QSS_NN; ++k) {
       const double phi = k < QSS_N ? r * Yb[k * bld + i] * qss_inv_W[k] : Tb[i];
-      const double e = 0.5 * h * (FN1[k * bld + i] - FN0[k * bld + i]);
-      const double w = o.rtol * fabs(phi) + (k < QSS_N ? o.atol_C : o.atol_T);
-      const double q = e / w;
+      const double f0 = FN0[k * bld + i], f1 = FN1[k * bld + i];
+      const double e = bdf2 ? ce * ((f1 - f0) - w * (f0 - FP[k * S + s])) : ce * (f1 - f0);
+      const double wt = o.rtol * fabs(phi) + (k < QSS_N ? o.atol_C : o.atol_T);
+      const double q = e / wt;
       e2 = fma(q, q, e2);
     }
     const double err = sqrt(e2 / QSS_NN);
+    // 0.9 err^(-1/(p+1)) for the substep's order p
+    const double gr = err > 0.0 ? (bdf2 ? 0.9 / cbrt(err) : 0.9 / sqrt(err)) : 0.0;
     if (err <= 1.0) {
+      if (o.order == 2) {   // history for the next substep: phi_n, f_n, h
+#pragma unroll
+        for (int k = 0; k < QSS_NN; ++k) {
+          PP[k * S + s] = k < QSS_N ? r * Y[k * ld + c] * qss_inv_W[k] : T[c];
+          FP[k * S + s] = FN0[k * bld + i];
+        }
+        HP[s] = h;
+      }
       T[c] = Tb[i];
 #pragma unroll
       for (int k = 0; k < QSS_N; ++k) Y[k * ld + c] = Yb[k * bld + i];
@@ -674,12 +725,12 @@ qss_integ_accept_kernel(long long c0, long long ld, double* __restrict__ T, doub
         IS[s] = 0;
         keep = false;
       } else {
-        const double g = err > 0.0 ? 0.9 / sqrt(err) : 4.0;
-        HH[s] = fmin(h * fmin(4.0, fmax(0.2, g)), rem);
+        const double g = err > 0.0 ? gr : g_max;
+        HH[s] = fmin(h * fmin(g_max, fmax(0.2, g)), rem);
       }
     } else {
-      // rejected (also for a NaN error): shrink by the error's square root
-      const double g = err > 0.0 ? 0.9 / sqrt(err) : 0.25;
+      // rejected (also for a NaN error)
+      const double g = err > 0.0 ? gr : 0.25;
       HH[s] = h * (g == g ? fmin(0.9, fmax(0.2, g)) : 0.25);
     }
   }

@@ -1,5 +1,5 @@
-"""qss_integrate (backward-Euler substeps with local error control) on the
-GPU against the oracle's integrator.
+"""qss_integrate (backward-Euler or variable-step BDF2 substeps with local
+error control) on the GPU against the oracle's integrator.
 
 Both run the same controller; a substep decision (accept/reject, err <= 1)
 can flip where err is within rounding of 1, after which the two substep
@@ -24,17 +24,18 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("key,ncells,D", [("tiny", 512, 1e-7), ("hydrocarbon", 64, 1e-8)])
 @pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
-def test_integrate_matches_oracle(key, ncells, D, prec):
+def test_integrate_matches_oracle(key, ncells, D, prec, order):
     m = workloads.mechanism(key)
     om = oracle.OracleMech(m)
     gm = binding.Mechanism(build_mechanism(m), 0)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
     t, y = dev(T), dev(Y)
-    ns, st = gm.integrate(dev(rho), t, y, D, precision=prec, opts=binding.integrate_opts(**OPTS))
+    ns, st = gm.integrate(dev(rho), t, y, D, precision=prec, opts=binding.integrate_opts(**OPTS, order=order))
     ns, st = ns.cpu().numpy(), st.cpu().numpy()
-    To, Yo, nso, sto = om.integrate(rho, T, Y, D, **OPTS)
+    To, Yo, nso, sto = om.integrate(rho, T, Y, D, order=order, **OPTS)
     same = (st == sto) & (ns == nso)
     assert same.mean() >= 0.9, (np.bincount(st, minlength=3), np.bincount(sto, minlength=3))
     done = same & (st == 0)
@@ -52,7 +53,8 @@ def test_integrate_rejects_bad_options():
     m = workloads.mechanism("tiny")
     gm = binding.Mechanism(build_mechanism(m), 0)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES["tiny"], 64)
-    for bad in (dict(atol_C=0.0), dict(h_min=0.0), dict(max_rounds=0), dict(rtol=-1.0)):
+    for bad in (dict(atol_C=0.0), dict(h_min=0.0), dict(max_rounds=0), dict(rtol=-1.0), dict(order=3),
+                dict(order=0)):
         with pytest.raises(binding.QSSError):
             gm.integrate(dev(rho), dev(T), dev(Y), 1e-7, opts=binding.integrate_opts(**bad))
 
@@ -71,3 +73,21 @@ def test_integrate_reaches_where_one_step_fails():
     st1, st2 = st1.cpu().numpy(), st2.cpu().numpy()
     rescued = (st1 != 0) & (st2 == 0)
     assert rescued.sum() > 0, (np.bincount(st1), np.bincount(st2, minlength=3))
+
+
+def test_bdf2_needs_fewer_substeps():
+    """At the same tolerance the second-order substeps cover the interval in
+    far fewer substeps (the oracle's pins fix the order of accuracy)."""
+    key, ncells, D = "tiny", 512, 1e-7
+    m = workloads.mechanism(key)
+    gm = binding.Mechanism(build_mechanism(m), 0)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    res = {}
+    for order in (1, 2):
+        ns, st = gm.integrate(dev(rho), dev(T), dev(Y), D, opts=binding.integrate_opts(
+            rtol=1e-5, atol_C=1e-8, atol_T=1e-5, order=order, max_rounds=4000))
+        res[order] = (ns.cpu().numpy(), st.cpu().numpy())
+    both = (res[1][1] == 0) & (res[2][1] == 0)
+    assert both.mean() > 0.5
+    assert np.median(res[2][0][both]) * 2 < np.median(res[1][0][both]), (
+        np.median(res[1][0][both]), np.median(res[2][0][both]))
