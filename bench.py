@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-implicit", action="store_true")
+    p.add_argument("--integrate", action="store_true",
+                   help="also time qss_integrate (backward Euler vs BDF2 substeps; about 30 s)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--implicit-ncells", type=int, default=0)
@@ -256,6 +258,43 @@ def implicit_bench(gm, mech, ncells, dt, oracle_sample=0):
                              "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell"}
     res["speedup_fp32ir_over_fp64"] = res["fp32ir"]["cells_per_s"] / res["fp64"]["cells_per_s"]
     res["workload"] = f"{mech['name']} backward Euler, dt = {dt:g} s, {ncells} cells"
+    return res
+
+
+def integrate_bench(gm, mech, ncells=16384, D=1e-9, rtol=1e-3, max_rounds=400):
+    """Integration of the implicit workload's first cells over an interval D
+    (qss_integrate, FP32 LU + FP64 refinement), backward-Euler and BDF2
+    substeps at the same tolerance: cells/s over the interval, substeps per
+    cell, outcome counts.  One untimed run on a small batch first.  The wall
+    time is set by the slowest cells: every round is a sequence of Newton
+    launches, and one cell's Jacobian evaluation alone takes about a
+    millisecond (one thread computes it), so max_rounds bounds the run."""
+    import torch
+    from paper_2405_05974_b300 import binding, mechgen, workloads
+    rho, T, Y = mechgen.generate_states(mech, workloads.STATES["implicit"], ncells)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    r = d(rho)
+    res = {"workload": f"{mech['name']}: {ncells} cells over {D:g} s, rtol {rtol:g}, atol_C 1e-6, "
+                       f"atol_T 1e-3, at most {max_rounds} substep attempts, FP32 LU + FP64 refinement"}
+    for order in (1, 2):
+        opts = binding.integrate_opts(rtol=rtol, atol_C=1e-6, atol_T=1e-3, order=order, max_rounds=max_rounds)
+        gm.integrate(d(rho[:256]), d(T[:256]), d(Y[:, :256]), D, precision=binding.QSS_LU_FP32_IR, opts=opts)
+        t, y = d(T), d(Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ns, st = gm.integrate(r, t, y, D, precision=binding.QSS_LU_FP32_IR, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ns, st = ns.cpu().numpy(), st.cpu().numpy()
+        done = st == 0
+        res[f"order{order}"] = {
+            "cells_per_s": ncells / (ms * 1e-3), "ms": ms,
+            "status_counts": {"done": int(done.sum()), "rounds_exhausted": int((st == 1).sum()),
+                              "below_h_min": int((st == 2).sum())},
+            "substeps_median": float(np.median(ns[done])) if done.any() else None,
+            "substeps_mean": float(ns[done].mean()) if done.any() else None}
     return res
 
 
@@ -523,6 +562,9 @@ def main():
     if not a.no_implicit and key == "hydrocarbon":
         implicit = implicit_bench(gm, mech, a.implicit_ncells or workloads.NCELLS["implicit"],
                                   workloads.IMPLICIT_DT)
+    integration = None
+    if a.integrate and key == "hydrocarbon" and rank == 0:
+        integration = integrate_bench(gm, mech)
     serving = None
     if not a.no_serve and key == "hydrocarbon" and rank == 0:
         from paper_2405_05974_b300 import binding as _b
@@ -550,7 +592,8 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
             "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps * launches_per_step, "clocks": clk.summary(),
-            "implicit": implicit, "serving": serving, "jacobian_variants": variants,
+            "implicit": implicit, "integration": integration, "serving": serving,
+            "jacobian_variants": variants,
             "kernel": {"ptxas": {k: v for k, v in meta["kernels"].items() if k.startswith("qss_jac")},
                        "defines": meta.get("defines", []),
                        "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}

@@ -73,14 +73,14 @@ def test_csr_host_path():
     assert torch.equal(Jh, Jd.cpu())
 
 
-@pytest.mark.parametrize("key,ncells", [("tiny", 2048), ("hydrocarbon", 1024)])
-def test_csr_implicit_step_equals_dense(key, ncells):
+@pytest.mark.parametrize("key,parts,ncells", [("tiny", 0, 2048), ("tiny", 2, 2048), ("hydrocarbon", 0, 1024)])
+def test_csr_implicit_step_equals_dense(key, parts, ncells):
     m = workloads.mechanism(key)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
     for prec in (binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR):
         out = []
         for fmt in ("dense", "csr"):
-            gm = gpu_mech(key, fmt)
+            gm = gpu_mech(key, fmt, parts)
             r, t, y = dev(rho), dev(T), dev(Y)
             it, st = gm.implicit_step(r, t, y, workloads.IMPLICIT_DT, precision=prec)
             torch.cuda.synchronize()
