@@ -20,6 +20,11 @@ Parity status of each function (see the test files named beside them):
   jac_fd / jac_fd_errbound ........ pinned: first- and second-order
                                      convergence to the complex-step Jacobian
   qss_groups / tarjan ............. pinned: the paper's Fig. 2 example graph
+  integrate (backward Euler, BDF2)  pinned: A <=> B relaxation (global error
+                                     ~ tol^(1/2) and tol^(2/3)), two BDF2
+                                     substeps against the closed-form linear
+                                     solves, one substep = one BE step, mass
+                                     (tests/test_integrate_oracle.py)
 """
 from __future__ import annotations
 
