@@ -2,7 +2,10 @@
 //
 // Newton on G(phi) = phi - phi0 - dt f(phi), phi = (C, T), f = (wdot, Tdot) at
 // constant volume, with the matrix M = I - dt J where J is the analytic
-// Jacobian, re-evaluated every iteration.  One Newton iteration is two
+// Jacobian, re-evaluated every iteration.  phi0 is the initial state, or a
+// constant term supplied by the caller (a BDF2 substep of qss_integrate:
+// phi0 = a1 phi_n + a2 phi_n-1, dt = beta h); the iteration starts from the
+// state either way.  One Newton iteration is two
 // launches over the cells that are still iterating (a compacted list):
 //   qss_jac_kernel (list mode)   f and J at the current iterate, one thread
 //                                per cell (the generated body is compiled in
@@ -37,7 +40,7 @@
 //                                        sectors shared by consecutive warps)
 //   F [k * sld + t]                       f at the current iterate (written by
 //                                        the Jacobian kernel in list mode)
-//   PHI, PHI0 [k * sld + s]               iterate, initial state
+//   PHI, PHI0 [k * sld + s]               iterate, constant term of G
 //   ACT, ST, IT [s]                       active flag, status, iterations
 //   LIST[2][sld], NACT[2]                 active lists (double-buffered)
 #pragma once
