@@ -256,7 +256,16 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
     }
   }
   __syncwarp();
-  // scaled rows in FP32
+  // scaled matrix in FP32: the NN x NN entries split evenly over the lanes
+  // (the FP64 multiply and the conversion run on the FP64 pipe; lane = row
+  // would leave most lanes of the second row slot idle), staged through LU,
+  // which the factorisation overwrites once every lane holds its rows
+#pragma unroll 4
+  for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
+    const int r = e / QSS_NN, j = e - r * QSS_NN;
+    LU[r * QSS_MSTRIDE + j] = (float)(Ms[r * QSS_MSTRIDE + j] * qss_pow2(-(se[r] + se[QSS_NN + j])));
+  }
+  __syncwarp();
   float A[QSS_NSLOT][QSS_NN];
   int ord[QSS_NSLOT];
 #pragma unroll
@@ -264,9 +273,9 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
     const int r = lane + 32 * sl;
     ord[sl] = -1;
 #pragma unroll
-    for (int j = 0; j < QSS_NN; ++j)
-      A[sl][j] = live[sl] ? (float)(Ms[r * QSS_MSTRIDE + j] * qss_pow2(-(er[sl] + se[QSS_NN + j]))) : 0.0f;
+    for (int j = 0; j < QSS_NN; ++j) A[sl][j] = live[sl] ? LU[r * QSS_MSTRIDE + j] : 0.0f;
   }
+  __syncwarp();
   // factorisation, one pivot step per iteration
 #pragma unroll 1
   for (int k = 0; k < QSS_NN; ++k) {
