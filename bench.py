@@ -299,12 +299,12 @@ def integrate_bench(gm, mech, ncells=16384, D=1e-9, rtol=1e-3, max_rounds=400):
 
 
 # ---------------------------------------------------------------------------
-# Section 3.3 figures: simplified Jacobians, FD Jacobian
+# Section 3.2 figures: simplified Jacobians, FD Jacobian
 # ---------------------------------------------------------------------------
 def variants_bench(key, gm, r, t, y, ncells_fd=1 << 18):
     """The relative Frobenius error (Eq. frobErr) of the exact, constant-QSS
     and zero-QSS Jacobians against the central FD Jacobian (step 1e-4) over
-    100 states of the Section 3.3.1 protocol, the nonzero fraction of their
+    100 states of the Section 3.2.1 protocol, the nonzero fraction of their
     species blocks (Table memQSS), and the throughput of the FD Jacobian
     kernel against the analytic one on the bench workload's first cells."""
     import torch

@@ -14,7 +14,7 @@
  *   state vector and Jacobian .............. Section 3.1, Eq. (JacExptr)
  *   chain rule through C_QSS ............... Section 3.2, Eq. (JQSS)
  *   symbolic construction with CSE ......... Section 3.2.2
- *   simplified Jacobians, FD Jacobian ...... Section 3.3.1, Eq. (frobErr); FD T column 3.3.2
+ *   simplified Jacobians, FD Jacobian ...... Section 3.2.1, Eq. (frobErr); FD T column 3.2.2
  *   implicit steps and integration ......... Section 3.1 (the stiff 0D use the Jacobian serves)
  * The mechanism compiler (paper_2405_05974_b300.qssc) produces the artefacts
  * this library loads; linearization of quadratic QSS couplings (Section 2.2,
@@ -127,11 +127,11 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
                  void* stream);
 
 /* Which Jacobian qss_jacobian computes is fixed when the artefact is built:
- * the exact one above (default), or the simplified ones of Section 3.3.1
+ * the exact one above (default), or the simplified ones of Section 3.2.1
  * (constant-QSS: the second term of Eq. JQSS dropped; zero-QSS: that term
  * dropped and the QSS concentrations set to zero inside the Jacobian), each
  * with the temperature column analytic or by the central difference of
- * Section 3.3.2 (step h = 2^(e-20) for T in [2^e, 2^(e+1))).  The row of T
+ * Section 3.2.2 (step h = 2^(e-20) for T in [2^e, 2^(e+1))).  The row of T
  * follows from the species rows by the chain rule in every variant. */
 
 /* A mechanism built with a partitioned Jacobian (a prefix kernel and column-

@@ -272,8 +272,8 @@ class OracleMech:
     JAC_VARIANTS = {"exact": 0, "const_qss": 1, "zero_qss": 2}
 
     def eval_variant(self, rho, T, Y, jac_variant="exact", t_column="analytic", nthreads=0):
-        """The Jacobian of a simplified construction (Section 3.3.1) and/or
-        with the finite-difference T column (Section 3.3.2), with running
+        """The Jacobian of a simplified construction (Section 3.2.1) and/or
+        with the finite-difference T column (Section 3.2.2), with running
         error bounds: {"wdot", "Tdot", "jac", "jac_err"} (bounds absolute)."""
         rho, T, Y, ld = self._state(rho, T, Y)
         w = np.zeros((self.N, ld)); td = np.zeros(ld)

@@ -380,11 +380,11 @@ S side_product_deriv(const Side& s, int N, const std::vector<S>& C, int k) {
   return found ? p : S(0.0);
 }
 
-// Jacobian variants (Section 3.3.1): JV_EXACT is Eq. (JQSS) in full;
+// Jacobian variants (Section 3.2.1): JV_EXACT is Eq. (JQSS) in full;
 // JV_CONST_QSS drops its second term (C_Q held at the solved values);
 // JV_ZERO_QSS drops it and sets C_Q = 0 inside the Jacobian.  t_fd replaces
 // the temperature column of the species rows by the central difference of
-// Section 3.3.2 with h = 2^(e-20), T in [2^e, 2^(e+1)).  The temperature row
+// Section 3.2.2 with h = 2^(e-20), T in [2^e, 2^(e+1)).  The temperature row
 // is always the derivative of Tdot through the species rows in use.
 enum { JV_EXACT = 0, JV_CONST_QSS = 1, JV_ZERO_QSS = 2 };
 

@@ -1,4 +1,4 @@
-"""Jacobian quality and structure figures of Section 3.3, on device tensors.
+"""Jacobian quality and structure figures of Section 3.2, on device tensors.
 
 These are reporting helpers (reductions over cells of Jacobians produced by
 the kernels), not part of the evaluation path.  Jacobians use the library's

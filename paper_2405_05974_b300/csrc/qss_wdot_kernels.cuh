@@ -17,7 +17,7 @@ qss_wdot_kernel(long long ncells, long long ld, const double* __restrict__ rho,
 }
 
 // Central finite-difference Jacobian of f = (wdot, Tdot) in phi = (C, T)
-// (Section 3.3: the FD Jacobian the analytic one is measured against, Eq.
+// (Section 3.2: the FD Jacobian the analytic one is measured against, Eq.
 // frobErr): column j = (f(phi + h e_j) - f(phi - h e_j)) / (2 h), h = dC for
 // the concentrations and dT for the temperature.  2(N + 1) evaluations of the
 // source term per cell, through one inlined copy of it: f(phi + h e_j) is

@@ -19,8 +19,8 @@ Builds, on one hash-consed DAG (``expr.Graph``):
   dependence on C enters as one more chain-rule level (d[M]_j/dC_k is the
   collision efficiency), which keeps the dense third-body contributions to a
   rank-one update per row;
-* the simplified Jacobians of Section 3.3.1 (constant-QSS and zero-QSS) and
-  the finite-difference temperature column of Section 3.3.2 as build options;
+* the simplified Jacobians of Section 3.2.1 (constant-QSS and zero-QSS) and
+  the finite-difference temperature column of Section 3.2.2 as build options;
 * the temperature row from Tdot = -T sum_k (h_k/RT - 1) w_k / sum_k C_k (c_p,k/R - 1)
   (constant volume), differentiated with the production rates as
   placeholders and closed with the rows of J.
@@ -336,7 +336,7 @@ class _Builder:
                 J[i][c] = acc
         fd_vars = None
         if self.t_column == "fd":
-            # Section 3.3.2: dw/dT by a central difference of the production
+            # Section 3.2.2: dw/dT by a central difference of the production
             # rates at T + h and T - h (h an exact power of two, so that both
             # shifted temperatures and 1/(2h) are exact); the full QSS
             # evaluation, C_Q included, is repeated at each temperature.
@@ -413,8 +413,8 @@ def build_model(ir: MechIR, jac_variant: str = "exact", t_column: str = "analyti
     """``jac_variant``: "exact" (Eq. JQSS with the chain rule through C_Q),
     "const_qss" (the second term of Eq. JQSS dropped: C_Q held at its solved
     value) or "zero_qss" (that term dropped and C_Q set to zero inside the
-    Jacobian), Section 3.3.1.  ``t_column``: "analytic" or "fd" (central
-    difference in T, Section 3.3.2).  The temperature row always follows from
+    Jacobian), Section 3.2.1.  ``t_column``: "analytic" or "fd" (central
+    difference in T, Section 3.2.2).  The temperature row always follows from
     the species rows by the chain rule; wdot and Tdot are exact in every
     variant."""
     return _Builder(ir, jac_variant, t_column).build()

@@ -1,12 +1,12 @@
 """Jacobian variants and the finite-difference Jacobian on the GPU.
 
-* The simplified Jacobians of Section 3.3.1 (constant-QSS, zero-QSS) and the
-  finite-difference temperature column of Section 3.3.2, each a build option
+* The simplified Jacobians of Section 3.2.1 (constant-QSS, zero-QSS) and the
+  finite-difference temperature column of Section 3.2.2, each a build option
   of the mechanism compiler, against the oracle's own implementation of the
   same variant (same gate as the exact Jacobian).
 * qss_jacobian_fd (central differences of the source term) against the
   oracle's FD Jacobian, with the running-error bound of the differences.
-* The Section 3.3 figures: the relative Frobenius error, Eq. (frobErr), of
+* The Section 3.2 figures: the relative Frobenius error, Eq. (frobErr), of
   each construction against the FD Jacobian on the paper's sampling protocol,
   and the nonzero fraction of the species block (Table memQSS).
 """
@@ -38,7 +38,7 @@ def dev(a):
 
 
 def paper_states(m, n, seed):
-    """Section 3.3.1 protocol: C ~ U[1e-4, 1] mol/m^3, T ~ U[300, 1300] K."""
+    """Section 3.2.1 protocol: C ~ U[1e-4, 1] mol/m^3, T ~ U[300, 1300] K."""
     rng = np.random.default_rng(seed)
     N = sum(1 for s in m["species"] if not s["qss"])
     C = rng.uniform(1e-4, 1.0, size=(N, n))
@@ -86,7 +86,7 @@ def test_fd_jacobian_rejects_bad_steps():
 
 @pytest.mark.parametrize("key", ["tiny", "hydrocarbon"])
 def test_section3_frobenius_error_and_sparsity(key):
-    """Eq. (frobErr) over 100 states of the Section 3.3.1 protocol, FD step
+    """Eq. (frobErr) over 100 states of the Section 3.2.1 protocol, FD step
     1e-4: the exact construction is close to the FD Jacobian (the paper's
     Fig. symb_stats: below 1e-5 relative), the simplified ones are not (Tab.
     nosymb_stab_stats: 8-72 %); zero-QSS removes nonzeros of the species block

@@ -317,7 +317,7 @@ def test_running_error_bound_holds(key, n):
 
 
 # ---------------------------------------------------------------------------
-# Simplified Jacobians (Section 3.3.1) and the FD temperature column (3.3.2)
+# Simplified Jacobians (Section 3.2.1) and the FD temperature column (3.2.2)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("key,n", [("tiny", 64), ("hydrocarbon", 16)])
@@ -372,7 +372,7 @@ def test_variants_coincide_without_qss_species():
 
 @pytest.mark.parametrize("key,n", [("tiny", 64), ("hydrocarbon", 16)])
 def test_fd_temperature_column(key, n):
-    """Section 3.3.2 reading: the species rows' T column by a central
+    """Section 3.2.2 reading: the species rows' T column by a central
     difference with h = 2^(e-20) (T in [2^e, 2^(e+1))).  It agrees with the
     complex-step T column to the difference's truncation and rounding error;
     the concentration columns are those of the analytic Jacobian."""
