@@ -91,3 +91,35 @@ def test_bdf2_needs_fewer_substeps():
     assert both.mean() > 0.5
     assert np.median(res[2][0][both]) * 2 < np.median(res[1][0][both]), (
         np.median(res[1][0][both]), np.median(res[2][0][both]))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_integrate_per_cell_intervals_and_ragged_tail(order):
+    """Per-cell intervals (dt_stride 1), ncells < ld: the tail columns are
+    untouched, and the integrated cells follow the oracle's integrator."""
+    key = "tiny"
+    m = workloads.mechanism(key)
+    om = oracle.OracleMech(m)
+    gm = binding.Mechanism(build_mechanism(m), 0)
+    ld, ncells = 600, 600 - 17
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells, ld=ld)
+    D = np.exp(np.random.default_rng(9).uniform(np.log(1e-9), np.log(1e-7), ld))
+    t, y = dev(T), dev(Y)
+    ns = torch.full((ld,), -5, dtype=torch.int32, device="cuda")
+    st = torch.full((ld,), -5, dtype=torch.int32, device="cuda")
+    gm.integrate(dev(rho), t, y, dev(D), precision=binding.QSS_LU_FP64, ncells=ncells, nsteps=ns, status=st,
+                 opts=binding.integrate_opts(**OPTS, order=order))
+    t, y, ns, st = t.cpu().numpy(), y.cpu().numpy(), ns.cpu().numpy(), st.cpu().numpy()
+    assert (ns[ncells:] == -5).all() and (st[ncells:] == -5).all()
+    assert np.array_equal(t[ncells:], T[ncells:]) and np.array_equal(y[:, ncells:], Y[:, ncells:])
+    To, Yo, nso, sto = om.integrate(rho[:ncells], T[:ncells], Y[:, :ncells], D[:ncells], order=order, **OPTS)
+    same = (st[:ncells] == sto) & (ns[:ncells] == nso)
+    assert same.mean() >= 0.9
+    done = same & (sto == 0)
+    assert done.mean() >= 0.7
+    W = om.W[:, None]
+    pg = np.vstack([rho[None, :ncells] * y[:, :ncells] / W, t[None, :ncells]])[:, done]
+    po = np.vstack([rho[None, :ncells] * Yo / W, To[None]])[:, done]
+    atol = np.r_[np.full(om.N, 1e-12), 1e-8][:, None]
+    ok = np.abs(pg - po) <= 1e-8 * np.abs(po) + atol
+    assert ok.all(axis=0).mean() >= 0.99
