@@ -227,7 +227,7 @@ typedef struct {
   double h0;                     /* first substep in s (0: 1 % of the interval)     */
   double h_min;                  /* smallest substep / interval (default 1e-14)     */
   int max_rounds;                /* substep attempts per cell (default 400)         */
-  qss_newton_opts newton;        /* each substep's Newton solve                      */
+  qss_newton_opts newton;        /* each substep's Newton solve (default max_iter 6) */
   int order;                     /* 1 backward Euler (default), 2 variable-step BDF2 */
 } qss_integrate_opts;
 

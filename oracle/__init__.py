@@ -332,7 +332,7 @@ class OracleMech:
 
     def integrate(self, rho, T, Y, dt_total, rtol=1e-4, atol_C=1e-10, atol_T=1e-4, h0=0.0, h_min=1e-14,
                   max_rounds=400, newton_rtol=1e-12, newton_atol_C=1e-20, newton_atol_T=1e-10,
-                  max_iter=20, order=1, nthreads=0):
+                  max_iter=6, order=1, nthreads=0):
         """Integration over dt_total by error-controlled substeps of order 1
         (backward Euler) or 2 (variable-step BDF2); returns (T_new, Y_new,
         nsteps, status)."""

@@ -46,9 +46,10 @@ class IntegrateOpts(ctypes.Structure):
 
 def integrate_opts(rtol=1e-4, atol_C=1e-10, atol_T=1e-4, h0=0.0, h_min=1e-14, max_rounds=400,
                    newton: Optional["NewtonOpts"] = None, order=1) -> IntegrateOpts:
-    """order 1: backward-Euler substeps; 2: variable-step BDF2 substeps."""
+    """order 1: backward-Euler substeps; 2: variable-step BDF2 substeps.  The
+    substep Newton defaults to at most 6 iterations (the library's default)."""
     return IntegrateOpts(rtol, atol_C, atol_T, h0, h_min, max_rounds,
-                         newton if newton is not None else NewtonOpts(20, 1e-12, 1e-20, 1e-10, 10, 1e-8),
+                         newton if newton is not None else NewtonOpts(6, 1e-12, 1e-20, 1e-10, 10, 1e-8),
                          order)
 
 
