@@ -25,12 +25,12 @@ def dev(a):
 
 
 @pytest.mark.parametrize("order", [1, 2])
-@pytest.mark.parametrize("key,ncells,D", [("tiny", 512, 1e-7), ("hydrocarbon", 64, 1e-8)])
+@pytest.mark.parametrize("key,ncells,D", [("tiny", 512, 1e-7), ("hydrocarbon", 64, 1e-8), ("large", 32, 1e-10)])
 @pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
 def test_integrate_matches_oracle(key, ncells, D, prec, order):
     m = workloads.mechanism(key)
     om = oracle.OracleMech(m)
-    gm = binding.Mechanism(build_mechanism(m), 0)
+    gm = binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
     t, y = dev(T), dev(Y)
     ns, st = gm.integrate(dev(rho), t, y, D, precision=prec, opts=binding.integrate_opts(**OPTS, order=order))
