@@ -150,6 +150,29 @@ def cubin_digest(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
+def _profile_lines(kernel, workload):
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    vals = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("@") and ":" in line:
+                k, v = line[1:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    return vals
+
+
+def profile_value(kernel, workload, cubin_key, name):
+    """A figure of the committed ncu summary of this kernel ('@name: value'),
+    if it was taken on the same compiled kernel; e.g. hw_fp64_frac, the
+    hardware FP64 flops ((2 dfma + dadd + dmul) per cycle, ncu) over twice
+    the DFMA peak rate."""
+    vals = _profile_lines(kernel, workload)
+    try:
+        return float(vals[name]) if vals.get("cubin_sha256") == cubin_key else None
+    except (KeyError, ValueError):
+        return None
+
+
 def traffic_from_profile(kernel, workload, cubin_key, ncells):
     """DRAM bytes per launch from the committed ncu summary of this kernel
     (lines starting with '@'), if it was taken on the same compiled kernel
@@ -503,20 +526,19 @@ def main():
     flops_cell = meta["flops_jac"]
     achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
     parts = int(meta.get("jac_parts", 0) or 0)
-    launches_per_step = 1
-    if parts >= 2:
-        # the library processes a partitioned Jacobian in chunks that fit its
-        # 4 GiB frontier buffer: one prefix and `parts` group launches each
-        fr_cells = max(32, ((4 << 30) // (8 * int(meta["frontier"]))) // 32 * 32)
-        launches_per_step = -(-ncells // fr_cells) * (parts + 1)
+    # a partitioned Jacobian runs in chunks that fit the handle's frontier
+    # buffer: one prefix and `parts` group launches each
+    launches_per_step = gm.jacobian_launches(ncells)
     jac_kernel = "qss_jac_kernel" if parts < 2 else f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel"
-    traffic = traffic_from_profile("qss_jac_kernel", key, cubin_digest(os.path.join(art, "jac.cubin")),
-                                   ncells) if parts < 2 else None
+    cubin_key = cubin_digest(os.path.join(art, "jac.cubin")) if parts < 2 else None
+    traffic = traffic_from_profile("qss_jac_kernel", key, cubin_key, ncells) if parts < 2 else None
+    hw_frac = profile_value("qss_jac_kernel", key, cubin_key, "hw_fp64_frac") if parts < 2 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "measured live on this GPU: FP64 DFMA microbenchmark "
                            "(qss_measure_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
             "flops_per_cell": flops_cell, "fp64_instr_per_cell_est": meta.get("fp64_instr_jac"),
+            "hw_fp64_frac_ncu": hw_frac,
             "kernel": jac_kernel, "kernel_ms": kernel_ms,
             "hbm_algorithmic_gbs": (8.0 * (2 + gm.N + gm.N + 1 + n * n) * ncells) / (kernel_ms * 1e-3) / 1e9}
 

@@ -142,6 +142,12 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
  * QSS_ERR_INVALID_ARG if the limit holds fewer than 32 cells. */
 int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 
+/* Number of kernel launches qss_jacobian makes for ncells cells with the
+ * handle's current frontier limit: 1 for a single-kernel Jacobian, (chunks) x
+ * (groups + 1) for a partitioned one (for launch accounting).  Errors:
+ * QSS_ERR_INVALID_ARG for a null handle or output, or ncells < 0. */
+int qss_jacobian_launches(qss_mech_t mech, int64_t ncells, int64_t* launches);
+
 /* Central finite-difference Jacobian of f = (wdot, Tdot), the reference of
  * Eq. (frobErr): column j = (f(phi + h e_j) - f(phi - h e_j)) / (2h), with the
  * absolute step h = dC (mol/m^3) for the concentration columns and h = dT (K)

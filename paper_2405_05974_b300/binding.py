@@ -88,6 +88,7 @@ def lib():
         L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
+        L.qss_jacobian_launches.argtypes = [_vp, _i64, ctypes.POINTER(_i64)]
         L.qss_mech_jac_pattern.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                                            ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
         L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
@@ -232,6 +233,12 @@ class Mechanism:
         rows = [i * n + self.jac_col[p] for i in range(n) for p in range(self.jac_row_ptr[i], self.jac_row_ptr[i + 1])]
         out[torch.tensor(rows, device=jac.device)] = jac
         return out
+
+    def jacobian_launches(self, ncells: int) -> int:
+        """Kernel launches of one qss_jacobian call over ncells cells."""
+        v = _i64()
+        check(lib().qss_jacobian_launches(self.h, int(ncells), ctypes.byref(v)))
+        return v.value
 
     def set_frontier_bytes(self, nbytes: int):
         """Size limit of the partitioned Jacobian's frontier buffer."""

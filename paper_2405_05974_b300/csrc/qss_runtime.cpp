@@ -347,6 +347,16 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   return QSS_OK;
 }
 
+int qss_jacobian_launches(qss_mech_t m, int64_t ncells, int64_t* launches) {
+  if (!m || !launches || ncells < 0) return fail(QSS_ERR_INVALID_ARG, "bad argument");
+  if (ncells == 0) { *launches = 0; return QSS_OK; }
+  if (m->jac_parts < 2) { *launches = 1; return QSS_OK; }
+  const size_t per = frontier_bytes_per_cell(m);
+  const int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(m->fr_budget / per)), (ncells + 31) / 32 * 32);
+  *launches = (ncells + want - 1) / want * (m->jac_parts + 1);
+  return QSS_OK;
+}
+
 int qss_mech_set_frontier_bytes(qss_mech_t m, size_t bytes) {
   if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
   if (m->jac_parts >= 2 && bytes < 32 * frontier_bytes_per_cell(m))

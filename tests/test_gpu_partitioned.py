@@ -55,8 +55,12 @@ def test_partitioned_several_frontier_chunks():
     gp.set_frontier_bytes(400 << 20)
     try:
         Jp, wp, tp = gp.jacobian(r, t, y)
+        launches = gp.jacobian_launches(ncells)
     finally:
         gp.set_frontier_bytes(4 << 30)
+    # several chunks of one prefix and four group launches each
+    assert launches % 5 == 0 and launches >= 10, launches
+    assert gp.jacobian_launches(ncells) < launches and gpu_mech(key, 0).jacobian_launches(ncells) == 1
     Jm, wm, tm = gpu_mech(key, 0).jacobian(r, t, y)
     Jp, Jm = Jp.cpu().numpy(), Jm.cpu().numpy()
     idx = np.arange(0, ncells, 499)
