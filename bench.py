@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--implicit-ncells", type=int, default=0)
     p.add_argument("--jac-parts", type=int, default=-1,
                    help="Jacobian as a prefix + this many column-group kernels (default: per workload)")
+    p.add_argument("--jac-format", default="dense", choices=["dense", "csr"],
+                   help="store every Jacobian entry or only the structural nonzeros")
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -451,7 +453,8 @@ def main():
            "mechanism": {"transported": sum(1 for s in mech["species"] if not s["qss"]),
                          "qss": sum(1 for s in mech["species"] if s["qss"]),
                          "reactions": len(mech["reactions"])},
-           "layout": "SoA fp64, ld = ncells", "l2": "inputs and outputs larger than L2 (no flush)",
+           "layout": "SoA fp64, ld = ncells" + ("" if a.jac_format == "dense" else
+                                                    ", Jacobian as its structural nonzeros (CSR order)"), "l2": "inputs and outputs larger than L2 (no flush)",
            "parallelism": f"independent batches x{world}"}
 
     if a.impl == "reference":
@@ -482,6 +485,8 @@ def main():
     opts = workloads.build_options(key)
     if a.jac_parts >= 0:
         opts["jac_parts"] = a.jac_parts
+    if a.jac_format != "dense":
+        opts["jac_format"] = a.jac_format
     art = autotune.artefact(mech, torch.cuda.get_device_name(local), **opts)
     meta = load_meta(art)
     gm = binding.Mechanism(art, local)
