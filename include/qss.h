@@ -142,6 +142,14 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
  * QSS_ERR_INVALID_ARG if the limit holds fewer than 32 cells. */
 int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 
+/* Size limit in bytes of the handle's Newton scratch, used by
+ * qss_implicit_step and qss_integrate (batches larger than the limit run in
+ * chunks, each with its own tail of Newton iterations in which few cells are
+ * left).  Default: 1/16 of the device's memory, at least 1 GiB.  A chunk holds
+ * at least 32 cells whatever the limit; the scratch is allocated on first use
+ * and kept (freed by qss_mech_free). */
+int qss_mech_set_newton_bytes(qss_mech_t mech, size_t bytes);
+
 /* Number of kernel launches qss_jacobian makes for ncells cells with the
  * handle's current frontier limit: 1 for a single-kernel Jacobian, (chunks) x
  * (groups + 1) for a partitioned one (for launch accounting).  Errors:

@@ -89,6 +89,7 @@ def lib():
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.qss_jacobian_launches.argtypes = [_vp, _i64, ctypes.POINTER(_i64)]
+        L.qss_mech_set_newton_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.qss_mech_jac_pattern.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                                            ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
         L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
@@ -239,6 +240,11 @@ class Mechanism:
         v = _i64()
         check(lib().qss_jacobian_launches(self.h, int(ncells), ctypes.byref(v)))
         return v.value
+
+    def set_newton_bytes(self, nbytes: int):
+        """Size limit of the Newton scratch of the implicit step and the
+        interval integrator (default 1/16 of the device's memory)."""
+        check(lib().qss_mech_set_newton_bytes(self.h, int(nbytes)))
 
     def set_frontier_bytes(self, nbytes: int):
         """Size limit of the partitioned Jacobian's frontier buffer."""

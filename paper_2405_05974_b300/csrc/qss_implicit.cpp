@@ -13,7 +13,6 @@
 using namespace qss;
 
 namespace {
-constexpr size_t kScratchBudget = size_t(4) << 30;   // bytes of Newton scratch per handle
 
 }  // namespace
 
@@ -153,7 +152,7 @@ extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   const size_t per_cell = newton_scratch_per_cell(m, precision);
-  const int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(kScratchBudget / per_cell)),
+  const int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per_cell)),
                                          (ncells + 31) / 32 * 32);
   rc = scratch_acquire(m, per_cell * (size_t)want + 256, (CUstream)stream);
   if (rc) return rc;

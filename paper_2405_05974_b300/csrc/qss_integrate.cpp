@@ -21,7 +21,6 @@ using namespace qss;
 
 namespace {
 
-constexpr size_t kIntegBudget = size_t(4) << 30;   // bytes of integration scratch per call
 constexpr int kCheckEvery = 8;                     // rounds between host checks of the count
 
 struct IntegOptsDev {   // layout of QssIntegOpts in qss_newton.cuh
@@ -64,7 +63,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   CUstream st = (CUstream)stream;
   const int N = m->N, n = N + 1;
   const size_t per = integ_per_cell(m, precision);
-  const int64_t S = std::min<int64_t>(chunk_cells(m, (int64_t)(kIntegBudget / per)), (ncells + 31) / 32 * 32);
+  const int64_t S = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per)), (ncells + 31) / 32 * 32);
   // layout (offsets in bytes, every array 256-byte aligned)
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t D = al((size_t)S * sizeof(double)), I = al((size_t)S * sizeof(int));

@@ -48,6 +48,10 @@ struct qss_mech_s {
   CUdeviceptr newton_scratch = 0;
   size_t newton_scratch_bytes = 0;
   CUevent newton_done = nullptr;   // recorded after each call's last use of the scratch
+  // size limit of that scratch (qss_mech_set_newton_bytes; default 1/16 of
+  // the device's memory, at least 1 GiB): larger chunks mean fewer Newton
+  // tails, the iterations in which only a few slow cells are left
+  size_t newton_budget = size_t(4) << 30;
 };
 
 namespace qss {

@@ -240,6 +240,9 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
         tpb > 0)
       m->upd_threads[i] = tpb;
   }
+  size_t free_b = 0, total_b = 0;
+  if (drv().cuMemGetInfo(&free_b, &total_b) == CUDA_SUCCESS && total_b > 0)
+    m->newton_budget = std::max<size_t>(size_t(1) << 30, total_b / 16);
   // cells of one full wave of the (first) Jacobian kernel: chunked paths use
   // multiples of it, so that no chunk ends in a partly filled wave
   int sms = 0, per_sm = 0;
@@ -344,6 +347,13 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
       return rc;
   }
   CU_TRY(drv().cuEventRecord(m->fr_done, s));
+  return QSS_OK;
+}
+
+int qss_mech_set_newton_bytes(qss_mech_t m, size_t bytes) {
+  if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
+  std::lock_guard<std::mutex> lock(m->mu);
+  m->newton_budget = bytes;
   return QSS_OK;
 }
 
