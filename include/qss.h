@@ -137,9 +137,10 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
 /* A mechanism built with a partitioned Jacobian (a prefix kernel and column-
  * group kernels exchanging per-cell values through a frontier buffer) runs
  * qss_jacobian in chunks of cells that fit that buffer, which the handle owns
- * and keeps.  This sets its size limit in bytes (default 4 GiB; larger chunks
- * fill the GPU better).  No effect for a single-kernel Jacobian.  Errors:
- * QSS_ERR_INVALID_ARG if the limit holds fewer than 32 cells. */
+ * and keeps.  This sets its size limit in bytes (default 1/16 of the device's
+ * memory, at least 1 GiB; larger chunks mean fewer launches).  No effect for
+ * a single-kernel Jacobian.  Errors: QSS_ERR_INVALID_ARG if the limit holds
+ * fewer than 32 cells. */
 int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 
 /* Size limit in bytes of the handle's Newton scratch, used by

@@ -30,7 +30,8 @@ struct qss_mech_s {
   // across streams (recorded after each call's last group kernel)
   CUdeviceptr fr_scratch = 0;
   int64_t fr_cells = 0;
-  size_t fr_budget = size_t(4) << 30;   // bytes of that buffer (qss_mech_set_frontier_bytes)
+  size_t fr_budget = size_t(4) << 30;   // bytes of that buffer (qss_mech_set_frontier_bytes;
+                                        // set at load to 1/16 of the device's memory)
   CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
   // stored Jacobian entries per cell and their pattern (CSR; dense = all)

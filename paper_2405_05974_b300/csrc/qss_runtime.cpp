@@ -241,8 +241,10 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
       m->upd_threads[i] = tpb;
   }
   size_t free_b = 0, total_b = 0;
-  if (drv().cuMemGetInfo(&free_b, &total_b) == CUDA_SUCCESS && total_b > 0)
+  if (drv().cuMemGetInfo(&free_b, &total_b) == CUDA_SUCCESS && total_b > 0) {
     m->newton_budget = std::max<size_t>(size_t(1) << 30, total_b / 16);
+    m->fr_budget = m->newton_budget;
+  }
   // cells of one full wave of the (first) Jacobian kernel: chunked paths use
   // multiples of it, so that no chunk ends in a partly filled wave
   int sms = 0, per_sm = 0;
