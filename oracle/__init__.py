@@ -10,7 +10,12 @@ NumPy arrays across ctypes.  It shares no code with the CUDA path.
 Parity status of each function (see the test files named beside them):
   eval (wdot, Tdot, C_QSS, J) ..... pinned: closed forms, invariants,
                                      complex-step, central and one-sided FD,
-                                     binary128 rerun (tests/test_oracle_*.py)
+                                     binary128 rerun (tests/test_oracle_*.py);
+                                     the Troe broadening by its centre value,
+                                     its pole and the affine law of 1/f1 in
+                                     1/x; Tdot by a single-coefficient closed
+                                     form and conservation of the internal
+                                     energy along an integration
   be_step ......................... pinned: closed-form linear case, mass
                                      invariant, Newton residual
   eval_variant (constant-QSS, zero-QSS, FD T column)

@@ -201,6 +201,76 @@ def test_troe_centre_point():
     assert o["wdot"][2, 0] == pytest.approx(1e7 * Pr / (1 + Pr) * Fc, rel=1e-12)
 
 
+def _troe_log10_F(troe, T, x, lFc):
+    """log10 of the oracle's broadening factor at log10 Pr = x - c(F_cent):
+    the falloff rate divided by its Lindemann part k_inf Pr/(1 + Pr) C_A C_B."""
+    c = -0.4 - 0.67 * lFc
+    Pr = 10.0 ** (x - c)
+    C = [1.0, 1.0, 0.0, 2.0]
+    A0 = Pr * 1e7 / (sum(C) * 1e-12)
+    m = _troe_mech(1e13, A0, troe)
+    o = oracle.OracleMech(m).eval(*state_from_C(m, C, T))
+    return math.log10(o["wdot"][2, 0] / (1e7 * Pr / (1 + Pr)))
+
+
+# (alpha, T***, T*, T**) and T: each F_cent term alone, and mixtures
+_TROE_CASES = [((0.0, 300.0, 2000.0, 1e300), 1300.0),     # (1 - alpha) exp(-T/T***) only
+               ((1.0, 300.0, 2000.0, 1e300), 1300.0),     # alpha exp(-T/T*) only
+               ((0.0, 1.0, 2000.0, 6000.0), 1300.0),      # exp(-T**/T) only
+               ((0.35, 300.0, 2000.0, 6000.0), 1300.0),
+               ((0.7, 120.0, 900.0, 4500.0), 950.0)]
+
+
+def _fcent(troe, T):
+    alpha, T3, T1, T2 = troe
+    return (1 - alpha) * math.exp(-T / T3) + alpha * math.exp(-T / T1) + math.exp(-T2 / T)
+
+
+@pytest.mark.parametrize("troe,T", _TROE_CASES)
+def test_troe_fcent_terms_at_centre(troe, T):
+    """At the centre of the broadening curve (f1 = 0) F equals F_cent.  The
+    parameter sets switch on one F_cent term at a time ((1 - alpha)
+    exp(-T/T***), alpha exp(-T/T*), exp(-T**/T)), so a wrong sign, a swapped
+    T/T* ratio or a dropped term in any of them moves the centre value."""
+    lFc = math.log10(_fcent(troe, T))
+    assert _troe_log10_F(troe, T, 0.0, lFc) == pytest.approx(lFc, rel=1e-12)
+
+
+@pytest.mark.parametrize("troe,T", _TROE_CASES[3:])
+def test_troe_broadening_off_centre(troe, T):
+    """Away from the centre, the Gilbert-Luther-Troe broadening satisfies
+    log10 F = log10 F_cent / (1 + f1^2) with 1/f1 = n'/x - 0.14, an exact
+    affine relation between 1/f1 and 1/x (x = log10 Pr + c).  Recovering f1
+    from the oracle's F at points on both sides of the centre and fitting
+    1/f1 against 1/x must give intercept -0.14 and slope
+    n' = 0.75 - 1.27 log10 F_cent with zero residual: 0.41 for 0.14, a sign
+    slip in n' (0.75 + 1.27 log F_cent), a wrong c (which shifts every x) or a
+    missing square fails it.  The fit is also the large-|Pr| limit: as
+    1/x -> 0 the intercept is the limit of 1/f1, log10 F -> log10 F_cent /
+    (1 + 0.14^-2)."""
+    lFc = math.log10(_fcent(troe, T))
+    xs = np.array([-12.0, -6.0, -3.0, -1.5, -0.6, 0.4, 1.0, 2.5, 4.0])
+    lF = np.array([_troe_log10_F(troe, T, x, lFc) for x in xs])
+    f1 = np.sign(xs) * np.sqrt(lFc / lF - 1.0)
+    A = np.vstack([1.0 / xs, np.ones_like(xs)]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, 1.0 / f1, rcond=None)
+    assert icpt == pytest.approx(-0.14, abs=1e-10)
+    assert slope == pytest.approx(0.75 - 1.27 * lFc, rel=1e-10)
+    assert np.max(np.abs(A @ np.array([slope, icpt]) - 1.0 / f1)) <= 1e-10
+
+
+@pytest.mark.parametrize("troe,T", _TROE_CASES[3:])
+def test_troe_broadening_vanishes_at_pole(troe, T):
+    """Where the denominator n' - 0.14 x of f1 vanishes (x = n'/0.14), f1 is
+    infinite and the broadening factor is exactly 1; just past the pole F
+    drops below 1 again.  Pins n' and 0.14 jointly at a point far from the
+    centre."""
+    lFc = math.log10(_fcent(troe, T))
+    xp = (0.75 - 1.27 * lFc) / 0.14
+    assert abs(_troe_log10_F(troe, T, xp, lFc)) <= 1e-13
+    assert _troe_log10_F(troe, T, xp + 2.0, lFc) < -1e-4
+
+
 # ---------------------------------------------------------------------------
 # QSS closed forms
 # ---------------------------------------------------------------------------
@@ -503,3 +573,74 @@ def test_be_mass_and_residual_hydrocarbon():
     G = phi - phi0 - dt * f
     scale = np.abs(phi) + np.abs(phi0) + dt * np.abs(f)
     assert np.all(np.abs(G[:, ok]) <= 1e-10 * scale[:, ok].max(axis=0))
+
+
+# ---------------------------------------------------------------------------
+# Temperature equation (constant volume, Section 3.2.2: heat release from the
+# production rates)
+# ---------------------------------------------------------------------------
+
+def test_tdot_single_coefficient_closed_form():
+    """A -> B + C, irreversible, NASA sets with only a1 and a6: h/RT = a1 + a6/T,
+    so the molar internal energy is u = R (T (a1 - 1) + a6) and c_v = R (a1 - 1).
+    With q = k_f C_A the constant-volume energy equation gives
+    Tdot = -q sum_k nu_k (T (a1_k - 1) + a6_k) / sum_k C_k (a1_k - 1).
+    The reaction changes the mole count, so h in place of u (an extra R T per
+    mole) fails, and c_p in place of c_v in the denominator fails."""
+    T = 1234.5
+    nasa = {"A": (3.0, 1500.0), "B": (4.2, -2500.0), "C": (2.5, 700.0), "N2": (3.5, 0.0)}
+    sp = [hm.species("A", {"C": 1, "H": 4}, nasa=[nasa["A"][0], 0, 0, 0, 0, nasa["A"][1], 0.0]),
+          hm.species("B", {"C": 1, "H": 3}, nasa=[nasa["B"][0], 0, 0, 0, 0, nasa["B"][1], 0.0]),
+          hm.species("C", {"H": 1}, nasa=[nasa["C"][0], 0, 0, 0, 0, nasa["C"][1], 0.0]),
+          hm.species("N2", {"N": 2}, nasa=[nasa["N2"][0], 0, 0, 0, 0, 0.0, 0.0])]
+    kf = 3.0e4
+    m = hm.mech("tdot", sp, [hm.reaction({"A": 1}, {"B": 1, "C": 1}, kf, reversible=False)])
+    C = {"A": 0.8, "B": 0.3, "C": 0.2, "N2": 5.0}
+    o = oracle.OracleMech(m).eval(*state_from_C(m, [C[k] for k in ("A", "B", "C", "N2")], T))
+    q = kf * C["A"]
+    nu = {"A": -1, "B": 1, "C": 1, "N2": 0}
+    num = sum(nu[k] * (T * (nasa[k][0] - 1.0) + nasa[k][1]) for k in nu)
+    den = sum(C[k] * (nasa[k][0] - 1.0) for k in nu)
+    assert o["Tdot"][0] == pytest.approx(-q * num / den, rel=1e-13)
+
+
+def _internal_energy(mech, om, rho, T, Y):
+    """U = sum_k C_k u_k(T) per unit volume, with the molar internal energy
+    u = h - R T from the NASA-7 enthalpy h/RT = a1 + a2 T/2 + a3 T^2/3 +
+    a4 T^3/4 + a5 T^4/5 + a6/T (single-range sets); also returns
+    sum_k |C_k u_k| as a scale."""
+    tr = [s for s in mech["species"] if not s["qss"]]
+    C = om.conc(rho, Y)
+    u = np.zeros_like(C)
+    for k, s in enumerate(tr):
+        assert s["nasa_lo"] == s["nasa_hi"]
+        a = s["nasa_lo"]
+        h_RT = a[0] + a[1] * T / 2 + a[2] * T ** 2 / 3 + a[3] * T ** 3 / 4 + a[4] * T ** 4 / 5 + a[5] / T
+        u[k] = hm.R * T * (h_RT - 1.0)
+    return (C * u).sum(0), np.abs(C * u).sum(0), C, u
+
+
+def test_internal_energy_conserved_along_integration():
+    """At constant volume the mixture's internal energy sum_k C_k u_k(T) is
+    constant: the chemistry only moves energy between chemical and sensible
+    forms.  Integrating the tiny workload over 2e-9 s (T moves by up to a few
+    hundred K), the oracle's trajectory keeps U to 2e-4 of the sensible energy
+    it moved at rtol 1e-7, and the drift falls like the backward-Euler global
+    error, tol^(1/2) (ten times over two decades); c_p in place of c_v, or h
+    in place of u, in Tdot changes the temperature rise by tens of percent
+    and fails it."""
+    m = workloads.mechanism("tiny")
+    om = oracle.OracleMech(m)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["tiny"], 6)
+    U0, S0, _, u0 = _internal_energy(m, om, rho, T, Y)
+    drift = []
+    for rtol in (1e-5, 1e-7):
+        T2, Y2, ns, st = om.integrate(rho, T, Y, 2e-9, rtol=rtol, atol_C=1e-14, atol_T=1e-8,
+                                      max_rounds=20000)
+        assert np.all(st == 0)
+        U1, _, C1, u1 = _internal_energy(m, om, rho, T2, Y2)
+        sensible = np.abs((C1 * (u1 - u0)).sum(0))
+        assert np.all(np.abs(T2 - T) > 1.0)
+        drift.append(np.abs(U1 - U0) / sensible)
+    assert np.all(drift[1] <= 2e-4), drift
+    assert np.all(drift[0] / drift[1] > 5.0), drift
