@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--jac-format", default="dense", choices=["dense", "csr"],
                    help="store every Jacobian entry or only the structural nonzeros")
     p.add_argument("--serve-seconds", type=float, default=8.0)
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the tiny and large workloads' entries (by_config)")
     return p.parse_args()
 
 
@@ -237,9 +239,29 @@ def cpu_baseline(mech, states_cfg, seconds, ncells_cap=1 << 20):
 # ---------------------------------------------------------------------------
 # implicit step (backward Euler, FP64 LU vs FP32 LU + FP64 refinement)
 # ---------------------------------------------------------------------------
-def implicit_bench(gm, mech, ncells, dt, oracle_sample=0):
-    """One timed step per precision on the implicit workload (2^20 hydrocarbon
-    cells, dt = 1e-6 s) after one warm-up step."""
+def _phi(gm, rho, T, Y):
+    W = np.array(gm.W)[:, None]
+    return np.vstack([rho[None, :] * Y / W, T[None, :]])
+
+
+def _rel_err(gm, pa, pb):
+    """max_k |pa_k - pb_k| / (|pb_k| + 10 atol_k) per cell (atol_C 1e-20, atol_T 1e-10)."""
+    atol = np.r_[np.full(gm.N, 1e-20), 1e-10][:, None]
+    with np.errstate(invalid="ignore"):
+        return np.max(np.abs(pa - pb) / (np.abs(pb) + 10 * atol), axis=0)
+
+
+STATUS = ("converged", "maxiter", "nonfinite", "singular")
+
+
+def implicit_bench(gm, mech, ncells, dt):
+    """One timed step per precision (after one warm-up step) of the implicit
+    workload: hydrocarbon mechanism and states, `ncells` cells, step dt.
+    Reports the throughput over all cells and over the cells that converged,
+    the status counts, Newton iterations, the FP32-IR/FP64 difference on the
+    cells both converge on and the cells whose status differs.  Returns the
+    line and the host copies of the results (for the oracle comparison of the
+    CPU-baseline leg)."""
     import torch
     from paper_2405_05974_b300 import binding, mechgen, workloads
     rho, T, Y = mechgen.generate_states(mech, workloads.STATES["implicit"], ncells)
@@ -264,26 +286,74 @@ def implicit_bench(gm, mech, ncells, dt, oracle_sample=0):
         stn, itn = st.cpu().numpy(), it.cpu().numpy()
         out[name] = (t.cpu().numpy(), y.cpu().numpy(), stn)
         conv = stn == 0
-        res[name] = {"cells_per_s": ncells / (ms * 1e-3), "ms": ms,
-                     "status_counts": {"converged": int(conv.sum()), "maxiter": int((stn == 1).sum()),
-                                       "nonfinite": int((stn == 2).sum()), "singular": int((stn == 3).sum())},
+        res[name] = {"cells_per_s": ncells / (ms * 1e-3),
+                     "converged_cells_per_s": int(conv.sum()) / (ms * 1e-3),
+                     "converged_fraction": float(conv.mean()), "ms": ms,
+                     "status_counts": {nm: int((stn == i).sum()) for i, nm in enumerate(STATUS)},
                      "newton_iters_mean": float(itn[conv].mean()) if conv.any() else None,
                      "newton_iters_max": int(itn[conv].max()) if conv.any() else None}
     a, b = out["fp64"], out["fp32ir"]
     both = (a[2] == 0) & (b[2] == 0)
-    W = np.array(gm.W)[:, None]
-    ca, cb = rho[None, :] * a[1] / W, rho[None, :] * b[1] / W
-    pa, pb = np.vstack([ca, a[0][None]]), np.vstack([cb, b[0][None]])
-    atol = np.r_[np.full(gm.N, 1e-20), 1e-10][:, None]
-    rel = np.max(np.abs(pa - pb) / (np.abs(pa) + 10 * atol), axis=0)[both]
+    rel = _rel_err(gm, _phi(gm, rho, b[1], b[0]), _phi(gm, rho, a[1], a[0]))[both]
+    differ = a[2] != b[2]
     res["fp32ir_vs_fp64"] = {"cells_converged_both": int(both.sum()),
                              "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
                              "median_rel": float(np.median(rel)) if both.any() else None,
                              "max_rel": float(rel.max()) if both.any() else None,
-                             "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell"}
+                             "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell",
+                             "status_differs": int(differ.sum()),
+                             "status_pairs_fp64_to_fp32ir": {
+                                 f"{STATUS[i]}->{STATUS[j]}": int(((a[2] == i) & (b[2] == j)).sum())
+                                 for i in range(4) for j in range(4) if i != j and
+                                 ((a[2] == i) & (b[2] == j)).any()}}
     res["speedup_fp32ir_over_fp64"] = res["fp32ir"]["cells_per_s"] / res["fp64"]["cells_per_s"]
     res["workload"] = f"{mech['name']} backward Euler, dt = {dt:g} s, {ncells} cells"
-    return res
+    return res, (rho, T, Y, out)
+
+
+def implicit_cpu_baseline(gm, mech, dt, data, seconds):
+    """The oracle's backward-Euler step (as it stands, OpenMP on all host
+    threads) on a bounded sample of the same cells: its cells/s, and the GPU
+    results of the same sampled cells compared with it, for both forms."""
+    import oracle
+    rho, T, Y, out = data
+    n = rho.shape[0]
+    om = oracle.OracleMech(mech)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    order = rng.permutation(n)
+    done, chunk, el = 0, 256, 0.0
+    idx_all, res = [], []
+    while done < n and el < seconds:
+        idx = np.sort(order[done:done + chunk])
+        t0 = time.perf_counter()
+        To, Yo, ito, sto = om.be_step(rho[idx], T[idx], np.ascontiguousarray(Y[:, idx]), dt, max_iter=20,
+                                      nthreads=cores)
+        el += time.perf_counter() - t0
+        idx_all.append(idx)
+        res.append((To, Yo, sto))
+        done += idx.size
+        chunk = min(chunk * 2, 4096)
+    idx = np.concatenate(idx_all)
+    To = np.concatenate([r[0] for r in res])
+    Yo = np.concatenate([r[1] for r in res], axis=1)
+    sto = np.concatenate([r[2] for r in res])
+    po = _phi(gm, rho[idx], Yo, To)
+    cmp = {}
+    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8)):
+        Tg, Yg, stg = out[name]
+        pg = _phi(gm, rho[idx], Yg[:, idx], Tg[idx])
+        both = (sto == 0) & (stg[idx] == 0)
+        rel = _rel_err(gm, pg, po)[both]
+        cmp[name] = {"cells_compared": int(both.sum()),
+                     "status_agrees_with_oracle": float(np.mean(sto == stg[idx])),
+                     "frac_within_gate": float(np.mean(rel <= gate)) if both.any() else None,
+                     "gate": f"{gate:g} relative + 10 atol", "median_rel": float(np.median(rel)) if both.any() else None,
+                     "max_rel": float(rel.max()) if both.any() else None}
+    return {"value": done / el, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} randomly sampled cells of the step's {n}, {el:.1f} s on {cores} host threads",
+            "oracle_converged_fraction": float(np.mean(sto == 0)),
+            "gpu_vs_oracle_on_sample": cmp}
 
 
 def integrate_bench(gm, mech, ncells=16384, D=1e-9, rtol=1e-3, max_rounds=400):
@@ -442,51 +512,45 @@ def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, 
 
 
 # ---------------------------------------------------------------------------
-def main():
-    a = parse()
-    rank, world, local, pg = dist_setup()
-    from paper_2405_05974_b300 import workloads
-    key = a.workload
-    mech = workloads.mechanism(key)
-    ncells = a.ncells or workloads.NCELLS[key]
-    cfg = {"workload": f"{mech['name']} wdot+Jacobian", "ncells_per_gpu": ncells,
-           "mechanism": {"transported": sum(1 for s in mech["species"] if not s["qss"]),
-                         "qss": sum(1 for s in mech["species"] if s["qss"]),
-                         "reactions": len(mech["reactions"])},
-           "layout": "SoA fp64, ld = ncells" + ("" if a.jac_format == "dense" else
-                                                    ", Jacobian as its structural nonzeros (CSR order)"), "l2": "inputs and outputs larger than L2 (no flush)",
-           "parallelism": f"independent batches x{world}"}
+def _config(mech, key, ncells, world, jac_format="dense", l2="inputs and outputs larger than L2 (no flush)"):
+    return {"workload": f"{mech['name']} wdot+Jacobian", "ncells_per_gpu": ncells,
+            "mechanism": {"transported": sum(1 for s in mech["species"] if not s["qss"]),
+                          "qss": sum(1 for s in mech["species"] if s["qss"]),
+                          "reactions": len(mech["reactions"])},
+            "layout": "SoA fp64, ld = ncells" + ("" if jac_format == "dense" else
+                                                   ", Jacobian as its structural nonzeros (CSR order)"),
+            "l2": l2, "parallelism": f"independent batches x{world}"}
 
-    if a.impl == "reference":
-        if rank != 0:
-            return
-        vals = []
-        base = None
-        per = max(2.0, a.cpu_seconds / max(a.steps + a.warmup, 1))
-        for s in range(a.warmup + a.steps):
-            b = cpu_baseline(mech, workloads.STATES[key], seconds=per, ncells_cap=1 << 16)
-            if s >= a.warmup:
-                vals.append(b["value"])
-                base = b
-        v = float(np.median(vals))
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ncells / v * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic (seeded)", "config": cfg,
-                "cpu_baseline": {**base, "value": v},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return
 
+def _jac_cubin_digest(art, parts):
+    """Digest of the Jacobian's cubins (the single kernel, or the prefix and
+    group kernels in order), matched against the committed ncu summary."""
+    import hashlib
+    names = ["jac.cubin"] if parts < 2 else ["jac_prefix.cubin"] + [f"jac_g{i}.cubin" for i in range(parts)]
+    h = hashlib.sha256()
+    for nm in names:
+        h.update(open(os.path.join(art, nm), "rb").read())
+    return h.hexdigest()[:16] if parts >= 2 else cubin_digest(os.path.join(art, "jac.cubin"))
+
+
+def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=True, cpu_seconds=0.0,
+                   jac_parts=-1, jac_format="dense", flush_l2=False):
+    """Timed qss_jacobian steps (wdot + Tdot + J of `ncells` cells of workload
+    `key`) through the C ABI, CUDA events on the launching stream, max over
+    ranks; the roofline of the Jacobian kernel(s) against the FP64 peak
+    measured live; optionally the end-to-end rate from pinned host arrays and
+    the oracle's CPU baseline.  With flush_l2 a 256 MB buffer is written
+    between timed steps (for workloads whose arrays fit in L2) and only the
+    steps themselves are timed."""
     import torch
-    from paper_2405_05974_b300 import autotune, binding, mechgen
-    from paper_2405_05974_b300.qssc.build import build_mechanism, load_meta
-    torch.cuda.set_device(local)
+    from paper_2405_05974_b300 import autotune, binding, mechgen, workloads
+    from paper_2405_05974_b300.qssc.build import load_meta
+    mech = workloads.mechanism(key)
     opts = workloads.build_options(key)
-    if a.jac_parts >= 0:
-        opts["jac_parts"] = a.jac_parts
-    if a.jac_format != "dense":
-        opts["jac_format"] = a.jac_format
+    if jac_parts >= 0:
+        opts["jac_parts"] = jac_parts
+    if jac_format != "dense":
+        opts["jac_format"] = jac_format
     art = autotune.artefact(mech, torch.cuda.get_device_name(local), **opts)
     meta = load_meta(art)
     gm = binding.Mechanism(art, local)
@@ -495,60 +559,62 @@ def main():
     rho, T, Y = mechgen.generate_states(mech, st_cfg, ncells)
     d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
     r, t, y = d(rho), d(T), d(Y)
-    n = gm.n
     J = torch.empty((gm.jac_nnz, ncells), dtype=torch.float64, device="cuda")
     w = torch.empty((gm.N, ncells), dtype=torch.float64, device="cuda")
     td = torch.empty(ncells, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    flush = torch.empty(32 << 20, dtype=torch.float64, device="cuda") if flush_l2 else None
 
     def step():
         gm.jacobian(r, t, y, jac=J, wdot=w, Tdot=td, stream=stream)
 
-    for _ in range(max(a.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
     peak = binding.measure_fp64_peak(local, 200)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(a.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier(pg)
     torch.cuda.synchronize()
     g0 = torch.cuda.Event(enable_timing=True)
     g1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         g0.record(stream)
-        for i in range(a.steps):
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(float(i))
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
         g1.record(stream)
         torch.cuda.synchronize()
     barrier(pg)
-    total_ms = max_over_ranks(pg, g0.elapsed_time(g1))
     per = [e0.elapsed_time(e1) for e0, e1 in ev]
-    ms_step = total_ms / a.steps
-    value = ncells * world * a.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(pg, float(np.sum(per)) if flush is not None else g0.elapsed_time(g1))
+    ms_step = total_ms / steps
+    value = ncells * world * steps / (total_ms * 1e-3)
     kernel_ms = float(np.mean(per))
-    flops_cell = meta["flops_jac"]
-    achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
     parts = int(meta.get("jac_parts", 0) or 0)
-    # a partitioned Jacobian runs in chunks that fit the handle's frontier
-    # buffer: one prefix and `parts` group launches each
+    flops_cell = meta["flops_jac_parts"] if parts >= 2 else meta["flops_jac"]
+    achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
     launches_per_step = gm.jacobian_launches(ncells)
-    jac_kernel = "qss_jac_kernel" if parts < 2 else f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel"
-    cubin_key = cubin_digest(os.path.join(art, "jac.cubin")) if parts < 2 else None
-    traffic = traffic_from_profile("qss_jac_kernel", key, cubin_key, ncells) if parts < 2 else None
-    hw_frac = profile_value("qss_jac_kernel", key, cubin_key, "hw_fp64_frac") if parts < 2 else None
+    if parts < 2:
+        jac_kernel, prof = "qss_jac_kernel", "qss_jac_kernel"
+    else:
+        jac_kernel, prof = f"qss_jac_prefix_kernel + {parts} x qss_jac_group_kernel", "qss_jac_parts"
+    cubin_key = _jac_cubin_digest(art, parts)
+    traffic = traffic_from_profile(prof, key, cubin_key, ncells)
+    hw_frac = profile_value(prof, key, cubin_key, "hw_fp64_frac")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "measured live on this GPU: FP64 DFMA microbenchmark "
                            "(qss_measure_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
             "flops_per_cell": flops_cell, "fp64_instr_per_cell_est": meta.get("fp64_instr_jac"),
-            "hw_fp64_frac_ncu": hw_frac,
-            "kernel": jac_kernel, "kernel_ms": kernel_ms,
+            "hw_fp64_frac_ncu": hw_frac, "kernel": jac_kernel, "kernel_ms": kernel_ms,
+            "cubin_digest": cubin_key,
+            "algorithmic_bytes_per_cell": 8 * (2 + gm.N + gm.N + 1 + gm.jac_nnz),
             "hbm_algorithmic_gbs": (8.0 * (2 + gm.N + gm.N + 1 + gm.jac_nnz) * ncells) / (kernel_ms * 1e-3) / 1e9}
-
     e2e = None
-    if not a.no_e2e:
+    if do_e2e:
         rh = torch.from_numpy(rho).pin_memory()
         th = torch.from_numpy(T).pin_memory()
         yh = torch.from_numpy(np.ascontiguousarray(Y)).pin_memory()
@@ -556,13 +622,82 @@ def main():
         wh = torch.empty((gm.N, ncells), dtype=torch.float64).pin_memory()
         tdh = torch.empty(ncells, dtype=torch.float64).pin_memory()
         gm.jacobian_host(rh, th, yh, jac=Jh, wdot=wh, Tdot=tdh)     # warm-up (staging alloc)
-        e_steps = max(1, min(a.steps, 3))
+        e_steps = max(1, min(steps, 3))
         barrier(pg)
         t0 = time.perf_counter()
         for _ in range(e_steps):
             gm.jacobian_host(rh, th, yh, jac=Jh, wdot=wh, Tdot=tdh)
         el = max_over_ranks(pg, time.perf_counter() - t0)
         nchunks = -(-ncells // 65536)
+        d2h = 8 * (gm.jac_nnz + gm.N + 1) * ncells
+        e2e = {"value": ncells * world * e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (2 + gm.N) * ncells, "d2h_bytes_per_step": d2h,
+               "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
+               "gpu_launches_per_step": nchunks * (1 if parts < 2 else parts + 1),
+               "d2h_gbs_achieved": d2h * e_steps / el / 1e9}
+        del Jh
+    cpu = None
+    if rank == 0 and cpu_seconds > 0:
+        cpu = cpu_baseline(mech, workloads.STATES[key], cpu_seconds)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_step, "steps": steps,
+           "warmup": max(warmup, 3), "config": _config(mech, key, ncells, world, jac_format,
+                                                         "arrays fit in L2: a 256 MB buffer is written between "
+                                                         "timed steps" if flush_l2 else
+                                                         "inputs and outputs larger than L2 (no flush)"),
+           "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": steps * launches_per_step,
+           "clocks": clk.summary(),
+           "kernel": {"ptxas": {k: v for k, v in meta["kernels"].items() if k.startswith("qss_jac")},
+                      "defines": meta.get("defines", []),
+                      "ops_per_cell": meta["ops_jac"] if parts < 2 else
+                      {"prefix": meta["ops_prefix"], "groups": meta["ops_groups"]},
+                      "artefact": os.path.basename(art)}}
+    return out, (gm, r, t, y, mech)
+
+
+def main():
+    a = parse()
+    rank, world, local, pg = dist_setup()
+    from paper_2405_05974_b300 import workloads
+    key = a.workload
+    mech = workloads.mechanism(key)
+    ncells = a.ncells or workloads.NCELLS[key]
+    cfg = _config(mech, key, ncells, world, a.jac_format)
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        vals, walls, cells = [], [], []
+        base = None
+        per = max(2.0, a.cpu_seconds / max(a.steps + a.warmup, 1))
+        for s in range(a.warmup + a.steps):
+            t0 = time.perf_counter()
+            b = cpu_baseline(mech, workloads.STATES[key], seconds=per, ncells_cap=1 << 16)
+            wall = time.perf_counter() - t0
+            if s >= a.warmup:
+                vals.append(b["value"])
+                walls.append(wall)
+                base = b
+        v = float(np.median(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": float(np.median(walls)) * 1e3,
+                "ms_per_step_note": "wall time of one step = one bounded sample of the workload (see "
+                                    "cpu_baseline.sample); the full workload at this rate would take "
+                                    f"{ncells / v * 1e3:.0f} ms (extrapolated, cells are independent)",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded)", "config": cfg,
+                "cpu_baseline": {**base, "value": v},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_2405_05974_b300 import binding
+    from paper_2405_05974_b300.qssc.build import build_mechanism
+    torch.cuda.set_device(local)
+    head, (gm, r, t, y, _) = jacobian_bench(key, ncells, a.steps, a.warmup, local, rank, world, pg,
+                                           do_e2e=not a.no_e2e, jac_parts=a.jac_parts,
+                                           jac_format=a.jac_format)
+    if head["e2e"] is not None:
         # the host link on its own: one 2 GiB device -> pinned host copy
         hb = torch.empty(1 << 28, dtype=torch.float64).pin_memory()
         db = torch.empty(1 << 28, dtype=torch.float64, device="cuda")
@@ -571,32 +706,43 @@ def main():
         t1 = time.perf_counter()
         hb.copy_(db)
         torch.cuda.synchronize()
-        link = hb.numel() * 8 / (time.perf_counter() - t1) / 1e9
+        head["e2e"]["host_link_d2h_gbs"] = hb.numel() * 8 / (time.perf_counter() - t1) / 1e9
         del hb, db
-        d2h = 8 * (gm.jac_nnz + gm.N + 1) * ncells
-        e2e = {"value": ncells * world * e_steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": 8 * (2 + gm.N) * ncells,
-               "d2h_bytes_per_step": d2h,
-               "api": "qss_jacobian_host (pinned host arrays, chunked copy/compute overlap)",
-               "gpu_launches_per_step": nchunks,
-               "d2h_gbs_achieved": d2h * e_steps / el / 1e9,
-               "host_link_d2h_gbs": link}
-        del Jh
+    # the other workloads of the wdot+Jacobian metric (tiny: 4096 cells,
+    # L2-resident; large: 2^20 cells, partitioned Jacobian), each with its own
+    # roofline, end-to-end rate and CPU baseline
+    by_config = None
+    if not a.no_configs and key == "hydrocarbon" and ncells == workloads.NCELLS["hydrocarbon"]:
+        by_config = {}
+        for k2 in ("tiny", "large"):
+            c2, (g2, *_rest) = jacobian_bench(k2, workloads.NCELLS[k2], min(a.steps, 10), 3, local, rank, world,
+                                              pg, do_e2e=not a.no_e2e,
+                                              cpu_seconds=0.0 if a.no_cpu else 4.0, flush_l2=(k2 == "tiny"))
+            by_config[k2] = c2
+            del g2, _rest
+            torch.cuda.empty_cache()
     variants = None
     if not a.no_variants and rank == 0 and key in ("tiny", "hydrocarbon"):
         variants = variants_bench(key, gm, r, t, y)
     implicit = None
     if not a.no_implicit and key == "hydrocarbon":
-        implicit = implicit_bench(gm, mech, a.implicit_ncells or workloads.NCELLS["implicit"],
-                                  workloads.IMPLICIT_DT)
+        implicit = {}
+        for tag, dt in (("dt_1e-6", workloads.IMPLICIT_DT), ("dt_1e-11", workloads.IMPLICIT_DT_CONVERGING)):
+            res, data = implicit_bench(gm, mech, a.implicit_ncells or workloads.NCELLS["implicit"], dt)
+            if rank == 0 and not a.no_cpu:
+                res["cpu_baseline"] = implicit_cpu_baseline(gm, mech, dt, data, 4.0)
+            implicit[tag] = res
+            del data
+        implicit["note"] = ("dt_1e-6 is the configured step; at dt_1e-11 plain Newton from the initial "
+                            "state converges in >= 95 % of the cells (the synthetic states' fastest "
+                            "time scales are ~1e-11 s), so both forms are compared on nearly every cell")
     integration = None
     if a.integrate and key == "hydrocarbon" and rank == 0:
         integration = integrate_bench(gm, mech)
     serving = None
     if not a.no_serve and key == "hydrocarbon" and rank == 0:
-        from paper_2405_05974_b300 import binding as _b
         mechs = {k: (gm if k == "hydrocarbon" else
-                     _b.Mechanism(build_mechanism(workloads.mechanism(k), **workloads.build_options(k)), local))
+                     binding.Mechanism(build_mechanism(workloads.mechanism(k), **workloads.build_options(k)), local))
                  for k in ("tiny", "hydrocarbon", "large")}
         weights = [0.2, 0.6, 0.2]
         serving = {"mix": "tiny 0.2 / hydrocarbon 0.6 / large 0.2 (by request)",
@@ -604,7 +750,7 @@ def main():
                    "budget_bytes": 60 << 30, "load": 0.7, "graphs": True,
                    "capacity": "cells/s of one implicit step of 65536 cells per mechanism, "
                                "combined by the mix's cell-weighted harmonic mean"}
-        for prec, name in ((_b.QSS_LU_FP32_IR, "fp32ir"), (_b.QSS_LU_FP64, "fp64")):
+        for prec, name in ((binding.QSS_LU_FP32_IR, "fp32ir"), (binding.QSS_LU_FP64, "fp64")):
             caps = {k: implicit_capacity(mechs[k], k, prec) for k in mechs}
             cap = 1.0 / sum(w / caps[k] for w, k in zip(weights, mechs))
             serving[name] = serve_bench(mechs, weights, prec, a.serve_seconds, cap)
@@ -614,16 +760,14 @@ def main():
         cpu = cpu_baseline(mech, workloads.STATES[key], a.cpu_seconds)
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mechanism and states)",
-            "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": a.steps * launches_per_step, "clocks": clk.summary(),
-            "implicit": implicit, "integration": integration, "serving": serving,
-            "jacobian_variants": variants,
-            "kernel": {"ptxas": {k: v for k, v in meta["kernels"].items() if k.startswith("qss_jac")},
-                       "defines": meta.get("defines", []),
-                       "ops_per_cell": meta["ops_jac"], "artefact": os.path.basename(art)}}
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded mechanism and states)", "config": cfg, "roofline": head["roofline"],
+            "cpu_baseline": cpu, "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"], "by_config": by_config, "implicit": implicit,
+            "integration": integration, "serving": serving, "jacobian_variants": variants,
+            "kernel": head["kernel"]}
     print(json.dumps(line), flush=True)
 
 

@@ -187,8 +187,12 @@ int qss_jacobian_host(qss_mech_t mech, int64_t ncells, const double* rho, const 
  * 1 / (rtol |phi_i| + atol_i) is <= 1.  precision = QSS_LU_FP64 factors the
  * matrix with partial pivoting in FP64; QSS_LU_FP32_IR factors it in FP32
  * and refines the solution with FP64 residuals until the correction is below
- * refine_tol relative (or max_refine sweeps); rates, equilibrium constants,
- * the QSS solve and the Newton residual stay FP64 in both forms.
+ * refine_tol relative (or max_refine sweeps); a cell whose FP32
+ * factorisation meets a zero or non-finite pivot, or whose refinement turns
+ * non-finite, is solved in FP64 for that iteration instead, so the mixed form
+ * reports QSS_CELL_SINGULAR only where the FP64 form would.  Rates,
+ * equilibrium constants, the QSS solve and the Newton residual stay FP64 in
+ * both forms.
  * T [ld] and Y [N][ld] are updated in place (device arrays); dt is a device
  * array [ld] (dt_stride = 1) or a single device value (dt_stride = 0).
  * iters and cell_status (device int32 [ld]) may be NULL.
@@ -298,6 +302,7 @@ typedef struct {
   uint64_t graph_batches;    /* batches run by replaying a captured graph */
   uint64_t graphs_captured;  /* graphs captured (a re-capture after release counts again) */
   uint64_t graphs_cached;    /* graphs held now */
+  uint64_t in_flight_peak;   /* most batches on the device at once (streams in use) */
 } qss_serve_stats_t;
 
 int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts, qss_server_t* out);

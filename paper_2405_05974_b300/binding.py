@@ -64,7 +64,8 @@ class ServeStats(ctypes.Structure):
                                                  "bytes_in_use", "bytes_peak")] + \
                [(nm, ctypes.c_double) for nm in ("p50_latency_us", "p99_latency_us",
                                                  "mean_latency_us", "cells_per_s")] + \
-               [(nm, ctypes.c_uint64) for nm in ("graph_batches", "graphs_captured", "graphs_cached")]
+               [(nm, ctypes.c_uint64) for nm in ("graph_batches", "graphs_captured", "graphs_cached",
+                                                 "in_flight_peak")]
 
     def as_dict(self):
         return {nm: getattr(self, nm) for nm, _ in self._fields_}

@@ -28,9 +28,11 @@ struct NewtonOptsDev {   // layout of QssNewtonOpts in qss_newton.cuh
 namespace qss {
 // The handle's Newton scratch for a call enqueued on `st`: at least `bytes`,
 // reused only after the previous call's work (on any stream) is done with it
-// -- st waits for the event the previous call recorded (the caller records
-// it again with scratch_release once its work is enqueued).
-int scratch_acquire(qss_mech_s* m, size_t bytes, CUstream st) {
+// -- st waits for the event the previous call recorded (the caller records it
+// again with scratch_release once its work is enqueued).  One allocation
+// attempt: QSS_ERR_OOM when the device cannot hold `bytes` (nothing is
+// enqueued then, and the handle holds no scratch).
+int scratch_acquire_bytes(qss_mech_s* m, size_t bytes, CUstream st) {
   if (m->newton_scratch_bytes < bytes) {
     if (m->newton_done) CU_TRY(drv().cuEventSynchronize(m->newton_done));
     if (m->newton_scratch) {
@@ -38,13 +40,28 @@ int scratch_acquire(qss_mech_s* m, size_t bytes, CUstream st) {
       m->newton_scratch = 0;
       m->newton_scratch_bytes = 0;
     }
-    CUresult r = drv().cuMemAlloc(&m->newton_scratch, bytes);
-    if (r != CUDA_SUCCESS) return fail(QSS_ERR_OOM, "cannot allocate the Newton scratch");
+    if (drv().cuMemAlloc(&m->newton_scratch, bytes) != CUDA_SUCCESS) {
+      m->newton_scratch = 0;
+      return fail(QSS_ERR_OOM, "cannot allocate the Newton scratch");
+    }
     m->newton_scratch_bytes = bytes;
   }
   if (!m->newton_done) CU_TRY(drv().cuEventCreate(&m->newton_done, CU_EVENT_DISABLE_TIMING));
   else CU_TRY(drv().cuStreamWaitEvent(st, m->newton_done, 0));
   return QSS_OK;
+}
+
+// The same for `*cells` cells of `per_cell` bytes (plus 256 bytes of
+// alignment slack).  When the device cannot hold that much, the request is
+// halved (whole waves, at least 32 cells) until an allocation succeeds;
+// *cells is then the chunk the call runs in.
+int scratch_acquire(qss_mech_s* m, size_t per_cell, int64_t* cells, CUstream st) {
+  for (;;) {
+    int rc = scratch_acquire_bytes(m, per_cell * (size_t)*cells + 256, st);
+    if (rc != QSS_ERR_OOM) return rc;
+    if (*cells <= 32) return fail(QSS_ERR_OOM, "cannot allocate the Newton scratch for 32 cells");
+    *cells = chunk_cells(m, *cells / 2);
+  }
 }
 
 int scratch_release(qss_mech_s* m, CUstream st) {
@@ -152,9 +169,9 @@ extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   const size_t per_cell = newton_scratch_per_cell(m, precision);
-  const int64_t want = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per_cell)),
-                                         (ncells + 31) / 32 * 32);
-  rc = scratch_acquire(m, per_cell * (size_t)want + 256, (CUstream)stream);
+  int64_t cells = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per_cell)),
+                                    (ncells + 31) / 32 * 32);
+  rc = scratch_acquire(m, per_cell, &cells, (CUstream)stream);
   if (rc) return rc;
   rc = implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,
                        (CUstream)stream, m->newton_scratch, m->newton_scratch_bytes);

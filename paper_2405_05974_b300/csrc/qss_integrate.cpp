@@ -63,21 +63,33 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   CUstream st = (CUstream)stream;
   const int N = m->N, n = N + 1;
   const size_t per = integ_per_cell(m, precision);
-  const int64_t S = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per)), (ncells + 31) / 32 * 32);
-  // layout (offsets in bytes, every array 256-byte aligned)
+  int64_t S = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per)), (ncells + 31) / 32 * 32);
+  // layout (offsets in bytes, every array 256-byte aligned) for a chunk of S
+  // cells; S is halved (whole waves, at least 32 cells) while the device
+  // cannot hold the scratch
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t D = al((size_t)S * sizeof(double)), I = al((size_t)S * sizeof(int));
-  size_t off = 0;
+  size_t D, I, off;
   auto take = [&](size_t b) { size_t o0 = off; off += b; return o0; };
-  const size_t oTT = take(D), oHH = take(D), oDT = take(D), oIS = take(I), oNS = take(I);
-  const size_t oLA = take(I), oLB = take(I), oCNT = take(256);
-  const size_t oRb = take(D), oTb = take(D), oDtb = take(D), oYb = take((size_t)N * D);
-  const size_t oBst = take(I), oF0 = take((size_t)n * D), oF1 = take((size_t)n * D);
-  const size_t oHP = take(D), oPP = take((size_t)n * D), oFP = take((size_t)n * D), oPC = take((size_t)n * D);
-  const size_t oNewton = take(0);
+  size_t oTT, oHH, oDT, oIS, oNS, oLA, oLB, oCNT, oRb, oTb, oDtb, oYb, oBst, oF0, oF1, oHP, oPP, oFP, oPC,
+      oNewton;
+  for (;;) {
+    D = al((size_t)S * sizeof(double));
+    I = al((size_t)S * sizeof(int));
+    off = 0;
+    oTT = take(D); oHH = take(D); oDT = take(D); oIS = take(I); oNS = take(I);
+    oLA = take(I); oLB = take(I); oCNT = take(256);
+    oRb = take(D); oTb = take(D); oDtb = take(D); oYb = take((size_t)N * D);
+    oBst = take(I); oF0 = take((size_t)n * D); oF1 = take((size_t)n * D);
+    oHP = take(D); oPP = take((size_t)n * D); oFP = take((size_t)n * D); oPC = take((size_t)n * D);
+    oNewton = take(0);
+    const size_t total = off + newton_scratch_per_cell(m, precision) * (size_t)S + 256;
+    rc = scratch_acquire_bytes(m, total, st);
+    if (rc != QSS_ERR_OOM) break;
+    if (S <= 32) return fail(QSS_ERR_OOM, "cannot allocate the integration scratch for 32 cells");
+    S = chunk_cells(m, S / 2);
+  }
+  if (rc) return rc;
   const size_t newton_bytes = newton_scratch_per_cell(m, precision) * (size_t)S + 256;
-  const size_t total = off + newton_bytes;
-  if ((rc = scratch_acquire(m, total, st))) return rc;
   char* base = (char*)m->newton_scratch;
   double* TT = (double*)(base + oTT);
   double* HH = (double*)(base + oHH);

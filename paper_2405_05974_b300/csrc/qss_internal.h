@@ -31,7 +31,7 @@ struct qss_mech_s {
   CUdeviceptr fr_scratch = 0;
   int64_t fr_cells = 0;
   size_t fr_budget = size_t(4) << 30;   // bytes of that buffer (qss_mech_set_frontier_bytes;
-                                        // set at load to 1/16 of the device's memory)
+                                        // set at load like newton_budget)
   CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
   // stored Jacobian entries per cell and their pattern (CSR; dense = all)
@@ -50,8 +50,9 @@ struct qss_mech_s {
   size_t newton_scratch_bytes = 0;
   CUevent newton_done = nullptr;   // recorded after each call's last use of the scratch
   // size limit of that scratch (qss_mech_set_newton_bytes; default 1/16 of
-  // the device's memory, at least 1 GiB): larger chunks mean fewer Newton
-  // tails, the iterations in which only a few slow cells are left
+  // the device's memory, at most a quarter of the memory free at load):
+  // larger chunks mean fewer Newton tails, the iterations in which only a
+  // few slow cells are left
   size_t newton_budget = size_t(4) << 30;
 };
 
@@ -80,7 +81,8 @@ inline size_t frontier_bytes_per_cell(const qss_mech_s* m) {
   return m->jac_parts >= 2 ? (size_t)m->frontier * sizeof(double) : 0;
 }
 // the handle's Newton scratch, ordered across streams (qss_implicit.cpp)
-int scratch_acquire(qss_mech_s* m, size_t bytes, CUstream st);
+int scratch_acquire_bytes(qss_mech_s* m, size_t bytes, CUstream st);
+int scratch_acquire(qss_mech_s* m, size_t per_cell, int64_t* cells, CUstream st);
 int scratch_release(qss_mech_s* m, CUstream st);
 // implicit step (qss_implicit.cpp)
 size_t newton_scratch_per_cell(const qss_mech_s* m, int precision);

@@ -28,7 +28,9 @@
 //                  the solution refined with FP64 residuals g - M x (M from
 //                  the FP64 copy in shared memory, staged once per cell)
 //                  until the correction is below refine_tol relative, stops
-//                  shrinking, or after max_refine sweeps.
+//                  shrinking, or after max_refine sweeps; a zero or
+//                  non-finite FP32 pivot (or a non-finite correction) sends
+//                  that cell's solve to the FP64 elimination instead.
 // Rates, equilibrium constants, the QSS solve, J, M and the Newton residual
 // are FP64 in both forms.
 //
@@ -214,7 +216,9 @@ __device__ __forceinline__ bool qss_smem_solve_fp64(double* __restrict__ Ms, con
 // to shared memory (LU[r][k]: multiplier of row r at step k before its pivot
 // step, its U row from there on), and the substitutions are loops over them.
 // Scaling: rows, then columns, by powers of two (exact), so that FP32 holds
-// every entry near 1.  Returns false on a zero pivot.
+// every entry near 1.  Returns false on a zero or non-finite FP32 pivot, or
+// when a refinement sweep produces a non-finite correction (the caller then
+// solves the cell in FP64).
 __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, float* __restrict__ LU,
                                                  int* __restrict__ se, int* __restrict__ piv,
                                                  float* __restrict__ pinv, double* __restrict__ sx,
@@ -291,7 +295,7 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
       const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
       if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
     }
-    if (best <= 0) return false;
+    if (best <= 0 || best >= 0x7f800000) return false;   // zero, inf or NaN pivot
     const int pl = brow & 31, ps = brow >> 5;
     float p[QSS_NN];
 #pragma unroll
@@ -384,18 +388,21 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
         if (live[sl] && ord[sl] < k) z[sl] = fmaf(-LU[(lane + 32 * sl) * QSS_MSTRIDE + k], xk, z[sl]);
     }
     double dmax = 0.0, xmax = 0.0;
+    bool dfin = true;
     __syncwarp();
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int j = lane + 32 * sl;
       if (j < QSS_NN) {
         const double dd = (double)d[sl] * csr[sl] * qss_pow2(es);
+        dfin = dfin && qss_finite(dd);
         xo[sl] += dd;
         sx[j] = xo[sl];
         dmax = fmax(dmax, fabs(dd));
         xmax = fmax(xmax, fabs(xo[sl]));
       }
     }
+    if (!__all_sync(0xffffffffu, dfin)) return false;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
@@ -510,6 +517,25 @@ __device__ __forceinline__ void qss_newton_update(
     if constexpr (FP32IR) {
       solved = qss_solve_fp32ir(Ms, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
                                 sh_x[w], gr, xo, lane, o);
+      if (!solved) {
+        // the FP32 factorisation met a zero or non-finite pivot (or the
+        // refinement diverged): solve this cell's system in FP64 instead,
+        // from the intact FP64 copy of M, so that the mixed form reports no
+        // status the FP64 form would not
+        __syncwarp();
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+          const int r = lane + 32 * sl;
+          if (r < QSS_NN) Ms[r * QSS_MSTRIDE + QSS_NN] = gr[sl];
+        }
+        __syncwarp();
+        solved = qss_smem_solve_fp64(Ms, lane);
+#pragma unroll
+        for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+          const int r = lane + 32 * sl;
+          xo[sl] = r < QSS_NN ? Ms[r * QSS_MSTRIDE + QSS_NN] : 0.0;
+        }
+      }
     } else {
       solved = qss_smem_solve_fp64(Ms, lane);
 #pragma unroll

@@ -31,23 +31,26 @@ CUdeviceptr g_addr[kMaxDevices] = {};   // device address of the array, per devi
 
 // Once per device, with that device current: the array's device address.  In
 // host code `qss_noalloc_scratch` names a host-side stand-in, not device
-// memory, so it is never passed to a kernel directly.
-int scratch_address(int device, CUdeviceptr* out) {
-  if (device < 0 || device >= kMaxDevices) return fail(QSS_ERR_INVALID_ARG, "device ordinal out of range");
+// memory, so it is never passed to a kernel directly.  The handle's context
+// (the primary context of its device, which the CUDA runtime shares) is made
+// current for the lookup, so no other device's context is created; a context
+// that was current before is put back.
+int scratch_address(qss_mech_s* m, CUdeviceptr* out) {
+  if (m->device < 0 || m->device >= kMaxDevices) return fail(QSS_ERR_INVALID_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[device]) {
-    int prev = -1;
-    cudaError_t e = cudaGetDevice(&prev);
-    if (e == cudaSuccess) e = cudaSetDevice(device);
+  if (!g_addr[m->device]) {
+    CUcontext prev = nullptr;
+    if (drv().cuCtxGetCurrent(&prev) != CUDA_SUCCESS) prev = nullptr;
+    CU_TRY(drv().cuCtxSetCurrent(m->ctx));
     void* p = nullptr;
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, qss_noalloc_scratch);
-    if (prev >= 0) cudaSetDevice(prev);
+    const cudaError_t e = cudaGetSymbolAddress(&p, qss_noalloc_scratch);
+    if (prev && prev != m->ctx) drv().cuCtxSetCurrent(prev);
     if (e != cudaSuccess || !p)
       return fail(QSS_ERR_CUDA, std::string("cudaGetSymbolAddress(qss_noalloc_scratch): ") +
                                     cudaGetErrorString(e));
-    g_addr[device] = (CUdeviceptr)p;
+    g_addr[m->device] = (CUdeviceptr)p;
   }
-  *out = g_addr[device];
+  *out = g_addr[m->device];
   return QSS_OK;
 }
 }  // namespace
@@ -65,7 +68,7 @@ extern "C" int qss_implicit_step_noalloc(qss_mech_t m, int64_t ncells, int64_t l
                                     std::to_string(warp_chunk) + " bytes, the array holds " +
                                     std::to_string(QSS_NOALLOC_SCRATCH_BYTES));
   CUdeviceptr scratch = 0;
-  if ((rc = scratch_address(m->device, &scratch))) return rc;
+  if ((rc = scratch_address(m, &scratch))) return rc;
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
   return implicit_launch(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, o, iters, cell_status,
                          (CUstream)stream, scratch, QSS_NOALLOC_SCRATCH_BYTES);

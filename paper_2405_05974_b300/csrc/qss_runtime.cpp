@@ -240,9 +240,13 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
         tpb > 0)
       m->upd_threads[i] = tpb;
   }
+  // default scratch limits: 1/16 of the device's memory, but no more than a
+  // quarter of what is free at load time (on a shared device, or when the
+  // caller already holds most of the memory); allocation failures later halve
+  // the chunk instead of failing the call
   size_t free_b = 0, total_b = 0;
   if (drv().cuMemGetInfo(&free_b, &total_b) == CUDA_SUCCESS && total_b > 0) {
-    m->newton_budget = std::max<size_t>(size_t(1) << 30, total_b / 16);
+    m->newton_budget = std::max<size_t>(size_t(64) << 20, std::min(total_b / 16, free_b / 4));
     m->fr_budget = m->newton_budget;
   }
   // cells of one full wave of the (first) Jacobian kernel: chunked paths use
@@ -334,10 +338,20 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
   if (m->fr_cells < want) {
     if (m->fr_done) CU_TRY(drv().cuEventSynchronize(m->fr_done));
     if (m->fr_scratch) { drv().cuMemFree(m->fr_scratch); m->fr_scratch = 0; m->fr_cells = 0; }
-    if (drv().cuMemAlloc(&m->fr_scratch, per * (size_t)want) != CUDA_SUCCESS)
-      return fail(QSS_ERR_OOM, "cannot allocate the Jacobian frontier scratch");
+    // the device may hold less than the limit: halve the chunk (down to 32
+    // cells) until the buffer fits, and lower the limit to what fitted (so
+    // that qss_jacobian_launches stays exact and later calls do not retry)
+    bool halved = false;
+    while (drv().cuMemAlloc(&m->fr_scratch, per * (size_t)want) != CUDA_SUCCESS) {
+      m->fr_scratch = 0;
+      if (want <= 32) return fail(QSS_ERR_OOM, "cannot allocate the Jacobian frontier scratch for 32 cells");
+      want = chunk_cells(m, want / 2);
+      halved = true;
+    }
+    if (halved) m->fr_budget = per * (size_t)want;
     m->fr_cells = want;
   }
+  want = std::min(want, m->fr_cells);
   if (!m->fr_done) CU_TRY(drv().cuEventCreate(&m->fr_done, CU_EVENT_DISABLE_TIMING));
   else CU_TRY(drv().cuStreamWaitEvent(s, m->fr_done, 0));
   double* fr = (double*)m->fr_scratch;

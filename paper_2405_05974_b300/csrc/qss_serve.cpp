@@ -158,6 +158,7 @@ struct qss_server_s {
   bool graphs_on = true;
   std::map<GraphKey, GraphEntry> graphs;
   uint64_t use_clock = 0, graph_batches = 0, graphs_captured = 0;
+  uint64_t in_flight_peak = 0;
 };
 
 namespace {
@@ -283,7 +284,14 @@ bool arena_alloc(qss_server_s* s, size_t bytes, size_t* off) {
 
 // The cached graph for a batch of `cells` cells, captured on `st` if needed;
 // null when graphs are off, the bucket's graph is busy, or memory is short.
-GraphEntry* graph_for(qss_server_s* s, qss_mech_s* m, int prec, int64_t cells, CUstream st) {
+// Called by the scheduler with s->mu held (lk); a capture (max_iter x 2
+// launches recorded, then instantiated) runs with the lock released, so that
+// submit, wait and stats do not block behind it.  The entry is reserved busy
+// with its arena region before the lock is dropped: nothing else uses, evicts
+// or captures it meanwhile (only the scheduler thread touches the graph cache
+// and the arena, and `st` is the free slot's stream, used by no one else).
+GraphEntry* graph_for(qss_server_s* s, qss_mech_s* m, int prec, int64_t cells, CUstream st,
+                      std::unique_lock<std::mutex>& lk) {
   if (!s->graphs_on) return nullptr;
   int64_t bucket = 256;
   while (bucket < cells) bucket *= 2;
@@ -301,27 +309,36 @@ GraphEntry* graph_for(qss_server_s* s, qss_mech_s* m, int prec, int64_t cells, C
   if (!arena_alloc(s, bytes, &off)) return nullptr;
   Region g = region_of(s, m, off, bytes, bucket, prec, true);
   const size_t ldb = (size_t)((bucket + 31) / 32 * 32);
+  {
+    GraphEntry& e = s->graphs[key];   // placeholder: busy, no executable yet
+    e.exec = nullptr;
+    e.off = off;
+    e.bytes = bytes;
+    e.bucket = bucket;
+    e.busy = true;
+    e.last_use = ++s->use_clock;
+  }
+  const qss_newton_opts newton = s->newton;
+  lk.unlock();
   CUgraph graph = nullptr;
   CUgraphExec exec = nullptr;
   bool ok = drv().cuStreamBeginCapture(st, CU_STREAM_CAPTURE_MODE_RELAXED) == CUDA_SUCCESS;
-  int rc = ok ? implicit_launch(m, bucket, (int64_t)ldb, g.dt, 1, g.rho, g.T, g.Y, prec, s->newton,
+  int rc = ok ? implicit_launch(m, bucket, (int64_t)ldb, g.dt, 1, g.rho, g.T, g.Y, prec, newton,
                                 g.it, g.st, st, g.scratch, g.scratch_bytes, g.ncap)
               : QSS_ERR_CUDA;
   if (ok) ok = drv().cuStreamEndCapture(st, &graph) == CUDA_SUCCESS && rc == QSS_OK && graph;
   if (ok) ok = drv().cuGraphInstantiate(&exec, graph, 0) == CUDA_SUCCESS;
   if (graph) drv().cuGraphDestroy(graph);
+  lk.lock();
+  auto e = s->graphs.find(key);
   if (!ok) {
     s->arena->release(off, bytes);
+    s->graphs.erase(e);
     return nullptr;
   }
-  GraphEntry& e = s->graphs[key];
-  e.exec = exec;
-  e.off = off;
-  e.bytes = bytes;
-  e.bucket = bucket;
-  e.last_use = ++s->use_clock;
+  e->second.exec = exec;
   s->graphs_captured++;
-  return &e;
+  return &e->second;
 }
 
 void finish_batch(qss_server_s* s, Batch* b, int rc) {
@@ -389,7 +406,7 @@ void scheduler(qss_server_s* s) {
       // head request) until it fits, else wait for running batches
       size_t soff, need = 0;
       bool got = false;
-      b->graph = graph_for(s, head->mech, head->precision, b->cells, s->streams[free_slot]);
+      b->graph = graph_for(s, head->mech, head->precision, b->cells, s->streams[free_slot], lk);
       if (b->graph) {
         got = true;
         b->graph->busy = true;
@@ -415,6 +432,11 @@ void scheduler(qss_server_s* s) {
       }
       s->batches++;
       s->bytes_peak = std::max(s->bytes_peak, s->arena->used());
+      {
+        uint64_t busy = 0;
+        for (Batch* x : s->slot) busy += x ? 1 : 0;
+        s->in_flight_peak = std::max(s->in_flight_peak, busy);
+      }
       int rc = launch_batch(s, b);
       if (rc) {
         s->fatal = rc;
@@ -547,6 +569,7 @@ int qss_serve_stats(qss_server_t s, qss_serve_stats_t* out) {
   out->graph_batches = s->graph_batches;
   out->graphs_captured = s->graphs_captured;
   out->graphs_cached = s->graphs.size();
+  out->in_flight_peak = s->in_flight_peak;
   if (!s->lat_us.empty()) {
     std::vector<double> v = s->lat_us;
     std::sort(v.begin(), v.end());

@@ -52,6 +52,12 @@ BUILD_OPTIONS = {"large": {"jac_parts": 4}}
 def build_options(key: str) -> dict:
     return dict(BUILD_OPTIONS.get(key, {}))
 IMPLICIT_DT = 1.0e-6
+# A second implicit-step size at which plain Newton from the initial state
+# converges in >= 95 % of the hydrocarbon cells (oracle: 96.6 % at 1e-11 s,
+# 72 % at 1e-8 s, 32 % at 1e-6 s): the synthetic Dirichlet compositions put
+# radicals at mol/m^3 levels, so the fastest chemical time scales are ~1e-11 s
+# and a larger step must jump most cells close to equilibrium.
+IMPLICIT_DT_CONVERGING = 1.0e-11
 
 _cache = {}
 

@@ -54,20 +54,26 @@ def close(pa, pb, rel, N):
     return np.abs(pa - pb) <= rel * np.abs(pb) + 10 * atol
 
 
-@pytest.mark.parametrize("key,ncells,dt", [("tiny", 4096, workloads.IMPLICIT_DT),
-                                           ("hydrocarbon", 1024, workloads.IMPLICIT_DT),
-                                           ("large", 512, 1e-9)])
-def test_implicit_step_parity(key, ncells, dt):
-    """(The large mechanism at a shorter step: at 1e-6 s few of its synthetic
-    cells converge from phi0.)"""
+@pytest.mark.parametrize("key,ncells,dt,min_conv", [("tiny", 4096, workloads.IMPLICIT_DT, 0.25),
+                                                    ("hydrocarbon", 1024, workloads.IMPLICIT_DT, 0.25),
+                                                    ("hydrocarbon", 2048, workloads.IMPLICIT_DT_CONVERGING, 0.95),
+                                                    ("large", 512, 1e-9, 0.25),
+                                                    ("large", 1024, 1e-12, 0.95)])
+def test_implicit_step_parity(key, ncells, dt, min_conv):
+    """Converged cells against the oracle's step.  At the configured step
+    (1e-6 s; the large mechanism at 1e-9 s) plain Newton from phi0 converges
+    in only part of the synthetic cells; at 1e-11 s (hydrocarbon) and 1e-12 s
+    (large) it converges in >= 95 % of them, so the comparison covers nearly
+    every cell."""
     m, gm, om = mech(key)
-    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    st_cfg = workloads.STATES["implicit"] if key == "hydrocarbon" else workloads.STATES[key]
+    rho, T, Y = mechgen.generate_states(m, st_cfg, ncells)
     To, Yo, ito, sto = om.be_step(rho, T, Y, dt, max_iter=20)
     T64, Y64, it64, st64 = gpu_step(gm, rho, T, Y, dt, binding.QSS_LU_FP64)
     T32, Y32, it32, st32 = gpu_step(gm, rho, T, Y, dt, binding.QSS_LU_FP32_IR)
     N = gm.N
     both = (sto == 0) & (st64 == 0)
-    assert both.sum() >= 0.25 * ncells, (np.bincount(sto), np.bincount(st64))
+    assert both.sum() >= min_conv * ncells, (np.bincount(sto), np.bincount(st64))
     # the same cells converge (Newton paths only differ by rounding)
     agree = np.mean((sto == 0) == (st64 == 0))
     assert agree >= 0.97, agree
@@ -173,3 +179,31 @@ def test_empty_and_bad_arguments():
                                0, None, None, None, None) == -1
     assert L.qss_implicit_step(gm.h, 8, 8, x.data_ptr(), 0, x.data_ptr(), x.data_ptr(), Y.data_ptr(),
                                7, None, None, None, None) == -1
+
+
+def test_fp32ir_reports_no_status_fp64_does_not():
+    """The mixed form falls back to the FP64 solve for a cell whose FP32
+    factorisation fails, so it never ends a cell SINGULAR where the FP64 form
+    does not, and its statuses follow the FP64 form's."""
+    m, gm, om = mech("hydrocarbon")
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["implicit"], 8192)
+    _, _, _, st64 = gpu_step(gm, rho, T, Y, workloads.IMPLICIT_DT, binding.QSS_LU_FP64)
+    _, _, _, st32 = gpu_step(gm, rho, T, Y, workloads.IMPLICIT_DT, binding.QSS_LU_FP32_IR)
+    assert not np.any((st32 == 3) & (st64 != 3)), np.bincount(st32, minlength=4)
+    assert np.mean(st32 == st64) >= 0.97, (np.bincount(st64, minlength=4), np.bincount(st32, minlength=4))
+
+
+def test_small_newton_scratch_limit_same_results():
+    """A Newton scratch limit of 2 MB (the 3000-cell batch then runs in chunks
+    of 160 cells instead of one) changes nothing in the results."""
+    m, gm, om = mech("hydrocarbon")
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["implicit"], 3000)
+    ref = gpu_step(gm, rho, T, Y, 1e-8, binding.QSS_LU_FP64)
+    try:
+        gm.set_newton_bytes(2 << 20)
+        got = gpu_step(gm, rho, T, Y, 1e-8, binding.QSS_LU_FP64)
+    finally:
+        gm.set_newton_bytes(4 << 30)
+    assert np.array_equal(got[3], ref[3]) and np.array_equal(got[2], ref[2])
+    fin = ref[3] != 2
+    assert np.array_equal(got[0][fin], ref[0][fin]) and np.array_equal(got[1][:, fin], ref[1][:, fin])

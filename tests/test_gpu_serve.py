@@ -87,6 +87,47 @@ def test_same_result_alone_and_in_the_mix(prec):
         assert torch.equal(got_st, ref_st)
 
 
+@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
+def test_same_result_with_overlapping_batches(prec):
+    """Four streams: batches of three mechanisms run side by side on the
+    device (the server reports several in flight at once) while the probe is
+    served once early and once in the middle of the burst; both copies equal
+    the direct call bit for bit."""
+    _, tiny = mech("tiny")
+    _, hc = mech("hydrocarbon")
+    _, lg = mech("large")
+    probe = host_state("hydrocarbon", 1500, 31)
+    dt = 1e-8
+    ref_T, ref_Y, ref_st = direct("hydrocarbon", clone(probe), dt, prec)
+    srv = binding.Server(0, budget_bytes=8 << 30, n_streams=4, max_batch_cells=1 << 14)
+    try:
+        keep, ids = [], []
+        first = clone(probe)
+        st_first = torch.empty(1500, dtype=torch.int32).pin_memory()
+        ids.append(srv.submit(hc, *first, dt, prec, status=st_first))
+        for i in range(12):
+            for key, gm, n, dti in (("large", lg, 700 + 31 * i, 1e-9), ("tiny", tiny, 4000 + 97 * i, 1e-6),
+                                    ("hydrocarbon", hc, 3000 + 53 * i, 1e-7)):
+                s = host_state(key, n, 300 + 10 * i + len(keep))
+                keep.append(s)
+                ids.append(srv.submit(gm, *s, dti, prec))
+            if i == 6:
+                mid = clone(probe)
+                st_mid = torch.empty(1500, dtype=torch.int32).pin_memory()
+                ids.append(srv.submit(hc, *mid, dt, prec, status=st_mid))
+        for r in ids:
+            assert srv.wait(r) == 0
+        st = srv.stats()
+        assert st["completed"] == len(ids) and st["queued"] == 0
+        assert st["in_flight_peak"] >= 2, st
+    finally:
+        srv.close()
+    for got_T, got_Y, got_st in ((first[1], first[2], st_first), (mid[1], mid[2], st_mid)):
+        assert np.array_equal(got_T.numpy(), ref_T.numpy(), equal_nan=True)
+        assert np.array_equal(got_Y.numpy(), ref_Y.numpy(), equal_nan=True)
+        assert torch.equal(got_st, ref_st)
+
+
 def test_budget_admission_and_rejection():
     _, hc = mech("hydrocarbon")
     per_cell = 37 * 8 * 4 + 36 * 36 * 8 + 3 * 36 * 8   # io + FP64 scratch, approx

@@ -89,3 +89,25 @@ def test_noalloc_chunks_and_arguments():
                                      ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(Yz.data_ptr()), 0, None,
                                      None, None, None)
     assert rc == -1
+
+
+def test_noalloc_partitioned_mechanism_in_chunks():
+    """The large mechanism's partitioned Jacobian keeps its frontier inside the
+    same fixed array (after the Newton counters): about 61 KB per cell, so
+    3000 cells run in three chunks of 1088 cells, a per-cell size that does
+    not divide the array evenly.  Status, iterations and the new state match
+    the regular entry point's."""
+    L = binding.lib()
+    L.qss_implicit_step_noalloc.argtypes = L.qss_implicit_step.argtypes
+    m = workloads.mechanism("large")
+    gm = binding.Mechanism(build_mechanism(m, **workloads.build_options("large")), 0)
+    ncells = 3000
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES["large"], ncells)
+    r = torch.from_numpy(rho).cuda()
+    dt = torch.full((1,), 1e-9, dtype=torch.float64, device="cuda")
+    for prec in (binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR):
+        ref = _call(L.qss_implicit_step, gm, r, T, Y, dt, prec, ncells, ncells)
+        got = _call(L.qss_implicit_step_noalloc, gm, r, T, Y, dt, prec, ncells, ncells)
+        assert (ref[3] == 0).mean() > 0.5
+        assert np.array_equal(got[3], ref[3]) and np.array_equal(got[2], ref[2])
+        assert _close(np.vstack([got[1], got[0][None]]), np.vstack([ref[1], ref[0][None]]), gm.N).all()
