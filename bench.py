@@ -294,7 +294,7 @@ def implicit_bench(gm, mech, ncells, dt):
                      "newton_iters_max": int(itn[conv].max()) if conv.any() else None}
     a, b = out["fp64"], out["fp32ir"]
     both = (a[2] == 0) & (b[2] == 0)
-    rel = _rel_err(gm, _phi(gm, rho, b[1], b[0]), _phi(gm, rho, a[1], a[0]))[both]
+    rel = _rel_err(gm, _phi(gm, rho, b[0], b[1]), _phi(gm, rho, a[0], a[1]))[both]
     differ = a[2] != b[2]
     res["fp32ir_vs_fp64"] = {"cells_converged_both": int(both.sum()),
                              "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
@@ -338,11 +338,11 @@ def implicit_cpu_baseline(gm, mech, dt, data, seconds):
     To = np.concatenate([r[0] for r in res])
     Yo = np.concatenate([r[1] for r in res], axis=1)
     sto = np.concatenate([r[2] for r in res])
-    po = _phi(gm, rho[idx], Yo, To)
+    po = _phi(gm, rho[idx], To, Yo)
     cmp = {}
     for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8)):
         Tg, Yg, stg = out[name]
-        pg = _phi(gm, rho[idx], Yg[:, idx], Tg[idx])
+        pg = _phi(gm, rho[idx], Tg[idx], Yg[:, idx])
         both = (sto == 0) & (stg[idx] == 0)
         rel = _rel_err(gm, pg, po)[both]
         cmp[name] = {"cells_compared": int(both.sum()),

@@ -125,6 +125,29 @@ def _write_index(root: str, fast: str, name: str):
         os.replace(tmp, os.path.join(root, "index.json"))
 
 
+def prune_artefacts(keep, root: str = None) -> list:
+    """Remove the artefact directories under `root` that are not in `keep`
+    (paths returned by build_mechanism in this build) and their index
+    entries: a template or generator change leaves the previous artefacts
+    behind, and the tree would otherwise grow with every such change.
+    Returns the removed directory names."""
+    root = root or DEFAULT_ROOT
+    keep_names = {os.path.basename(os.path.normpath(k)) for k in keep}
+    removed = []
+    with _INDEX_LOCK:
+        idx = {k: v for k, v in _read_index(root).items() if v in keep_names}
+        tmp = os.path.join(root, "index.json.tmp%d" % os.getpid())
+        with open(tmp, "w") as f:
+            json.dump(idx, f, indent=0, sort_keys=True)
+        os.replace(tmp, os.path.join(root, "index.json"))
+        for d in sorted(os.listdir(root)):
+            p = os.path.join(root, d)
+            if os.path.isdir(p) and d not in keep_names:
+                shutil.rmtree(p, ignore_errors=True)
+                removed.append(d)
+    return removed
+
+
 def _complete(out: str) -> bool:
     return all(os.path.exists(os.path.join(out, f)) for f in ARTEFACT_FILES) and (
         os.path.exists(os.path.join(out, "jac.cubin")) or os.path.exists(os.path.join(out, "jac_prefix.cubin")))
