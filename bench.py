@@ -534,7 +534,7 @@ def _jac_cubin_digest(art, parts):
 
 
 def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=True, cpu_seconds=0.0,
-                   jac_parts=-1, jac_format="dense", flush_l2=False):
+                   jac_parts=-1, jac_format="dense", flush_l2=False, keep_sample=0):
     """Timed qss_jacobian steps (wdot + Tdot + J of `ncells` cells of workload
     `key`) through the C ABI, CUDA events on the launching stream, max over
     ranks; the roofline of the Jacobian kernel(s) against the FP64 peak
@@ -588,6 +588,15 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
         g1.record(stream)
         torch.cuda.synchronize()
     barrier(pg)
+    sample = None
+    if keep_sample:
+        # a seeded sample of the timed step's cells, with their outputs, for
+        # the oracle comparison of the CPU-baseline leg
+        idx = np.sort(np.random.default_rng(17).choice(ncells, size=min(keep_sample, ncells), replace=False))
+        ii = torch.from_numpy(idx).cuda()
+        sample = {"idx": idx, "rho": rho[idx], "T": T[idx], "Y": np.ascontiguousarray(Y[:, idx]),
+                  "jac": J.index_select(1, ii).cpu().numpy(), "wdot": w.index_select(1, ii).cpu().numpy(),
+                  "Tdot": td.index_select(0, ii).cpu().numpy(), "jac_format": jac_format}
     per = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms = max_over_ranks(pg, float(np.sum(per)) if flush is not None else g0.elapsed_time(g1))
     ms_step = total_ms / steps
@@ -651,7 +660,43 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
                       "ops_per_cell": meta["ops_jac"] if parts < 2 else
                       {"prefix": meta["ops_prefix"], "groups": meta["ops_groups"]},
                       "artefact": os.path.basename(art)}}
-    return out, (gm, r, t, y, mech)
+    return out, (gm, r, t, y, mech, sample)
+
+
+def parity_on_sample(mech, sample, seconds=20.0):
+    """The timed step's sampled cells against the oracle (CPU-baseline leg):
+    the per-entry gate |x - x_ref| <= 1e-10 |x_ref| + 1e-20 + 16 e_ref (e_ref
+    the oracle's running-error bound), how many entries needed the rounding
+    allowance, and for those the distance to the oracle's binary128 rerun."""
+    import oracle
+    om = oracle.OracleMech(mech)
+    t0 = time.perf_counter()
+    ref = om.eval(sample["rho"], sample["T"], sample["Y"])
+    eb = om.errbound(sample["rho"], sample["T"], sample["Y"])
+    out = {"cells": int(sample["idx"].size)}
+    for name in ("wdot", "Tdot", "jac"):
+        if name == "jac" and sample["jac_format"] != "dense":
+            continue
+        x, rf, b = sample[name], ref[name], eb[name]
+        err = np.abs(x - rf)
+        tol = 1e-10 * np.abs(rf) + 1e-20
+        ok = (err <= tol + 16 * b) & np.isfinite(x)
+        needed = ok & (err > tol)
+        d = {"entries": int(x.size), "fail": int((~ok).sum()), "needed_bound": int(needed.sum()),
+             "max_rel": float(np.max(err / np.maximum(np.abs(rf), 1e-300)))}
+        if needed.any() and time.perf_counter() - t0 < seconds:
+            cells = np.unique(np.nonzero(needed)[-1])
+            q = om.eval_q128(sample["rho"][cells], sample["T"][cells],
+                             np.ascontiguousarray(sample["Y"][:, cells]))[name]
+            sub = needed[..., cells]
+            xv, qv, bv = x[..., cells][sub], q[sub], b[..., cells][sub]
+            eq = np.abs(xv - qv)
+            d["needed_within_target_of_binary128"] = int((eq <= 1e-10 * np.abs(qv) + 1e-20).sum())
+            d["needed_within_gate_of_binary128"] = int((eq <= 1e-10 * np.abs(qv) + 1e-20 + 16 * bv).sum())
+            d["needed_max_rel_to_binary128"] = float(np.max(eq / np.maximum(np.abs(qv), 1e-300)))
+        out[name] = d
+    out["gate"] = "|x - x_ref| <= 1e-10 |x_ref| + 1e-20 + 16 e_ref (e_ref: the oracle's running-error bound)"
+    return out
 
 
 def main():
@@ -694,9 +739,10 @@ def main():
     from paper_2405_05974_b300 import binding
     from paper_2405_05974_b300.qssc.build import build_mechanism
     torch.cuda.set_device(local)
-    head, (gm, r, t, y, _) = jacobian_bench(key, ncells, a.steps, a.warmup, local, rank, world, pg,
-                                           do_e2e=not a.no_e2e, jac_parts=a.jac_parts,
-                                           jac_format=a.jac_format)
+    head, (gm, r, t, y, _, sample) = jacobian_bench(key, ncells, a.steps, a.warmup, local, rank, world, pg,
+                                                   do_e2e=not a.no_e2e, jac_parts=a.jac_parts,
+                                                   jac_format=a.jac_format,
+                                                   keep_sample=0 if (a.no_cpu or rank) else 512)
     if head["e2e"] is not None:
         # the host link on its own: one 2 GiB device -> pinned host copy
         hb = torch.empty(1 << 28, dtype=torch.float64).pin_memory()
@@ -717,7 +763,10 @@ def main():
         for k2 in ("tiny", "large"):
             c2, (g2, *_rest) = jacobian_bench(k2, workloads.NCELLS[k2], min(a.steps, 10), 3, local, rank, world,
                                               pg, do_e2e=not a.no_e2e,
-                                              cpu_seconds=0.0 if a.no_cpu else 4.0, flush_l2=(k2 == "tiny"))
+                                              cpu_seconds=0.0 if a.no_cpu else 4.0, flush_l2=(k2 == "tiny"),
+                                              keep_sample=0 if (a.no_cpu or rank) else 128)
+            if c2["cpu_baseline"] is not None and _rest[-1] is not None:
+                c2["cpu_baseline"]["gpu_vs_oracle_on_sample"] = parity_on_sample(workloads.mechanism(k2), _rest[-1])
             by_config[k2] = c2
             del g2, _rest
             torch.cuda.empty_cache()
@@ -758,6 +807,8 @@ def main():
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = cpu_baseline(mech, workloads.STATES[key], a.cpu_seconds)
+        if sample is not None:
+            cpu["gpu_vs_oracle_on_sample"] = parity_on_sample(mech, sample)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,

@@ -206,70 +206,117 @@ __device__ __forceinline__ bool qss_smem_solve_fp64(double* __restrict__ Ms, con
   return true;
 }
 
-// FP32 LU with FP64 iterative refinement of one cell's Newton system M x = g,
-// M (FP64) in shared memory, row r at Ms[r * QSS_MSTRIDE]; the warp's lanes
-// own rows lane + 32 slot.  Compact by design: an unrolled FP32 elimination
-// is fetch-bound (FP32 instructions retire faster than their code streams
-// in), so the factorisation runs as a loop over pivot steps with the live
-// rows in registers shifted left by one column per step (the pivot column is
-// always entry 0, and the shift folds into the elimination FMA); L and U go
-// to shared memory (LU[r][k]: multiplier of row r at step k before its pivot
-// step, its U row from there on), and the substitutions are loops over them.
-// Scaling: rows, then columns, by powers of two (exact), so that FP32 holds
-// every entry near 1.  Returns false on a zero or non-finite FP32 pivot, or
-// when a refinement sweep produces a non-finite correction (the caller then
-// solves the cell in FP64).
-__device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, float* __restrict__ LU,
-                                                 int* __restrict__ se, int* __restrict__ piv,
-                                                 float* __restrict__ pinv, double* __restrict__ sx,
-                                                 const double (&gr)[QSS_NSLOT], double (&xo)[QSS_NSLOT],
-                                                 const int lane, const QssNewtonOpts& o) {
+// Bit-level helpers of the FP32-IR solve: scalings by powers of two and the
+// conversions between the two precisions are exponent-field arithmetic on the
+// integer pipe (on this part every FP64-pipe instruction, even a conversion,
+// occupies the pipe for a whole warp).
+
+// float(x * 2^-s), mantissa truncated to 24 bits; 0 when x is zero or
+// subnormal or the result is below FLT_MIN.  The caller keeps the result
+// below 2^128.
+__device__ __forceinline__ float qss_scaled_float(double x, int s) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 - s;
+  const unsigned fb = (hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return (e < -126 || (hi & 0x7ff00000u) == 0) ? 0.0f : __uint_as_float(fb);
+}
+
+// (double)f * 2^k, exact; f normal or zero.  An exponent outside the normal
+// double range (never reached by the equilibrated systems) takes the FP64
+// multiply.
+__device__ __forceinline__ double qss_float_to_double_scaled(float f, int k) {
+  const unsigned b = __float_as_uint(f);
+  const int ef = (int)((b >> 23) & 0xffu);
+  const int ed = ef + 896 + k;
+  if (ef == 0) return 0.0;
+  if (ed < 1 || ed > 2046) return (double)f * qss_pow2(k);
+  const unsigned hi = (b & 0x80000000u) | ((unsigned)ed << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// 2^-s as a float (0 below FLT_MIN)
+__device__ __forceinline__ float qss_pow2f_neg(int s) {
+  return s > 126 ? 0.0f : __uint_as_float((unsigned)(127 - s) << 23);
+}
+
+// Rows of the last lane slot when it is at most half full (n = 33..48): the
+// FP64 residual of those rows is spread over the whole warp, QSS_R2 lanes
+// per column stride, instead of running on the few lanes that own them.
+#define QSS_RLAST (QSS_NN - 32 * (QSS_NSLOT - 1))
+#define QSS_SPREAD (QSS_NSLOT == 2 && QSS_RLAST <= 16)
+#define QSS_R2 (QSS_RLAST <= 1 ? 1 : QSS_RLAST <= 2 ? 2 : QSS_RLAST <= 4 ? 4 : QSS_RLAST <= 8 ? 8 : 16)
+#define QSS_G (32 / QSS_R2)
+
+// FP32 LU with FP64 iterative refinement of one cell's Newton system
+// (I - h J) x = g.  J (FP64) is in shared memory, row r at Js[r * QSS_MSTRIDE];
+// the warp's lanes own rows lane + 32 slot.
+//   Equilibration: row exponents er_r and column exponents ec_j (powers of
+//   two, from the exponent fields of h and J: every scaled entry of
+//   I - h J is below 4 in magnitude), so that FP32 holds every entry near 1.
+//   The scaled FP32 matrix is built in registers from J's bits: h J_rj 2^-s
+//   = hm * float(J_rj 2^(eh - s)) with h = hm 2^eh, plus 2^-s on the diagonal
+//   (integer and FP32 operations only).
+//   Factorisation: compact by design (an unrolled FP32 elimination is
+//   fetch-bound): a loop over pivot steps with the live rows in registers
+//   shifted left by one column per step (the pivot column is always entry 0,
+//   the shift folds into the elimination FMA); L and U go to shared memory
+//   (LU[r][k]: multiplier of row r at step k before its pivot step, its U row
+//   from there on), and the substitutions are loops over them.
+//   Refinement: r = g - x + h (J x) in FP64 (the rows of a thin last slot
+//   spread over the warp), scaled to FP32 by powers of two, corrected through
+//   the FP32 factors, until the correction is below refine_tol relative,
+//   stops shrinking, or after max_refine sweeps.
+// Returns false on a zero or non-finite FP32 pivot, or when a refinement
+// sweep produces a non-finite correction (the caller then solves the cell in
+// FP64).
+__device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Js, const double h,
+                                                 float* __restrict__ LU, int* __restrict__ se,
+                                                 int* __restrict__ piv, float* __restrict__ pinv,
+                                                 double* __restrict__ sx, const double (&gr)[QSS_NSLOT],
+                                                 double (&xo)[QSS_NSLOT], const int lane,
+                                                 const QssNewtonOpts& o) {
+  const int eh = qss_ilogb(h);
+  const float hm = qss_scaled_float(h, eh);   // h's mantissa, in [1, 2)
   int er[QSS_NSLOT];
   bool live[QSS_NSLOT];
-  // row exponents
+  // row exponents: er_r >= eh + e(J_rj) + 1 for every j, and >= 0 (the 1 on
+  // the diagonal)
 #pragma unroll
   for (int sl = 0; sl < QSS_NSLOT; ++sl) {
     const int r = lane + 32 * sl;
     live[sl] = r < QSS_NN;
-    long long mx = 0;
+    int mx = 0;
     if (live[sl]) {
 #pragma unroll 4
-      for (int j = 0; j < QSS_NN; ++j) mx = max(mx, qss_absbits(Ms[r * QSS_MSTRIDE + j]));
+      for (int j = 0; j < QSS_NN; ++j) {
+        const int ej = (__double2hiint(Js[r * QSS_MSTRIDE + j]) >> 20) & 0x7ff;
+        if (ej != 0) mx = max(mx, ej - 1023 + eh + 1);
+      }
+      se[r] = mx;
     }
-    const int e = qss_ilogb(__longlong_as_double(mx));
-    er[sl] = e < -1000 ? 0 : e;
-    if (live[sl]) se[r] = er[sl];
+    er[sl] = mx;
   }
   __syncwarp();
-  // column exponents (a lane per column)
-  double csr[QSS_NSLOT];
+  // column exponents (a lane per column): ec_j >= eh + e(J_rj) + 1 - er_r,
+  // and >= -er_j (the diagonal's 1)
+  int ec[QSS_NSLOT];
 #pragma unroll
   for (int sl = 0; sl < QSS_NSLOT; ++sl) {
     const int c = lane + 32 * sl;
-    csr[sl] = 1.0;
+    ec[sl] = 0;
     if (c < QSS_NN) {
-      int em = -1100;
+      int em = -se[c];
 #pragma unroll 4
       for (int r = 0; r < QSS_NN; ++r) {
-        const double v = Ms[r * QSS_MSTRIDE + c];
-        if (qss_absbits(v) != 0) em = max(em, qss_ilogb(v) - se[r]);
+        const int ej = (__double2hiint(Js[r * QSS_MSTRIDE + c]) >> 20) & 0x7ff;
+        if (ej != 0) em = max(em, ej - 1023 + eh + 1 - se[r]);
       }
-      const int ec = em < -1000 ? 0 : em;
-      se[QSS_NN + c] = ec;
-      csr[sl] = qss_pow2(-ec);
+      ec[sl] = em;
+      se[QSS_NN + c] = em;
     }
   }
   __syncwarp();
-  // scaled matrix in FP32: the NN x NN entries split evenly over the lanes
-  // (the FP64 multiply and the conversion run on the FP64 pipe; lane = row
-  // would leave most lanes of the second row slot idle), staged through LU,
-  // which the factorisation overwrites once every lane holds its rows
-#pragma unroll 4
-  for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
-    const int r = e / QSS_NN, j = e - r * QSS_NN;
-    LU[r * QSS_MSTRIDE + j] = (float)(Ms[r * QSS_MSTRIDE + j] * qss_pow2(-(se[r] + se[QSS_NN + j])));
-  }
-  __syncwarp();
+  // the scaled FP32 matrix, this lane's rows, in registers
   float A[QSS_NSLOT][QSS_NN];
   int ord[QSS_NSLOT];
 #pragma unroll
@@ -277,9 +324,16 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
     const int r = lane + 32 * sl;
     ord[sl] = -1;
 #pragma unroll
-    for (int j = 0; j < QSS_NN; ++j) A[sl][j] = live[sl] ? LU[r * QSS_MSTRIDE + j] : 0.0f;
+    for (int j = 0; j < QSS_NN; ++j) {
+      float v = 0.0f;
+      if (live[sl]) {
+        const int sc = er[sl] + se[QSS_NN + j];
+        const float jf = qss_scaled_float(Js[r * QSS_MSTRIDE + j], sc - eh);
+        v = fmaf(-hm, jf, r == j ? qss_pow2f_neg(sc) : 0.0f);
+      }
+      A[sl][j] = v;
+    }
   }
-  __syncwarp();
   // factorisation, one pivot step per iteration
 #pragma unroll 1
   for (int k = 0; k < QSS_NN; ++k) {
@@ -327,32 +381,65 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
     }
   }
   __syncwarp();
-  // refinement: r = g - M x in FP64, correction from the FP32 factors
+  // refinement: r = g - x + h (J x) in FP64, correction from the FP32 factors
 #pragma unroll
   for (int sl = 0; sl < QSS_NSLOT; ++sl) xo[sl] = 0.0;
   double prev = 1e308;
 #pragma unroll 1
   for (int sweep = 0; sweep <= o.max_refine; ++sweep) {
     double res[QSS_NSLOT];
-    long long rmx = 0;
+#pragma unroll
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) res[sl] = live[sl] ? gr[sl] : 0.0;
+    if (sweep > 0) {
+      double jx[QSS_NSLOT];
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+        jx[sl] = 0.0;
+        if (QSS_SPREAD && sl == QSS_NSLOT - 1) continue;
+        if (live[sl]) {
+          const int r = lane + 32 * sl;
+          double acc = 0.0;
+#pragma unroll 6
+          for (int j = 0; j < QSS_NN; ++j) acc = fma(Js[r * QSS_MSTRIDE + j], sx[j], acc);
+          jx[sl] = acc;
+        }
+      }
+      if (QSS_SPREAD) {
+        // rows 32.. of the thin last slot: lane l takes row 32 + (l mod R2)
+        // and columns l / R2 + G m; the partial sums of a row meet in its
+        // lane l < R by a butterfly over the lanes of equal l mod R2
+        const int rr = lane & (QSS_R2 - 1);
+        const int r = 32 + rr;
+        double acc = 0.0;
+        if (rr < QSS_RLAST) {
+#pragma unroll
+          for (int m = 0; m < (QSS_NN + QSS_G - 1) / QSS_G; ++m) {
+            const int j = lane / QSS_R2 + QSS_G * m;
+            if (j < QSS_NN) acc = fma(Js[r * QSS_MSTRIDE + j], sx[j], acc);
+          }
+        }
+#pragma unroll
+        for (int off = QSS_R2; off < 32; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        jx[QSS_NSLOT - 1] = acc;
+      }
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl)
+        if (live[sl]) res[sl] = fma(h, jx[sl], res[sl] - xo[sl]);
+    }
+    // scale to FP32: z_r = res_r 2^-(er_r + es), es the largest row exponent
+    int emax = -4000;
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const int r = lane + 32 * sl;
-      double acc = gr[sl];
-      if (sweep > 0 && live[sl]) {
-#pragma unroll 6
-        for (int j = 0; j < QSS_NN; ++j) acc = fma(-Ms[r * QSS_MSTRIDE + j], sx[j], acc);
-      }
-      res[sl] = live[sl] ? acc * qss_pow2(-er[sl]) : 0.0;
-      rmx = max(rmx, qss_absbits(res[sl]));
+      const int eb = (__double2hiint(res[sl]) >> 20) & 0x7ff;
+      if (live[sl] && eb != 0) emax = max(emax, eb - 1023 - er[sl]);
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) rmx = max(rmx, __shfl_xor_sync(0xffffffffu, rmx, off));
-    if (rmx == 0) break;
-    const int es = qss_ilogb(__longlong_as_double(rmx));
+    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    if (emax == -4000) break;   // zero residual: x is exact
+    const int es = emax;
     float z[QSS_NSLOT];
 #pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) z[sl] = (float)(res[sl] * qss_pow2(-es));
+    for (int sl = 0; sl < QSS_NSLOT; ++sl) z[sl] = live[sl] ? qss_scaled_float(res[sl], er[sl] + es) : 0.0f;
     // forward substitution
 #pragma unroll 1
     for (int k = 0; k < QSS_NN; ++k) {
@@ -387,28 +474,31 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Ms, 
       for (int sl = 0; sl < QSS_NSLOT; ++sl)
         if (live[sl] && ord[sl] < k) z[sl] = fmaf(-LU[(lane + 32 * sl) * QSS_MSTRIDE + k], xk, z[sl]);
     }
-    double dmax = 0.0, xmax = 0.0;
+    // correction dd_j = d_j 2^(es - ec_j), x += dd
+    long long dmx = 0, xmx = 0;
     bool dfin = true;
     __syncwarp();
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int j = lane + 32 * sl;
       if (j < QSS_NN) {
-        const double dd = (double)d[sl] * csr[sl] * qss_pow2(es);
-        dfin = dfin && qss_finite(dd);
+        dfin = dfin && (__float_as_uint(d[sl]) & 0x7f800000u) != 0x7f800000u;
+        const double dd = qss_float_to_double_scaled(d[sl], es - ec[sl]);
         xo[sl] += dd;
         sx[j] = xo[sl];
-        dmax = fmax(dmax, fabs(dd));
-        xmax = fmax(xmax, fabs(xo[sl]));
+        dmx = max(dmx, qss_absbits(dd));
+        xmx = max(xmx, qss_absbits(xo[sl]));
       }
     }
-    if (!__all_sync(0xffffffffu, dfin)) return false;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
-      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+      dmx = max(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+      xmx = max(xmx, __shfl_xor_sync(0xffffffffu, xmx, off));
     }
+    if (!__all_sync(0xffffffffu, dfin) || dmx >= 0x7ff0000000000000LL || xmx >= 0x7ff0000000000000LL)
+      return false;
     __syncwarp();
+    const double dmax = __longlong_as_double(dmx), xmax = __longlong_as_double(xmx);
     if (dmax <= o.refine_tol * xmax || dmax >= 0.5 * prev) break;
     prev = dmax;
   }
@@ -479,24 +569,45 @@ __device__ __forceinline__ void qss_newton_update(
       // form's 1 + m and m)
       for (int e = lane; e < QSS_NN * QSS_MSTRIDE; e += 32) {
         const int r = e / QSS_MSTRIDE;
-        Ms[e] = (e == r * (QSS_MSTRIDE + 1)) ? 1.0 : 0.0;
+        Ms[e] = (e == r * (QSS_MSTRIDE + 1) && !FP32IR) ? 1.0 : 0.0;
       }
       __syncwarp();
+      const int eh = qss_ilogb(hq);
 #pragma unroll 4
       for (int p = lane; p < QSS_JAC_NNZ; p += 32) {
         const int rc = qss_jac_rc[p];
         const int r = rc / QSS_NN, j = rc - r * QSS_NN;
-        const double m = -hq * Jq[4 * p];
-        fin = fin && qss_finite(m);
-        Ms[r * QSS_MSTRIDE + j] += m;
+        if constexpr (FP32IR) {   // J itself (see the dense branch)
+          const double v = Jq[4 * p];
+          fin = fin && qss_finite(v) && qss_ilogb(v) + eh < 1020;
+          Ms[r * QSS_MSTRIDE + j] = v;
+        } else {
+          const double m = -hq * Jq[4 * p];
+          fin = fin && qss_finite(m);
+          Ms[r * QSS_MSTRIDE + j] += m;
+        }
       }
 #else
+      if constexpr (FP32IR) {
+        // J itself (no FP64 operation): the FP32-IR solve builds its scaled
+        // FP32 matrix from J's bits and forms the residual from J; h J must
+        // not overflow
+        const int eh = qss_ilogb(hq);
 #pragma unroll 4
-      for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
-        const int r = e / QSS_NN, j = e - r * QSS_NN;
-        const double m = -hq * Jq[4 * e];
-        fin = fin && qss_finite(m);
-        Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
+        for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
+          const int r = e / QSS_NN, j = e - r * QSS_NN;
+          const double v = Jq[4 * e];
+          fin = fin && qss_finite(v) && qss_ilogb(v) + eh < 1020;
+          Ms[r * QSS_MSTRIDE + j] = v;
+        }
+      } else {
+#pragma unroll 4
+        for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
+          const int r = e / QSS_NN, j = e - r * QSS_NN;
+          const double m = -hq * Jq[4 * e];
+          fin = fin && qss_finite(m);
+          Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
+        }
       }
 #endif
     }
@@ -515,13 +626,20 @@ __device__ __forceinline__ void qss_newton_update(
     double xo[QSS_NSLOT];   // this lane's entries of the solution (index lane + 32 slot)
     bool solved;
     if constexpr (FP32IR) {
-      solved = qss_solve_fp32ir(Ms, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
+      solved = qss_solve_fp32ir(Ms, hq, &sh_lu[w * QSS_NN * QSS_MSTRIDE], sh_e[w], sh_piv[w], sh_pinvf[w],
                                 sh_x[w], gr, xo, lane, o);
       if (!solved) {
         // the FP32 factorisation met a zero or non-finite pivot (or the
         // refinement diverged): solve this cell's system in FP64 instead,
-        // from the intact FP64 copy of M, so that the mixed form reports no
-        // status the FP64 form would not
+        // M = I - h J formed from the intact FP64 copy of J as the FP64 form
+        // forms it, so that the mixed form reports no status the FP64 form
+        // would not
+        __syncwarp();
+        for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
+          const int r = e / QSS_NN, j = e - r * QSS_NN;
+          const double m = -hq * Ms[r * QSS_MSTRIDE + j];
+          Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
+        }
         __syncwarp();
 #pragma unroll
         for (int sl = 0; sl < QSS_NSLOT; ++sl) {

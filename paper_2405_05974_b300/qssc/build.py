@@ -156,7 +156,7 @@ def _complete(out: str) -> bool:
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
-                    jac_format: str = "dense") -> str:
+                    jac_format: str = "dense", emit_order: str = "first_use") -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -167,7 +167,10 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     its own translation unit; ``replace_nop`` > 0 applies Alg. 2's
     common-subexpression replacement with that operation threshold;
     ``jac_format`` "csr" makes the Jacobian kernels store only the structural
-    nonzeros, in CSR order (``emit.jac_layout``)."""
+    nonzeros, in CSR order (``emit.jac_layout``); ``emit_order`` "all_first"
+    computes every value before any output is stored (Alg. 3's recycling off,
+    for the memory study; the default "first_use" stores each output as soon
+    as it is final)."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
         variant += (f"parts{int(jac_parts)}",)
@@ -175,6 +178,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         variant += (f"nop{int(replace_nop)}",)
     if jac_format != "dense":
         variant += (jac_format,)
+    if emit_order != "first_use":
+        variant += (emit_order,)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -184,7 +189,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     t0 = time.time()
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
-    src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format)
+    src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format,
+                                           emit_order=emit_order)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")

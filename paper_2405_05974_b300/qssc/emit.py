@@ -34,12 +34,19 @@ def _lit(v: float) -> str:
 
 class Emitter:
     def __init__(self, model, input_names: Dict[int, str], leaves: Dict[int, str] = None,
-                 replace_nop: int = 0):
+                 replace_nop: int = 0, emit_order: str = "first_use"):
         self.m = model
         self.g = model.g
         self.inputs = input_names     # VAR node -> C identifier
         self.leaves = leaves or {}    # any node -> C identifier of an already computed value
         self.replace_nop = replace_nop   # Alg. 2 threshold n_op (0: no replacement)
+        if emit_order not in EMIT_ORDERS:
+            raise ValueError(f"unknown emission order {emit_order!r}")
+        # Alg. 3 on ("first_use": every output stored as soon as it is final,
+        # each value computed just before its first use) or off ("all_first":
+        # every value computed before any output is stored, so no value dies
+        # before the stores begin)
+        self.emit_order = emit_order
 
     def _resolve(self, i):
         g = self.g
@@ -219,9 +226,15 @@ class Emitter:
                 names[n] = f"t{n}"
                 lines.append(f"{indent}const double t{n} = {expr_of(n)};")
 
-        for (fmt, node), root in zip(outputs, roots):
-            visit(root)
-            lines.append(indent + fmt.format(v=ref(root)))
+        if self.emit_order == "first_use":
+            for (fmt, node), root in zip(outputs, roots):
+                visit(root)
+                lines.append(indent + fmt.format(v=ref(root)))
+        else:
+            for root in roots:
+                visit(root)
+            for (fmt, node), root in zip(outputs, roots):
+                lines.append(indent + fmt.format(v=ref(root)))
         # algorithmic count: each DAG operation once, independent of fusion
         dag = Counter()
         for n in seen:
@@ -256,6 +269,7 @@ def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
 
 
 JAC_FORMATS = ("dense", "csr")
+EMIT_ORDERS = ("first_use", "all_first")
 
 
 def jac_layout(model, jac_format: str = "dense"):
@@ -279,7 +293,7 @@ def jac_layout(model, jac_format: str = "dense"):
 
 
 def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
-                          jac_format: str = "dense") -> Tuple[str, dict]:
+                          jac_format: str = "dense", emit_order: str = "first_use") -> Tuple[str, dict]:
     ir = model.ir
     N, Q = ir.N, ir.Q
     n = N + 1
@@ -296,7 +310,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
             "  const double qss_p2 = __longlong_as_double(__double_as_longlong(T) & 0x7ff0000000000000LL);",
             "  const double qss_h = qss_p2 * 0x1p-20;",
             "  const double Tp = T + qss_h, Tm = T - qss_h, inv2h = 0x1p19 / qss_p2;"]
-    em = Emitter(model, inputs, replace_nop=replace_nop)
+    em = Emitter(model, inputs, replace_nop=replace_nop, emit_order=emit_order)
     out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
     out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
     body_w, cnt_w = em.emit(out_w + out_t, indent="  ")
@@ -306,7 +320,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         for i in range(n):
             if (i, c) in pos:
                 out_j.append((f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]))
-    em2 = Emitter(model, inputs, replace_nop=replace_nop)
+    em2 = Emitter(model, inputs, replace_nop=replace_nop, emit_order=emit_order)
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
     hdr = [
         f"// Generated by qssc for mechanism '{ir.name}' (digest {ir.digest}).",
@@ -342,6 +356,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
+        "emit_order": emit_order,
         "jac_format": jac_format, "jac_stored": len(col), "jac_row_ptr": row_ptr, "jac_col": col,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),

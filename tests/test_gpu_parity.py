@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2405_05974_b300 import binding, mechgen, workloads
 from paper_2405_05974_b300.qssc.build import build_mechanism
-from tests.parity import assert_gate
+from tests.parity import assert_gate, assert_gate_exact
 
 pytestmark = pytest.mark.gpu
 
@@ -47,9 +47,12 @@ def test_jacobian_parity(key, ncells):
     J, w, td = run_gpu(key, rho, T, Y)
     ref = om.eval(rho, T, Y)
     eb = om.errbound(rho, T, Y)
-    rw = assert_gate("wdot", w, ref["wdot"], eb["wdot"])
-    rt = assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
-    rj = assert_gate("jac", J, ref["jac"], eb["jac"])
+
+    def q128(name):
+        return lambda cells: om.eval_q128(rho[cells], T[cells], np.ascontiguousarray(Y[:, cells]))[name]
+    rw = assert_gate_exact("wdot", w, ref["wdot"], eb["wdot"], q128("wdot"))
+    rt = assert_gate_exact("Tdot", td, ref["Tdot"], eb["Tdot"], q128("Tdot"))
+    rj = assert_gate_exact("jac", J, ref["jac"], eb["jac"], q128("jac"))
     print(key, "wdot", rw, "Tdot", rt, "jac", rj)
 
 
@@ -136,11 +139,14 @@ def test_full_size_sampled_cells(key):
     ws = w.index_select(1, idx).cpu().numpy()
     del J
     torch.cuda.empty_cache()
-    rs, ts, ys = rho[idx_np], T[idx_np], Y[:, idx_np]
+    rs, ts, ys = rho[idx_np], T[idx_np], np.ascontiguousarray(Y[:, idx_np])
     ref = om.eval(rs, ts, ys)
     eb = om.errbound(rs, ts, ys)
-    assert_gate("jac", Js, ref["jac"], eb["jac"])
-    assert_gate("wdot", ws, ref["wdot"], eb["wdot"])
+
+    def q128(name):
+        return lambda cells: om.eval_q128(rs[cells], ts[cells], np.ascontiguousarray(ys[:, cells]))[name]
+    print(key, "jac", assert_gate_exact("jac", Js, ref["jac"], eb["jac"], q128("jac")))
+    print(key, "wdot", assert_gate_exact("wdot", ws, ref["wdot"], eb["wdot"], q128("wdot")))
 
 
 def test_deterministic_and_host_path_identical():
