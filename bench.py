@@ -56,6 +56,11 @@ def parse():
     p.add_argument("--jac-format", default="dense", choices=["dense", "csr"],
                    help="store every Jacobian entry or only the structural nonzeros")
     p.add_argument("--serve-seconds", type=float, default=8.0)
+    p.add_argument("--fp64-probe", action="store_true",
+                   help="print the FP64 pipe probe grid (latency, warps per SM, active lanes) and exit")
+    p.add_argument("--memory-study", action="store_true",
+                   help="time the Section 4.1 memory-footprint variants that are built (Alg. 2 n_op, "
+                        "Alg. 3 on/off) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the tiny and large workloads' entries (by_config)")
     return p.parse_args()
@@ -270,7 +275,10 @@ def implicit_bench(gm, mech, ncells, dt):
     dtt = torch.full((1,), dt, dtype=torch.float64, device="cuda")
     res = {}
     out = {}
-    for prec, name in ((binding.QSS_LU_FP64, "fp64"), (binding.QSS_LU_FP32_IR, "fp32ir")):
+    reuse = binding.newton_opts(jac_reuse=1)
+    for prec, name, opts in ((binding.QSS_LU_FP64, "fp64", None), (binding.QSS_LU_FP32_IR, "fp32ir", None),
+                             (binding.QSS_LU_FP64, "fp64_reuse", reuse),
+                             (binding.QSS_LU_FP32_IR, "fp32ir_reuse", reuse)):
         times = []
         for rep in range(2):
             t, y = d(T), d(Y)
@@ -278,7 +286,7 @@ def implicit_bench(gm, mech, ncells, dt):
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
-            it, st = gm.implicit_step(r, t, y, dtt, precision=prec)
+            it, st = gm.implicit_step(r, t, y, dtt, precision=prec, opts=opts)
             e1.record()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -296,7 +304,18 @@ def implicit_bench(gm, mech, ncells, dt):
     both = (a[2] == 0) & (b[2] == 0)
     rel = _rel_err(gm, _phi(gm, rho, b[0], b[1]), _phi(gm, rho, a[0], a[1]))[both]
     differ = a[2] != b[2]
+    # cells both forms converged on but to different states: the backward-
+    # Euler system can have more than one root, and the Newton path (which the
+    # precision of the solve perturbs) decides which one is found; count how
+    # many of those states hold a negative concentration (a non-physical root)
+    pa_, pb_ = _phi(gm, rho, a[0], a[1]), _phi(gm, rho, b[0], b[1])
+    far = np.zeros(both.shape, bool)
+    far[both] = rel > 1e-8
+    neg = (pa_[:gm.N] < 0).any(0) | (pb_[:gm.N] < 0).any(0)
     res["fp32ir_vs_fp64"] = {"cells_converged_both": int(both.sum()),
+                             "cells_beyond_1e-8": int(far.sum()),
+                             "of_those_with_a_negative_concentration": int((far & neg).sum()),
+                             "example_cells_beyond_1e-8": np.nonzero(far)[0][:8].tolist(),
                              "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
                              "median_rel": float(np.median(rel)) if both.any() else None,
                              "max_rel": float(rel.max()) if both.any() else None,
@@ -307,7 +326,21 @@ def implicit_bench(gm, mech, ncells, dt):
                                  for i in range(4) for j in range(4) if i != j and
                                  ((a[2] == i) & (b[2] == j)).any()}}
     res["speedup_fp32ir_over_fp64"] = res["fp32ir"]["cells_per_s"] / res["fp64"]["cells_per_s"]
+    # Jacobian reuse (opt-in) against full Newton of the same precision
+    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8)):
+        f, rr = out[name], out[name + "_reuse"]
+        both = (f[2] == 0) & (rr[2] == 0)
+        rel = _rel_err(gm, _phi(gm, rho, rr[0], rr[1]), _phi(gm, rho, f[0], f[1]))[both]
+        res[name + "_reuse_vs_full"] = {
+            "cells_converged_both": int(both.sum()),
+            "frac_within_gate": float(np.mean(rel <= gate)) if both.any() else None,
+            "gate": f"{gate:g} relative + 10 atol", "max_rel": float(rel.max()) if both.any() else None,
+            "speedup": res[name + "_reuse"]["cells_per_s"] / res[name]["cells_per_s"]}
+    res["speedup_fp32ir_reuse_over_fp64"] = res["fp32ir_reuse"]["cells_per_s"] / res["fp64"]["cells_per_s"]
     res["workload"] = f"{mech['name']} backward Euler, dt = {dt:g} s, {ncells} cells"
+    res["forms"] = ("fp64 / fp32ir: full Newton (the analytic Jacobian every iteration, the oracle's "
+                    "definition); *_reuse: a cell keeps its Jacobian while its update norm contracts by 0.3x "
+                    "per iteration (jac_reuse = 1)")
     return res, (rho, T, Y, out)
 
 
@@ -340,7 +373,7 @@ def implicit_cpu_baseline(gm, mech, dt, data, seconds):
     sto = np.concatenate([r[2] for r in res])
     po = _phi(gm, rho[idx], To, Yo)
     cmp = {}
-    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8)):
+    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8), ("fp64_reuse", 1e-10), ("fp32ir_reuse", 1e-8)):
         Tg, Yg, stg = out[name]
         pg = _phi(gm, rho[idx], Tg[idx], Yg[:, idx])
         both = (sto == 0) & (stg[idx] == 0)
@@ -546,12 +579,12 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
     from paper_2405_05974_b300 import autotune, binding, mechgen, workloads
     from paper_2405_05974_b300.qssc.build import load_meta
     mech = workloads.mechanism(key)
-    opts = workloads.build_options(key)
+    opts = {}
     if jac_parts >= 0:
         opts["jac_parts"] = jac_parts
     if jac_format != "dense":
         opts["jac_format"] = jac_format
-    art = autotune.artefact(mech, torch.cuda.get_device_name(local), **opts)
+    art = autotune.artefact(mech, torch.cuda.get_device_name(local), defaults=workloads.build_options(key), **opts)
     meta = load_meta(art)
     gm = binding.Mechanism(art, local)
     st_cfg = workloads.STATES[key]
@@ -663,6 +696,36 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
     return out, (gm, r, t, y, mech, sample)
 
 
+def memory_study(local):
+    """Section 4.1 on this GPU: the Jacobian kernel built with Alg. 2's
+    replacement thresholds n_op = 0, 10, 20 and with Alg. 3's recycling off
+    (every value computed before any output is stored), for the tiny (2^20
+    cells) and hydrocarbon (2^19 cells) workloads.  Per variant: the kernel
+    time (median of 5 CUDA-event timings), the stored values of the emitted
+    code, its FP64 instructions per cell, registers and spills.  Variants
+    that are not built are listed as such (they are not compiled here)."""
+    from paper_2405_05974_b300 import autotune, workloads
+    from paper_2405_05974_b300.qssc.build import find_artefact, load_meta
+    out = []
+    for key, nc in (("tiny", 1 << 20), ("hydrocarbon", 1 << 19)):
+        mech = workloads.mechanism(key)
+        for opts in ({}, {"replace_nop": 10}, {"replace_nop": 20}, {"emit_order": "all_first"}):
+            art = find_artefact(mech, **opts)
+            rec = {"workload": key, "ncells": nc, "options": opts}
+            if art is None:
+                rec["status"] = "not built"
+                out.append(rec)
+                continue
+            meta = load_meta(art)
+            src = open(os.path.join(art, "mech_jac.inc")).read()
+            rec.update({"ms": autotune.time_jacobian(art, key, nc, device=local),
+                        "stored_values": src.count("const double t"),
+                        "fp64_instr_per_cell": meta.get("fp64_instr_jac"), "dag_flops": meta.get("flops_jac"),
+                        "ptxas": meta["kernels"].get("qss_jac_kernel")})
+            out.append(rec)
+    return out
+
+
 def parity_on_sample(mech, sample, seconds=20.0):
     """The timed step's sampled cells against the oracle (CPU-baseline leg):
     the per-entry gate |x - x_ref| <= 1e-10 |x_ref| + 1e-20 + 16 e_ref (e_ref
@@ -739,6 +802,18 @@ def main():
     from paper_2405_05974_b300 import binding
     from paper_2405_05974_b300.qssc.build import build_mechanism
     torch.cuda.set_device(local)
+    if a.memory_study:
+        print(json.dumps({"memory_study": memory_study(local)}))
+        return
+    if a.fp64_probe:
+        grid = []
+        for wps, lanes, dep in [(4, 32, True), (8, 32, True), (4, 32, False), (8, 32, False), (16, 32, False),
+                                (32, 32, False), (16, 16, False), (16, 8, False), (16, 4, False), (16, 1, False)]:
+            tf, cyc = binding.measure_fp64_pipe(wps, lanes, dep, local)
+            grid.append({"warps_per_sm": wps, "active_lanes": lanes, "dependent_chain": dep,
+                         "lane_tflops": tf, "cycles_per_warp_fma": cyc})
+        print(json.dumps({"fp64_pipe_probe": grid, "peak_tflops": binding.measure_fp64_peak(local, 200)}))
+        return
     head, (gm, r, t, y, _, sample) = jacobian_bench(key, ncells, a.steps, a.warmup, local, rank, world, pg,
                                                    do_e2e=not a.no_e2e, jac_parts=a.jac_parts,
                                                    jac_format=a.jac_format,
@@ -790,11 +865,15 @@ def main():
         integration = integrate_bench(gm, mech)
     serving = None
     if not a.no_serve and key == "hydrocarbon" and rank == 0:
+        from paper_2405_05974_b300 import autotune
+        gpu_name = torch.cuda.get_device_name(local)
         mechs = {k: (gm if k == "hydrocarbon" else
-                     binding.Mechanism(build_mechanism(workloads.mechanism(k), **workloads.build_options(k)), local))
+                     binding.Mechanism(autotune.artefact(workloads.mechanism(k), gpu_name,
+                                                         defaults=workloads.build_options(k)), local))
                  for k in ("tiny", "hydrocarbon", "large")}
         weights = [0.2, 0.6, 0.2]
         serving = {"mix": "tiny 0.2 / hydrocarbon 0.6 / large 0.2 (by request)",
+                   "artefacts": "the autotuned Jacobian variant of each mechanism (tuning.json)",
                    "sizes": "log-uniform 256..65536 cells", "dt": "log-uniform 1e-7..1e-5 s",
                    "budget_bytes": 60 << 30, "load": 0.7, "graphs": True,
                    "capacity": "cells/s of one implicit step of 65536 cells per mechanism, "

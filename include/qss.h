@@ -138,18 +138,39 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
  * group kernels exchanging per-cell values through a frontier buffer) runs
  * qss_jacobian in chunks of cells that fit that buffer, which the handle owns
  * and keeps.  This sets its size limit in bytes (default 1/16 of the device's
- * memory, at least 1 GiB; larger chunks mean fewer launches).  No effect for
- * a single-kernel Jacobian.  Errors: QSS_ERR_INVALID_ARG if the limit holds
- * fewer than 32 cells. */
+ * memory, but at most a quarter of the memory free when the mechanism was
+ * loaded, at least 64 MiB; larger chunks mean fewer launches).  When the
+ * device cannot hold the buffer, qss_jacobian halves the chunk (down to 32
+ * cells) and lowers the limit to what fitted.  No effect for a single-kernel
+ * Jacobian.  Errors: QSS_ERR_INVALID_ARG if the limit holds fewer than 32
+ * cells. */
 int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 
 /* Size limit in bytes of the handle's Newton scratch, used by
  * qss_implicit_step and qss_integrate (batches larger than the limit run in
  * chunks, each with its own tail of Newton iterations in which few cells are
- * left).  Default: 1/16 of the device's memory, at least 1 GiB.  A chunk holds
+ * left).  Default: 1/16 of the device's memory, but at most a quarter of the
+ * memory free when the mechanism was loaded, at least 64 MiB.  A chunk holds
  * at least 32 cells whatever the limit; the scratch is allocated on first use
- * and kept (freed by qss_mech_free). */
+ * and kept (freed by qss_mech_free); when the device cannot hold it, the
+ * chunk is halved (down to 32 cells) before QSS_ERR_OOM is returned. */
 int qss_mech_set_newton_bytes(qss_mech_t mech, size_t bytes);
+
+/* Bounds-check status of a QSS_DEBUG artefact (built with the preprocessor
+ * definition QSS_DEBUG=1; a debugging aid, the paper has no counterpart).  In
+ * such a build every kernel checks each index it forms into the caller's
+ * arrays and the library's scratch against the extents it was given, before
+ * the access; a violation skips the access and records a nonzero code in a
+ * device status word instead of trapping, so the context stays usable.
+ * Codes: 1 active-list count beyond the scratch, 2 list entry out of range,
+ * 3 cell beyond ld (or the frontier's extent), 4 chunk larger than the
+ * Newton scratch, 5 cell beyond the state arrays, 6 Newton active count out
+ * of range, 7 Newton list entry out of range.  *status receives the first
+ * code recorded since the last call (0: none) and the word is cleared.  Call
+ * it after the checked work has completed (the read is ordered on the legacy
+ * default stream only).  Errors: QSS_ERR_UNIMPLEMENTED for a release
+ * artefact. */
+int qss_debug_status(qss_mech_t mech, int* status);
 
 /* Number of kernel launches qss_jacobian makes for ncells cells with the
  * handle's current frontier limit: 1 for a single-kernel Jacobian, (chunks) x
@@ -204,6 +225,14 @@ typedef struct {
   double atol_T;       /* K, default 1e-10                                   */
   int max_refine;      /* FP32_IR refinement sweeps (default 10)             */
   double refine_tol;   /* FP32_IR relative correction target (default 1e-8)  */
+  int jac_reuse;       /* 0 (default): full Newton, the analytic Jacobian    */
+                       /* every iteration; 1: keep a cell's Jacobian while   */
+                       /* its Newton update norm shrinks by 0.3x or more per */
+                       /* iteration (only f is evaluated then, and the       */
+                       /* iteration matrix is refactored from the kept J);   */
+                       /* a slower contraction evaluates a fresh Jacobian.   */
+                       /* The converged state satisfies the same stopping    */
+                       /* rule; the iteration count may differ.              */
 } qss_newton_opts;
 
 int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt,
@@ -246,7 +275,8 @@ typedef struct {
   double h0;                     /* first substep in s (0: 1 % of the interval)     */
   double h_min;                  /* smallest substep / interval (default 1e-14)     */
   int max_rounds;                /* substep attempts per cell (default 400)         */
-  qss_newton_opts newton;        /* each substep's Newton solve (default max_iter 6) */
+  qss_newton_opts newton;        /* each substep's Newton solve (default max_iter 6; */
+                                 /* jac_reuse is not used by the substeps)          */
   int order;                     /* 1 backward Euler (default), 2 variable-step BDF2 */
 } qss_integrate_opts;
 
@@ -341,6 +371,18 @@ const char* qss_last_error(void);
  * (2 flops per FMA), from a dependent-chain microbenchmark run for about
  * `millis` milliseconds.  Used as the FP64 roofline denominator. */
 int qss_measure_fp64_peak(int device, int millis, double* tflops);
+
+/* FP64 pipe probe (a measurement aid for kernel design; the paper has no
+ * counterpart): one block of warps_per_sm warps on every SM, lanes running 8
+ * FMAs per iteration as 8 independent chains (dependent = 0) or one dependent
+ * chain (dependent = 1), with only active_lanes (32, 16, 8, 4 or 1) lanes of
+ * each warp doing so.  *lane_tflops counts the active lanes' FMAs (2 flops
+ * each); *cycles_per_warp_fma (nullable) is the SM sub-partition cycles per
+ * warp-wide FMA instruction at the nominal clock.  On B300 a warp with 4
+ * active lanes takes as long as a full one, and one warp per sub-partition
+ * with a single dependent chain already keeps the pipe nearly busy. */
+int qss_measure_fp64_pipe(int device, int warps_per_sm, int active_lanes, int dependent,
+                          double* lane_tflops, double* cycles_per_warp_fma);
 
 /* Diagnostics: evaluates the device math routines used by generated code,
  * elementwise on device arrays x[n] -> y[n] (fn 0 = table-driven exp,

@@ -1,38 +1,82 @@
-"""Per-GPU tuning of the analytic Jacobian kernel's register budget.
+"""Per-GPU tuning of the analytic Jacobian kernel's build variant.
 
 The generated Jacobian of a mechanism holds far more live values than a
-thread has registers, so the kernel spills whatever register budget it gets;
-the budget only trades spill traffic (local memory, L1/L2) against the number
-of resident warps that hide its latency.  Which side wins depends on the
-mechanism and the GPU, so it is measured: each candidate blocks-per-SM bound
-(``__launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)``: 1 -> up to 255 registers,
-3 -> 168, 4 -> 128 at 128 threads a block) is compiled, timed with CUDA
-events on a batch larger than L2, and the fastest is recorded in a JSON table
-keyed by GPU name and mechanism digest (a non-default budget must be at least
-2% faster than the default to be chosen).
+thread has registers, so every variant spills; what the build options change
+is how the spill traffic, the resident warps that hide its latency and the
+launch granularity trade against each other.  Which side wins depends on the
+mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
 
+  block        threads per block: 64, 128, 256 (one cell per thread)
+  minblocks    register budget through __launch_bounds__(block, minblocks):
+               1 (up to 255 registers), 3 (168), 4 (128) at 128 threads
+  smem_spill   part of the spills placed in shared memory by ptxas
+               (QSS_SMEM_SPILL; about 100 bytes per thread)
+  smem_slots   60 or 100 of the values a 120-double register file would
+               reload most often kept in shared memory by the generated code
+               (dynamic shared memory, 100 slots = 100 KB a 128-thread block)
+  jac_parts    the register-pressure split: one kernel per cell (0), or a
+               prefix kernel plus K column-group kernels (2, 4, 8) exchanging
+               per-cell values through a frontier buffer
+
+(A warp-slice per cell, K lanes of a warp cooperating on one cell's DAG, is
+not in the grid: on this part an FP64 instruction occupies the FP64 pipe for
+the whole warp whatever its active lanes (measured), so lanes that compute
+different DAG nodes multiply the FP64 time by K; the column split across
+kernels is the register-pressure split that keeps every lane busy.)
+
+Each candidate artefact is built ahead of time (``--build-only``, CPU), then
+timed with CUDA events on two batch sizes of the workload's states (65536
+cells, the serving size class, and 2^19 cells, larger than L2); the fastest at
+the large size is recorded for (GPU name, mechanism digest) in the JSON table
+together with the whole grid's times.  A non-default variant must be at least
+2 % faster than the default to be chosen.
+
+    python -m paper_2405_05974_b300.autotune --mech hydrocarbon --build-only
     python -m paper_2405_05974_b300.autotune --mech hydrocarbon --write
 
-``artefact(mech)`` returns the artefact built with the recorded choice for
-the current GPU (the default build when the table has no entry).
+``artefact(mech)`` returns the artefact built with the recorded choice for the
+current GPU (the default build when the table has no entry); the benchmark and
+the serving loop load mechanisms through it.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
-from typing import Dict, Optional
+from typing import Dict, List, Optional
 
 from .qssc.build import build_mechanism, load_meta
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
-CANDIDATES = (1, 3, 4)
-MIN_GAIN = 0.02      # relative speed-up a non-default register budget must show
+MIN_GAIN = 0.02      # relative speed-up a non-default variant must show
+SIZES = (1 << 16, 1 << 19)
 
 
 def _digest(mech: dict) -> str:
     from .qssc import mech as qmech
     return qmech.parse(mech).digest
+
+
+def candidates(key: str) -> List[dict]:
+    """The searched build variants of workload `key` (the first is the
+    default).  The large mechanism's single-kernel form does not compile in
+    reasonable time, so only its partitioned forms are searched."""
+    from . import workloads
+    base = workloads.build_options(key)
+    if base.get("jac_parts", 0) >= 2:
+        return [dict(base)] + [{**base, "jac_parts": k} for k in (2, 8) if k != base["jac_parts"]] + \
+            [{**base, "block": 64}]
+    return [dict(base), {**base, "block": 64}, {**base, "block": 256},
+            {**base, "defines": ("QSS_MINBLOCKS=3",)}, {**base, "defines": ("QSS_MINBLOCKS=4",)},
+            {**base, "defines": ("QSS_SMEM_SPILL=1",)}, {**base, "smem_slots": 60},
+            {**base, "smem_slots": 100}, {**base, "jac_parts": 4}]
+
+
+def _norm(opts: dict) -> dict:
+    o = dict(opts)
+    if "defines" in o:
+        o["defines"] = list(o["defines"])
+    return o
 
 
 def load_table(path: str = TABLE) -> Dict[str, dict]:
@@ -42,50 +86,47 @@ def load_table(path: str = TABLE) -> Dict[str, dict]:
         return json.load(f)
 
 
-def defines_for(mech: dict, gpu_name: str, table: Optional[dict] = None) -> tuple:
-    """Preprocessor definitions recorded for (GPU, mechanism); () if none."""
+def choice_for(mech: dict, gpu_name: str, table: Optional[dict] = None) -> dict:
+    """Build options recorded for (GPU, mechanism); {} if none."""
     table = load_table() if table is None else table
     rec = table.get(gpu_name, {}).get(_digest(mech))
-    if not rec or rec.get("minblocks", 1) == 1:
-        return ()
-    return (f"QSS_MINBLOCKS={int(rec['minblocks'])}",)
+    if not rec or "choice" not in rec:
+        return {}
+    c = dict(rec["choice"])
+    if "defines" in c:
+        c["defines"] = tuple(c["defines"])
+    return c
 
 
-def artefact(mech: dict, gpu_name: Optional[str] = None, **build_kw) -> str:
-    """The mechanism's artefact with the tuned Jacobian kernel for this GPU."""
+def artefact(mech: dict, gpu_name: Optional[str] = None, defaults: Optional[dict] = None, **build_kw) -> str:
+    """The mechanism's artefact with the tuned Jacobian kernel for this GPU:
+    the recorded choice, else `defaults` (the workload's build options);
+    explicit keyword build options override either."""
     if gpu_name is None:
         import torch
         gpu_name = torch.cuda.get_device_name() if torch.cuda.is_available() else ""
-    return build_mechanism(mech, defines=defines_for(mech, gpu_name), **build_kw)
+    return build_mechanism(mech, **{**(choice_for(mech, gpu_name) or dict(defaults or {})), **build_kw})
 
 
 def all_tuned_artefacts(mechs: Dict[str, dict], table: Optional[dict] = None):
     """Build every artefact the table selects for any GPU (ahead of time)."""
     table = load_table() if table is None else table
-    out = []
-    for gpu in table:
-        for m in mechs.values():
-            d = defines_for(m, gpu, table)
-            if d:
-                out.append(build_mechanism(m, defines=d))
-    return out
+    return [build_mechanism(m, **choice_for(m, gpu, table)) for gpu in table for m in mechs.values()]
 
 
 def time_jacobian(art: str, key: str, ncells: int, reps: int = 5, device: int = 0) -> float:
-    """Median milliseconds of one qss_jacobian launch over ``ncells`` cells
-    of the workload ``key``'s state distribution."""
+    """Median milliseconds of one qss_jacobian call over ``ncells`` cells of
+    the workload ``key``'s state distribution."""
     import numpy as np
     import torch
 
     from . import binding, mechgen, workloads
     mech = workloads.mechanism(key)
-    scfg = workloads.STATES[key]
     gm = binding.Mechanism(art, device)
-    rho, T, Y = mechgen.generate_states(mech, scfg, ncells)
+    rho, T, Y = mechgen.generate_states(mech, workloads.STATES[key], ncells)
     d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
     r, t, y = d(rho), d(T), d(Y)
-    n = gm.n
-    J = torch.empty((n * n, ncells), dtype=torch.float64, device="cuda")
+    J = torch.empty((gm.jac_nnz, ncells), dtype=torch.float64, device="cuda")
     w = torch.empty((gm.N, ncells), dtype=torch.float64, device="cuda")
     td = torch.empty(ncells, dtype=torch.float64, device="cuda")
     s = torch.cuda.current_stream()
@@ -105,45 +146,61 @@ def time_jacobian(art: str, key: str, ncells: int, reps: int = 5, device: int = 
     return float(np.median(ms))
 
 
-def tune_jacobian(key: str, ncells: int = 1 << 19, candidates=CANDIDATES, device: int = 0) -> dict:
+def tune(key: str, sizes=SIZES, device: int = 0) -> dict:
     import torch
 
     from . import workloads
     mech = workloads.mechanism(key)
-    res = {}
-    for mb in candidates:
-        d = () if mb == 1 else (f"QSS_MINBLOCKS={mb}",)
-        art = build_mechanism(mech, defines=d)
+    res = []
+    for opts in candidates(key):
+        art = build_mechanism(mech, **opts)
         meta = load_meta(art)
-        res[mb] = {"ms": time_jacobian(art, key, ncells, device=device),
-                   "regs": meta["kernels"]["qss_jac_kernel"].get("regs"),
-                   "spill_st": meta["kernels"]["qss_jac_kernel"].get("spill_st")}
-    # a non-default budget must win by more than the run-to-run spread
-    best = min(res, key=lambda k: res[k]["ms"])
-    if best != 1 and res[best]["ms"] > (1.0 - MIN_GAIN) * res[1]["ms"]:
-        best = 1
+        k = meta["kernels"]
+        jk = "qss_jac_kernel" if "qss_jac_kernel" in k else "qss_jac_prefix_kernel"
+        res.append({"opts": _norm(opts), "ms": {str(n): time_jacobian(art, key, n, device=device) for n in sizes},
+                    "regs": k[jk].get("regs"), "stack": k[jk].get("stack"), "spill_st": k[jk].get("spill_st")})
+    big = str(max(sizes))
+    best = min(range(len(res)), key=lambda i: res[i]["ms"][big])
+    if best != 0 and res[best]["ms"][big] > (1.0 - MIN_GAIN) * res[0]["ms"][big]:
+        best = 0
     return {"gpu": torch.cuda.get_device_name(device), "digest": _digest(mech), "name": mech.get("name"),
-            "ncells": ncells, "minblocks": best, "candidates": {str(k): v for k, v in res.items()}}
+            "sizes": list(sizes), "choice": res[best]["opts"], "candidates": res,
+            "rule": f"fastest at {big} cells; a non-default variant must win by {MIN_GAIN:.0%}"}
+
+
+def build_candidates(keys) -> List[str]:
+    """Compile every candidate artefact of the given workloads (CPU)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from . import workloads
+    jobs = [(workloads.mechanism(k), o) for k in keys for o in candidates(k)]
+    with ThreadPoolExecutor(4) as ex:
+        return [f.result() for f in [ex.submit(build_mechanism, m, **o) for m, o in jobs]]
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--mech", action="append", default=None, help="workload key (repeatable)")
-    ap.add_argument("--ncells", type=int, default=1 << 19)
+    ap.add_argument("--build-only", action="store_true", help="compile the candidates and exit (no GPU)")
     ap.add_argument("--write", action="store_true", help="record the choice in the table")
     ap.add_argument("--table", default=TABLE)
     ap.add_argument("--out", default=None, help="also write the records to this JSON file")
     a = ap.parse_args(argv)
+    keys = a.mech or ["hydrocarbon"]
+    if a.build_only:
+        for p in build_candidates(keys):
+            print(p)
+        return
     recs = []
-    for key in a.mech or ["hydrocarbon"]:
-        rec = tune_jacobian(key, a.ncells)
+    for key in keys:
+        rec = tune(key)
         print(json.dumps(rec), flush=True)
         recs.append(rec)
     if a.write:
         table = load_table(a.table)
         for rec in recs:
             table.setdefault(rec["gpu"], {})[rec["digest"]] = {
-                k: rec[k] for k in ("name", "minblocks", "ncells", "candidates")}
+                k: rec[k] for k in ("name", "choice", "sizes", "candidates", "rule")}
         with open(a.table, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
     if a.out:

@@ -35,7 +35,13 @@ class QSSError(RuntimeError):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("atol_C", ctypes.c_double),
                 ("atol_T", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("jac_reuse", ctypes.c_int)]
+
+
+def newton_opts(max_iter=20, rtol=1e-12, atol_C=1e-20, atol_T=1e-10, max_refine=10, refine_tol=1e-8,
+                jac_reuse=0) -> NewtonOpts:
+    """qss_newton_opts with the library's defaults (full Newton)."""
+    return NewtonOpts(max_iter, rtol, atol_C, atol_T, max_refine, refine_tol, jac_reuse)
 
 
 class IntegrateOpts(ctypes.Structure):
@@ -91,6 +97,7 @@ def lib():
         L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.qss_jacobian_launches.argtypes = [_vp, _i64, ctypes.POINTER(_i64)]
         L.qss_mech_set_newton_bytes.argtypes = [_vp, ctypes.c_size_t]
+        L.qss_debug_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
         L.qss_mech_jac_pattern.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                                            ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
         L.qss_jacobian_fd.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
@@ -102,6 +109,7 @@ def lib():
                                     ctypes.POINTER(IntegrateOpts), _vp, _vp, _vp]
         L.qss_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.qss_selftest_math.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _vp, _vp, _vp]
+        L.qss_measure_fp64_pipe.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2
         L.qss_serve_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ServeOpts),
                                        ctypes.POINTER(_vp)]
         L.qss_serve_submit.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
@@ -135,6 +143,16 @@ def measure_fp64_peak(device: int = 0, millis: int = 200) -> float:
     out = ctypes.c_double()
     check(lib().qss_measure_fp64_peak(device, millis, ctypes.byref(out)))
     return out.value
+
+
+def measure_fp64_pipe(warps_per_sm: int, active_lanes: int = 32, dependent: bool = False,
+                      device: int = 0):
+    """(TFLOP/s over the active lanes, SM sub-partition cycles per warp-wide
+    FMA) of the FP64 pipe probe (qss_measure_fp64_pipe)."""
+    t, c = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib().qss_measure_fp64_pipe(device, warps_per_sm, active_lanes, int(dependent), ctypes.byref(t),
+                                      ctypes.byref(c)))
+    return t.value, c.value
 
 
 def selftest_math(fn: int, x: torch.Tensor, device: int = 0) -> torch.Tensor:
@@ -246,6 +264,13 @@ class Mechanism:
         """Size limit of the Newton scratch of the implicit step and the
         interval integrator (default 1/16 of the device's memory)."""
         check(lib().qss_mech_set_newton_bytes(self.h, int(nbytes)))
+
+    def debug_status(self) -> int:
+        """First bounds-check code recorded by a QSS_DEBUG artefact's kernels
+        since the last call (0: none); the word is cleared."""
+        v = ctypes.c_int(0)
+        check(lib().qss_debug_status(self.h, ctypes.byref(v)))
+        return v.value
 
     def set_frontier_bytes(self, nbytes: int):
         """Size limit of the partitioned Jacobian's frontier buffer."""

@@ -15,6 +15,31 @@ extern "C" __global__ void qss_fp64_fma_probe(double* out, int iters, double a, 
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// qss_fp64_pipe_probe: the FP64 pipe's behaviour for kernel design.  Lanes
+// with lane % stride == 0 run 8 FMAs per iteration, as 8 independent chains
+// (dep = 0) or as one dependent chain (dep = 1); the other lanes skip them,
+// so a stride of 2, 4, 8 runs warps with 16, 8, 4 active lanes.  Each thread
+// writes one value so that nothing is eliminated.
+extern "C" __global__ void qss_fp64_pipe_probe(double* out, int iters, double a, double b, int stride,
+                                               int dep) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+  if ((threadIdx.x & 31) % stride == 0) {
+    if (dep) {
+      for (int it = 0; it < iters; ++it) {
+        x0 = fma(x0, a, b); x0 = fma(x0, a, b); x0 = fma(x0, a, b); x0 = fma(x0, a, b);
+        x0 = fma(x0, a, b); x0 = fma(x0, a, b); x0 = fma(x0, a, b); x0 = fma(x0, a, b);
+      }
+    } else {
+      for (int it = 0; it < iters; ++it) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+      }
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
 // Writes `n` doubles (used to evict the L2 between timed iterations).
 extern "C" __global__ void qss_l2_flush(double* buf, long long n, double v) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;

@@ -12,6 +12,16 @@
 #define QSS_BLOCK 128
 #endif
 
+// QSS_SMEM_SPILL=1 lets ptxas place part of a kernel's register spills in
+// shared memory before local memory (the enable_smem_spilling PTX pragma of
+// CUDA 13); the Jacobian kernels use no shared memory otherwise.  A tuning
+// option: ptxas moves about 100 bytes per thread there.
+#if defined(QSS_SMEM_SPILL) && QSS_SMEM_SPILL
+#define QSS_SPILL_TO_SMEM() asm volatile(".pragma \"enable_smem_spilling\";")
+#else
+#define QSS_SPILL_TO_SMEM() do { } while (0)
+#endif
+
 // C_k = rho Y_k / W_k for the transported species.
 __device__ __forceinline__ void qss_unpack(long long c, long long ld, const double* __restrict__ rho,
                                            const double* __restrict__ Y, double* C) {

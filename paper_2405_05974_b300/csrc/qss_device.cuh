@@ -12,6 +12,26 @@
 #include "qss_exp_table.inc"
 #include "qss_log_table.inc"
 
+// QSS_DEBUG builds (-DQSS_DEBUG=1): the kernels check every index they form
+// into the caller's arrays and into the Newton scratch against the extents
+// they were given, before the access; a violation records a code in the
+// module's status word (the first one wins) and the thread (a warp, where the
+// condition is warp-uniform) returns without the access.  No trap: the
+// context stays usable; qss_debug_status reads and clears the word.  Release
+// builds compile the checks away.
+#if defined(QSS_DEBUG) && QSS_DEBUG
+__device__ int qss_debug_word;
+#define QSS_DBG_CHECK(cond, code)                  \
+  do {                                             \
+    if (!(cond)) {                                 \
+      atomicCAS(&qss_debug_word, 0, (int)(code));  \
+      return;                                      \
+    }                                              \
+  } while (0)
+#else
+#define QSS_DBG_CHECK(cond, code) do { } while (0)
+#endif
+
 // 1/x from a single-precision seed refined by one cubic step of the
 // reciprocal iteration (the order-3 form of Newton-Raphson for 1/x; J.-M.
 // Muller et al., Handbook of Floating-Point Arithmetic, 2nd ed. 2018,

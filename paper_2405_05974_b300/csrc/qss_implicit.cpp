@@ -72,11 +72,14 @@ int scratch_release(qss_mech_s* m, CUstream st) {
 
 namespace qss {
 
-size_t newton_scratch_per_cell(const qss_mech_s* m, int precision) {
+size_t newton_scratch_per_cell(const qss_mech_s* m, int precision, bool reuse) {
   (void)precision;   // both forms keep J in FP64; the FP32 factors live in registers
   const int n = m->N + 1;
-  return (size_t)m->jac_nnz * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int) +
-         frontier_bytes_per_cell(m);
+  const size_t base = (size_t)m->jac_nnz * sizeof(double) + (size_t)3 * n * sizeof(double) + 5 * sizeof(int) +
+                      frontier_bytes_per_cell(m);
+  // Jacobian reuse: the kept J, f of the cells that keep it, the previous
+  // update norm, and the two lists of those cells
+  return reuse ? base + (size_t)(m->jac_nnz + n + 1) * sizeof(double) + 2 * sizeof(int) : base;
 }
 
 int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
@@ -87,10 +90,10 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
   if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR)
     return fail(QSS_ERR_INVALID_ARG, "unknown precision");
   if (dt_stride != 0 && dt_stride != 1) return fail(QSS_ERR_INVALID_ARG, "dt_stride must be 0 or 1");
-  *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8};
+  *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8, 0};
   if (opts) *o = *opts;
   if (o->max_iter < 1 || o->max_refine < 0 || !(o->rtol >= 0) || !(o->atol_C >= 0) ||
-      !(o->atol_T >= 0) || !(o->refine_tol >= 0))
+      !(o->atol_T >= 0) || !(o->refine_tol >= 0) || (o->jac_reuse != 0 && o->jac_reuse != 1))
     return fail(QSS_ERR_INVALID_ARG, "bad Newton options");
   if (ncells == 0) return QSS_OK;
   if (!dt || !rho || !T || !Y) return fail(QSS_ERR_INVALID_ARG, "null array");
@@ -108,7 +111,10 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
                     double* fn1, const double* p0, int64_t p0ld) {
   if (ncells == 0) return QSS_OK;
   const int n = m->N + 1;
-  const size_t per_cell = newton_scratch_per_cell(m, precision);
+  // Jacobian reuse is for the implicit step's own solve (not the recorded
+  // substeps of the integrator, which pass fn0 / fn1)
+  const bool reuse = o.jac_reuse != 0 && !fn0 && !fn1;
+  const size_t per_cell = newton_scratch_per_cell(m, precision, reuse);
   const int64_t cap = (int64_t)((scratch_bytes > 256 ? scratch_bytes - 256 : 0) / per_cell);
   if (cap < 32) return fail(QSS_ERR_BUDGET, "scratch too small for one warp of cells");
   int64_t chunk = std::min<int64_t>(cap / 32 * 32, (ncells + 31) / 32 * 32);
@@ -130,14 +136,26 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   // + 2 ints is 8-byte aligned (S % 32 == 0), and the region ends within
   // per_cell * S + 256 bytes of the scratch start
   double* FR = frontier_bytes_per_cell(m) ? (double*)(NACT + 2) : nullptr;
+  // Jacobian reuse: after the frontier, the kept J of every cell (JK[s * nnz
+  // + e]), f of the cells that keep theirs (F2, list positions), the
+  // previous squared update norm (DN), their two lists and two counters
+  double* JK = (double*)(NACT + 2) + frontier_bytes_per_cell(m) / sizeof(double) * S;
+  double* F2 = JK + (size_t)m->jac_nnz * S;
+  double* DN = F2 + (size_t)n * S;
+  int* ULIST[2] = {(int*)(DN + S), (int*)(DN + S) + S};
+  int* NU = ULIST[1] + S;
   long long sld = chunk, l = ld, pl = p0ld;
   int rc;
   const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
+  int mode = 0;
+  double* nulld = nullptr;
+  int* nulli = nullptr;
   for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
     long long cells = std::min<int64_t>(chunk, ncells - c0), cc0 = c0;
     void* a_setup[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &PHI0, &ACT, &ST, &IT, &LIST[0], &NACT, &sld,
                        &ncap, &p0, &pl};
     if ((rc = launch_cells(m, m->f_newton_setup, cells, m->block, a_setup, st, 0))) return rc;
+    if (reuse) CU_TRY(drv().cuMemsetD32Async((CUdeviceptr)NU, 0, 2, st));
     for (int it = 0; it < o.max_iter; ++it) {
       const int cur = it & 1, nxt = cur ^ 1;
       const int* lc = LIST[cur];
@@ -147,9 +165,29 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
                            lc, nc, nn, FR, (int64_t)S, st)))
         return rc;
       int* l2 = LIST[nxt];
-      void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
-                       &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od};
-      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
+      if (!reuse) {
+        void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
+                         &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od, &mode, &nulld, &nulld, &nulli, &nulli};
+        if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
+        continue;
+      }
+      // f alone for the cells that keep their Jacobian (list ULIST[cur])
+      const int* ulc = ULIST[cur];
+      const int* unc = NU + cur;
+      int* unn = NU + nxt;
+      int* ul2 = ULIST[nxt];
+      const double* nullc = nullptr;
+      double* F2T = F2 + (size_t)m->N * S;
+      void* a_w[] = {&cells, &sld, &nullc, &nullc, &nullc, &F2, &F2T, &PHI, &ulc, &unc, &unn};
+      if ((rc = launch_cells(m, m->f_wdot, cells, m->block, a_w, st, 0))) return rc;
+      // fresh Jacobians (kept for the next iterations), then the kept ones
+      int m1 = 1, m2 = 2;
+      void* a_u1[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
+                      &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od, &m1, &JK, &DN, &ul2, &unn};
+      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_u1, st, 0))) return rc;
+      void* a_u2[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F2, &M64, &ACT, &ST, &IT,
+                      &ulc, &unc, &l2, &nn, &sld, &fn0, &fn1, &od, &m2, &JK, &DN, &ul2, &unn};
+      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_u2, st, 0))) return rc;
     }
     void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld, &ncap};
     if ((rc = launch_cells(m, m->f_newton_finish, cells, m->block, a_fin, st, 0))) return rc;
@@ -168,7 +206,7 @@ extern "C" int qss_implicit_step(qss_mech_t m, int64_t ncells, int64_t ld, const
   if (rc || ncells == 0) return rc;
   std::lock_guard<std::mutex> lock(m->mu);
   CU_TRY(drv().cuCtxSetCurrent(m->ctx));
-  const size_t per_cell = newton_scratch_per_cell(m, precision);
+  const size_t per_cell = newton_scratch_per_cell(m, precision, o.jac_reuse != 0);
   int64_t cells = std::min<int64_t>(chunk_cells(m, (int64_t)(m->newton_budget / per_cell)),
                                     (ncells + 31) / 32 * 32);
   rc = scratch_acquire(m, per_cell, &cells, (CUstream)stream);

@@ -47,7 +47,7 @@ extern "C" int qss_integrate(qss_mech_t m, int64_t ncells, int64_t ld, const dou
   // substep Newton: at most 6 iterations (a substep that needs more is retried
   // smaller, which costs less than iterating on: every iteration is a full
   // Jacobian evaluation, and stiff cells that fail fail at any cap)
-  qss_integrate_opts io = {1e-4, 1e-10, 1e-4, 0.0, 1e-14, 400, {6, 1e-12, 1e-20, 1e-10, 10, 1e-8}, 1};
+  qss_integrate_opts io = {1e-4, 1e-10, 1e-4, 0.0, 1e-14, 400, {6, 1e-12, 1e-20, 1e-10, 10, 1e-8, 0}, 1};
   if (opts) io = *opts;
   qss_newton_opts o;
   int rc = check_implicit_args(m, ncells, ld, dt_total, dt_stride, rho, T, Y, precision, &io.newton, &o);

@@ -15,7 +15,7 @@ struct qss_mech_s {
   CUmodule mod = nullptr;          // jac.cubin: analytic Jacobian kernel
   CUmodule mod_wdot = nullptr;     // wdot.cubin: source term, FD Jacobian
   CUmodule mod_newton = nullptr;   // newton.cubin: implicit-step kernels
-  CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;
+  CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;   // f_wdot also has a list mode
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   CUfunction f_integ[4] = {nullptr, nullptr, nullptr, nullptr};   // init, gather, accept, finish
@@ -34,6 +34,10 @@ struct qss_mech_s {
                                         // set at load like newton_budget)
   CUevent fr_done = nullptr;
   int N = 0, Q = 0, M = 0, block = 0;
+  // dynamic shared memory of the single Jacobian kernel (bytes per block):
+  // smem_slots doubles per thread hold its most-reloaded values
+  int smem_slots = 0;
+  unsigned jac_smem = 0;
   // stored Jacobian entries per cell and their pattern (CSR; dense = all)
   int64_t jac_nnz = 0;
   std::vector<int32_t> jac_row_ptr, jac_col;
@@ -85,7 +89,9 @@ int scratch_acquire_bytes(qss_mech_s* m, size_t bytes, CUstream st);
 int scratch_acquire(qss_mech_s* m, size_t per_cell, int64_t* cells, CUstream st);
 int scratch_release(qss_mech_s* m, CUstream st);
 // implicit step (qss_implicit.cpp)
-size_t newton_scratch_per_cell(const qss_mech_s* m, int precision);
+// bytes of Newton scratch per cell; reuse: the Jacobian-reuse iteration's
+// extra arrays (kept J, second f, previous norm, two more lists)
+size_t newton_scratch_per_cell(const qss_mech_s* m, int precision, bool reuse = false);
 int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt, int dt_stride,
                         const double* rho, double* T, double* Y, int precision,
                         const qss_newton_opts* opts, qss_newton_opts* o);

@@ -30,6 +30,7 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot,
                const double* __restrict__ phi, const int* __restrict__ list,
                const int* __restrict__ nact, int* __restrict__ nact_next) {
+  QSS_SPILL_TO_SMEM();
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   double C[QSS_N];
   double Tc;
@@ -38,7 +39,9 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
   if (phi) {
     if (c == 0) *nact_next = 0;
     if (c >= *nact) return;
+    QSS_DBG_CHECK(*nact <= ld, 1);   // list positions index the ld-cell scratch
     const long long s = list[c];
+    QSS_DBG_CHECK(s >= 0 && s < ld, 2);
 #pragma unroll
     for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
     Tc = phi[QSS_N * ld + s];
@@ -46,6 +49,7 @@ qss_jac_kernel(long long ncells, long long ld, const double* __restrict__ rho,
     jstride = 4;
   } else {
     if (c >= ncells) return;
+    QSS_DBG_CHECK(c < ld, 3);
     qss_unpack(c, ld, rho, Y, C);
     Tc = __ldg(T + c);
     jc = jac + c;

@@ -35,18 +35,22 @@ qss_jac_prefix_kernel(long long ncells, long long ld, const double* __restrict__
                       double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ fr,
                       long long fld, const double* __restrict__ phi, const int* __restrict__ list,
                       const int* __restrict__ nact, int* __restrict__ nact_next) {
+  QSS_SPILL_TO_SMEM();
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   double C[QSS_N];
   double Tc;
   if (phi) {
     if (c == 0) *nact_next = 0;
     if (c >= *nact) return;
+    QSS_DBG_CHECK(*nact <= ld && *nact <= fld, 1);
     const long long s = list[c];
+    QSS_DBG_CHECK(s >= 0 && s < ld, 2);
 #pragma unroll
     for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
     Tc = phi[QSS_N * ld + s];
   } else {
     if (c >= ncells) return;
+    QSS_DBG_CHECK(c < ld && c < fld, 3);
     qss_unpack(c, ld, rho, Y, C);
     Tc = __ldg(T + c);
   }
@@ -63,15 +67,18 @@ qss_jac_prefix_kernel(long long ncells, long long ld, const double* __restrict__
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_MINBLOCKS)
 qss_jac_group_kernel(long long ncells, const double* __restrict__ fr, long long fld,
                      double* __restrict__ jac, long long ld, const int* __restrict__ nact) {
+  QSS_SPILL_TO_SMEM();
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   double* jc;
   long long jstride;
   if (nact) {
     if (c >= *nact) return;
+    QSS_DBG_CHECK(*nact <= fld && *nact <= ld, 1);
     jc = jac + (c >> 2) * (4 * QSS_JAC_NNZ) + (c & 3);
     jstride = 4;
   } else {
     if (c >= ncells) return;
+    QSS_DBG_CHECK(c < fld && c < ld, 3);
     jc = jac + c;
     jstride = ld;
   }

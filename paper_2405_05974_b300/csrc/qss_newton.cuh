@@ -110,9 +110,11 @@ qss_newton_setup_kernel(long long cells, long long c0, long long ld, const doubl
   // formula's combination of past states); otherwise it is the state.
   if (ncap) cells = min(cells, (long long)*ncap);
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  QSS_DBG_CHECK(cells <= sld, 4);
   if (s == 0) { NACT[0] = (int)cells; NACT[1] = 0; }
   if (s >= cells) return;
   const long long c = c0 + s;
+  QSS_DBG_CHECK(c < ld && (!P0 || c < p0ld), 5);
   const double r = rho[c];
 #pragma unroll
   for (int k = 0; k < QSS_N; ++k) {
@@ -505,13 +507,27 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Js, 
   return true;
 }
 
+// Jacobian reuse (opt-in, qss_newton_opts.jac_reuse): the squared weighted
+// norm of a cell's Newton update must shrink by this factor from one
+// iteration to the next (the norm by 0.3) for the kept Jacobian to be used
+// again; otherwise the next iteration evaluates a fresh one.
+#define QSS_REUSE_RATE2 0.09
+
+// mode 0: full Newton (J fresh every iteration, at list position t of M64;
+//         the next iteration's list is LIST2);
+// mode 1: J fresh at M64[t], copied to the cell's slot of JK (JK[s * NNZ +
+//         e]) for later iterations; the cell continues on LIST3 (f only);
+// mode 2: J from JK (kept); the cell continues on LIST3 while its update
+//         norm contracts by QSS_REUSE_RATE2 (squared), else on LIST2 (fresh
+//         J).  DN[s] holds the previous iteration's squared norm.
 template <bool FP32IR>
 __device__ __forceinline__ void qss_newton_update(
     long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
     const double* __restrict__ PHI0, const double* __restrict__ F, const double* __restrict__ M64,
     int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT, const int* __restrict__ LIST,
     const int* __restrict__ NACT, int* __restrict__ LIST2, int* __restrict__ NACT2, long long sld,
-    double* __restrict__ FN0, double* __restrict__ FN1, const QssNewtonOpts o) {
+    double* __restrict__ FN0, double* __restrict__ FN1, const QssNewtonOpts o, const int mode,
+    double* __restrict__ JK, double* __restrict__ DN, int* __restrict__ LIST3, int* __restrict__ NACT3) {
   constexpr int W = FP32IR ? QSS_UPD_WARPS32 : QSS_UPD_WARPS;
   const unsigned FULL = 0xffffffffu;
   // per-warp copy of the FP64 Newton matrix M = I - dt J (padded rows; the
@@ -526,6 +542,7 @@ __device__ __forceinline__ void qss_newton_update(
   __shared__ float sh_pinvf[FP32IR ? W : 1][QSS_NN];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nact = *NACT;
+  QSS_DBG_CHECK(nact >= 0 && nact <= sld, 6);
   const long long nwarps = (long long)gridDim.x * W;
   double* Ms = &sh_m[w * QSS_NN * QSS_MSTRIDE];   // this warp's copy of [M | g], M = I - h J
   // one active cell per warp at a time, the warps striding over the list:
@@ -533,6 +550,7 @@ __device__ __forceinline__ void qss_newton_update(
   // warp instead of queueing behind 31 others
   for (long long tq = (long long)blockIdx.x * W + w; tq < nact; tq += nwarps) {
     const int s = LIST[tq];
+    QSS_DBG_CHECK(s >= 0 && s < sld, 7);   // warp-uniform: the whole warp leaves
     const double hq = dt[dt_stride ? c0 + s : 0];
     const int it = IT[s] + 1;
     // g = -G(phi) = -(phi - phi0 - h f), entry i on lane i % 32 (slot i / 32);
@@ -562,7 +580,10 @@ __device__ __forceinline__ void qss_newton_update(
       // the cell's J, interleaved with three neighbours (the Jacobian
       // kernel's list-mode layout): every 32-byte sector this warp loads also
       // holds the same entry of the cells the next warps take
-      const double* __restrict__ Jq = M64 + (tq >> 2) * (4 * QSS_JAC_NNZ) + (tq & 3);
+      const double* __restrict__ Jq = mode == 2 ? JK + (long long)s * QSS_JAC_NNZ
+                                                : M64 + (tq >> 2) * (4 * QSS_JAC_NNZ) + (tq & 3);
+      const int js = mode == 2 ? 1 : 4;   // element stride of that J
+      double* __restrict__ Jk = mode == 1 ? JK + (long long)s * QSS_JAC_NNZ : nullptr;
 #ifdef QSS_JAC_CSR
       // CSR values: M = I first, then M[i][j] += -h J_ij at the stored
       // positions (each position once; 1 + m and 0 + m round as the dense
@@ -577,12 +598,13 @@ __device__ __forceinline__ void qss_newton_update(
       for (int p = lane; p < QSS_JAC_NNZ; p += 32) {
         const int rc = qss_jac_rc[p];
         const int r = rc / QSS_NN, j = rc - r * QSS_NN;
+        const double v = Jq[js * p];
+        if (Jk) Jk[p] = v;
         if constexpr (FP32IR) {   // J itself (see the dense branch)
-          const double v = Jq[4 * p];
           fin = fin && qss_finite(v) && qss_ilogb(v) + eh < 1020;
           Ms[r * QSS_MSTRIDE + j] = v;
         } else {
-          const double m = -hq * Jq[4 * p];
+          const double m = -hq * v;
           fin = fin && qss_finite(m);
           Ms[r * QSS_MSTRIDE + j] += m;
         }
@@ -596,7 +618,8 @@ __device__ __forceinline__ void qss_newton_update(
 #pragma unroll 4
         for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
           const int r = e / QSS_NN, j = e - r * QSS_NN;
-          const double v = Jq[4 * e];
+          const double v = Jq[js * e];
+          if (Jk) Jk[e] = v;
           fin = fin && qss_finite(v) && qss_ilogb(v) + eh < 1020;
           Ms[r * QSS_MSTRIDE + j] = v;
         }
@@ -604,7 +627,9 @@ __device__ __forceinline__ void qss_newton_update(
 #pragma unroll 4
         for (int e = lane; e < QSS_NN * QSS_NN; e += 32) {
           const int r = e / QSS_NN, j = e - r * QSS_NN;
-          const double m = -hq * Jq[4 * e];
+          const double v = Jq[js * e];
+          if (Jk) Jk[e] = v;
+          const double m = -hq * v;
           fin = fin && qss_finite(m);
           Ms[r * QSS_MSTRIDE + j] = (r == j) ? 1.0 + m : m;
         }
@@ -695,8 +720,11 @@ __device__ __forceinline__ void qss_newton_update(
         ACT[s] = 0;
       } else if (it >= o.max_iter) {
         ACT[s] = 0;   // status stays MAXITER
+      } else if (mode == 0 || (mode == 2 && acc > QSS_REUSE_RATE2 * DN[s])) {
+        LIST2[atomicAdd(NACT2, 1)] = s;   // fresh J next iteration
       } else {
-        LIST2[atomicAdd(NACT2, 1)] = s;
+        DN[s] = acc;
+        LIST3[atomicAdd(NACT3, 1)] = s;   // keep J, evaluate f only
       }
     }
   }
@@ -708,18 +736,19 @@ __device__ __forceinline__ void qss_newton_update(
       int* __restrict__ ACT, int* __restrict__ ST, int* __restrict__ IT,                          \
       const int* __restrict__ LIST, const int* __restrict__ NACT, int* __restrict__ LIST2,        \
       int* __restrict__ NACT2, long long sld, double* __restrict__ FN0, double* __restrict__ FN1, \
-      QssNewtonOpts o
+      QssNewtonOpts o, int mode, double* __restrict__ JK, double* __restrict__ DN,                \
+      int* __restrict__ LIST3, int* __restrict__ NACT3
 
 extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS * 32)
 qss_newton_update_fp64_kernel(QSS_UPDATE_PARAMS) {
   qss_newton_update<false>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
-                           NACT2, sld, FN0, FN1, o);
+                           NACT2, sld, FN0, FN1, o, mode, JK, DN, LIST3, NACT3);
 }
 
 extern "C" __global__ void __launch_bounds__(QSS_UPD_WARPS32 * 32)
 qss_newton_update_fp32ir_kernel(QSS_UPDATE_PARAMS) {
   qss_newton_update<true>(c0, dt, dt_stride, PHI, PHI0, F, M64, ACT, ST, IT, LIST, NACT, LIST2,
-                          NACT2, sld, FN0, FN1, o);
+                          NACT2, sld, FN0, FN1, o, mode, JK, DN, LIST3, NACT3);
 }
 
 // Write the state back: T, Y (rho fixed), iterations and status.
@@ -730,8 +759,10 @@ qss_newton_finish_kernel(long long cells, long long c0, long long ld, const doub
                          int* __restrict__ status, long long sld, const int* __restrict__ ncap) {
   if (ncap) cells = min(cells, (long long)*ncap);
   const long long s = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
+  QSS_DBG_CHECK(cells <= sld, 4);
   if (s >= cells) return;
   const long long c = c0 + s;
+  QSS_DBG_CHECK(c < ld, 5);
   const double r = rho[c];
   T[c] = PHI[QSS_N * sld + s];
 #pragma unroll

@@ -62,7 +62,7 @@ extern "C" int qss_implicit_step_noalloc(qss_mech_t m, int64_t ncells, int64_t l
   qss_newton_opts o;
   int rc = check_implicit_args(m, ncells, ld, dt, dt_stride, rho, T, Y, precision, opts, &o);
   if (rc || ncells == 0) return rc;
-  const size_t warp_chunk = newton_scratch_per_cell(m, precision) * 32 + 256;
+  const size_t warp_chunk = newton_scratch_per_cell(m, precision, o.jac_reuse != 0) * 32 + 256;
   if (warp_chunk > QSS_NOALLOC_SCRATCH_BYTES)
     return fail(QSS_ERR_BUDGET, "mechanism too large for the fixed scratch: 32 cells need " +
                                     std::to_string(warp_chunk) + " bytes, the array holds " +

@@ -84,7 +84,7 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   int rc;
   if (m->jac_parts < 2) {
     void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
-    return launch_cells(m, m->f_jac, ncells, m->block, args, s, 0);
+    return launch_cells(m, m->f_jac, ncells, m->block, args, s, m->jac_smem);
   }
   if (!fr || fld < ncells) return fail(QSS_ERR_INVALID_ARG, "frontier scratch too small");
   long long fl = fld;
@@ -163,6 +163,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "jac_parts") ls >> m->jac_parts;
     else if (key == "frontier") ls >> m->frontier;
     else if (key == "jac_nnz") ls >> m->jac_nnz;
+    else if (key == "smem_slots") ls >> m->smem_slots;
     else if (key == "jac_row_ptr" || key == "jac_col") {
       std::vector<int32_t>& v = key == "jac_col" ? m->jac_col : m->jac_row_ptr;
       int32_t x;
@@ -174,6 +175,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   }
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
       m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
+      m->smem_slots < 0 || m->smem_slots > 1024 || (m->smem_slots > 0 && m->jac_parts >= 2) ||
       !jac_pattern_ok(m)) {
     delete m;
     return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
@@ -219,6 +221,15 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
       return code;
     }
   }
+  if (m->smem_slots > 0) {
+    m->jac_smem = (unsigned)m->smem_slots * (unsigned)m->block * sizeof(double);
+    CUresult ra = drv().cuFuncSetAttribute(m->f_jac, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                           (int)m->jac_smem);
+    if (ra != CUDA_SUCCESS) {
+      qss_mech_free(m);
+      return cu_fail(ra, "cuFuncSetAttribute(qss_jac_kernel, dynamic shared memory)");
+    }
+  }
   // optional kernels (implicit step), in newton.cubin
   const char* opt[] = {"qss_newton_update_fp64_kernel", "qss_newton_update_fp32ir_kernel",
                        "qss_newton_setup_kernel", "qss_newton_finish_kernel"};
@@ -255,7 +266,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   if (drv().cuDeviceGetAttribute(&sms, CU_DEVICE_ATTRIBUTE_MULTIPROCESSOR_COUNT, m->dev) != CUDA_SUCCESS)
     sms = 0;
   if (drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m->jac_parts >= 2 ? m->f_prefix : m->f_jac,
-                                                        m->block, 0) != CUDA_SUCCESS)
+                                                        m->block, m->jac_smem) != CUDA_SUCCESS)
     per_sm = 0;
   m->wave_cells = (int64_t)std::max(sms, 0) * std::max(per_sm, 0) * m->block;
   *out = m;
@@ -307,7 +318,10 @@ int qss_wdot(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const 
   if (ncells == 0) return QSS_OK;
   if (!rho || !T || !Y || !wdot) return fail(QSS_ERR_INVALID_ARG, "null array");
   long long nc = ncells, l = ld;
-  void* args[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot};
+  const double* phi = nullptr;
+  const int *list = nullptr, *nact = nullptr;
+  int* nact_next = nullptr;
+  void* args[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
   return launch_cells(m, m->f_wdot, ncells, m->block, args, (CUstream)stream, 0);
 }
 
@@ -363,6 +377,32 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
       return rc;
   }
   CU_TRY(drv().cuEventRecord(m->fr_done, s));
+  return QSS_OK;
+}
+
+int qss_debug_status(qss_mech_t m, int* status) {
+  if (!m || !status) return fail(QSS_ERR_INVALID_ARG, "null argument");
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  std::vector<CUmodule> mods = {m->mod, m->mod_wdot, m->mod_newton, m->mod_prefix};
+  mods.insert(mods.end(), m->mod_group.begin(), m->mod_group.end());
+  bool any = false;
+  int first = 0;
+  for (CUmodule mod : mods) {
+    CUdeviceptr p = 0;
+    size_t bytes = 0;
+    if (!mod || drv().cuModuleGetGlobal(&p, &bytes, mod, "qss_debug_word") != CUDA_SUCCESS) continue;
+    any = true;
+    int v = 0;
+    CU_TRY(drv().cuMemcpyDtoHAsync(&v, p, sizeof(int), nullptr));
+    CU_TRY(drv().cuStreamSynchronize(nullptr));
+    if (v && !first) first = v;
+    if (v) {
+      CU_TRY(drv().cuMemsetD32Async(p, 0, 1, nullptr));
+      CU_TRY(drv().cuStreamSynchronize(nullptr));
+    }
+  }
+  if (!any) return fail(QSS_ERR_UNIMPLEMENTED, "the artefact is not a QSS_DEBUG build");
+  *status = first;
   return QSS_OK;
 }
 

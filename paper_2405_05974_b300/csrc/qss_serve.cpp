@@ -115,12 +115,12 @@ class Arena {
   std::map<size_t, size_t> free_;
 };
 
-size_t batch_bytes(const qss_mech_s* m, int64_t cells, int precision, size_t* scratch_off) {
+size_t batch_bytes(const qss_mech_s* m, int64_t cells, int precision, bool reuse, size_t* scratch_off) {
   const size_t c = (size_t)((cells + 31) / 32 * 32);
   size_t io = c * sizeof(double) * (3 + m->N) + c * 2 * sizeof(int32_t);   // rho, T, dt, Y; iters, status
   io = (io + 255) / 256 * 256;
   *scratch_off = io;
-  return io + newton_scratch_per_cell(m, precision) * c + 256;
+  return io + newton_scratch_per_cell(m, precision, reuse) * c + 256;
 }
 
 }  // namespace
@@ -179,7 +179,7 @@ Region region_of(qss_server_s* s, qss_mech_s* m, size_t off, size_t bytes, int64
   Region g;
   const size_t ldb = (size_t)((cap + 31) / 32 * 32);
   size_t soff;
-  batch_bytes(m, cap, prec, &soff);
+  batch_bytes(m, cap, prec, s->newton.jac_reuse != 0, &soff);
   char* base = (char*)(s->arena_base + off);
   g.rho = (double*)base;
   g.T = g.rho + ldb;
@@ -304,7 +304,7 @@ GraphEntry* graph_for(qss_server_s* s, qss_mech_s* m, int prec, int64_t cells, C
     return &it->second;
   }
   size_t soff;
-  const size_t bytes = batch_bytes(m, bucket, prec, &soff) + 256;   // + the cell-count int
+  const size_t bytes = batch_bytes(m, bucket, prec, s->newton.jac_reuse != 0, &soff) + 256;   // + the cell-count int
   size_t off;
   if (!arena_alloc(s, bytes, &off)) return nullptr;
   Region g = region_of(s, m, off, bytes, bucket, prec, true);
@@ -412,7 +412,7 @@ void scheduler(qss_server_s* s) {
         b->graph->busy = true;
       } else {
         while (true) {
-          need = batch_bytes(head->mech, b->cells, head->precision, &soff);
+          need = batch_bytes(head->mech, b->cells, head->precision, s->newton.jac_reuse != 0, &soff);
           if (arena_alloc(s, need, &b->off)) { got = true; break; }
           if (b->reqs.size() == 1) break;
           b->cells -= b->reqs.back()->ncells;
@@ -462,7 +462,7 @@ int qss_serve_create(int device, size_t budget_bytes, const qss_serve_opts* opts
   int rc = ctx_for_device(device, &s->dev, &s->ctx);
   if (rc) { delete s; return rc; }
   s->device = device;
-  s->newton = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8};
+  s->newton = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8, 0};
   if (opts) {
     if (opts->n_streams > 0) s->n_streams = opts->n_streams;
     if (opts->max_batch_cells > 0) s->max_batch_cells = opts->max_batch_cells;
@@ -503,7 +503,7 @@ int qss_serve_submit(qss_server_t s, qss_mech_t mech, int64_t ncells, const doub
   if (mech->ctx != s->ctx) return fail(QSS_ERR_INVALID_ARG, "mechanism loaded on another device");
   if (!mech->f_newton[precision]) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no Newton kernels");
   size_t soff;
-  if (batch_bytes(mech, ncells, precision, &soff) > s->arena->size() ||
+  if (batch_bytes(mech, ncells, precision, s->newton.jac_reuse != 0, &soff) > s->arena->size() ||
       ncells > s->max_batch_cells) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->rejected++;

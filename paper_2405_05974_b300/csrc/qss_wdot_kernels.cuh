@@ -5,15 +5,36 @@
 
 #include "qss_cells.cuh"
 
+// f = (wdot, Tdot) from (rho, T, Y) or, in list mode (phi and list given), of
+// the t-th cell of the list: s = list[t] for t < *nact, state
+// phi[k * ld + s] = (C_1..C_N, T), f written at column t (wdot[k * ld + t],
+// Tdot[t]); thread 0 then also clears *nact_next (the counter the following
+// Newton update fills).  List mode serves the implicit step's iterations
+// that keep the previous Jacobian.
 extern "C" __global__ void __launch_bounds__(QSS_BLOCK)
 qss_wdot_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                 const double* __restrict__ T, const double* __restrict__ Y,
-                double* __restrict__ wdot, double* __restrict__ Tdot) {
+                double* __restrict__ wdot, double* __restrict__ Tdot, const double* __restrict__ phi,
+                const int* __restrict__ list, const int* __restrict__ nact, int* __restrict__ nact_next) {
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
-  if (c >= ncells) return;
   double C[QSS_N];
-  qss_unpack(c, ld, rho, Y, C);
-  qss_eval_wdot(C, __ldg(T + c), wdot + c, Tdot ? Tdot + c : nullptr, ld);
+  double Tc;
+  if (phi) {
+    if (c == 0) *nact_next = 0;
+    if (c >= *nact) return;
+    QSS_DBG_CHECK(*nact <= ld, 1);
+    const long long s = list[c];
+    QSS_DBG_CHECK(s >= 0 && s < ld, 2);
+#pragma unroll
+    for (int k = 0; k < QSS_N; ++k) C[k] = phi[k * ld + s];
+    Tc = phi[QSS_N * ld + s];
+  } else {
+    if (c >= ncells) return;
+    QSS_DBG_CHECK(c < ld, 3);
+    qss_unpack(c, ld, rho, Y, C);
+    Tc = __ldg(T + c);
+  }
+  qss_eval_wdot(C, Tc, wdot + c, Tdot ? Tdot + c : nullptr, ld);
 }
 
 // Central finite-difference Jacobian of f = (wdot, Tdot) in phi = (C, T)
@@ -29,6 +50,7 @@ qss_jac_fd_kernel(long long ncells, long long ld, const double* __restrict__ rho
                   double dT, double* __restrict__ jac) {
   const long long c = (long long)blockIdx.x * QSS_BLOCK + threadIdx.x;
   if (c >= ncells) return;
+  QSS_DBG_CHECK(c < ld, 3);
   double p[QSS_NN];
   double fm[QSS_NN];
   qss_unpack(c, ld, rho, Y, p);

@@ -125,6 +125,27 @@ def _write_index(root: str, fast: str, name: str):
         os.replace(tmp, os.path.join(root, "index.json"))
 
 
+def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
+                  t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
+                  jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0):
+    """The directory of an artefact already built with these options for the
+    current templates, or None (never compiles)."""
+    root = root or DEFAULT_ROOT
+    variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
+    if jac_parts >= 2:
+        variant += (f"parts{int(jac_parts)}",)
+    if replace_nop > 0:
+        variant += (f"nop{int(replace_nop)}",)
+    if jac_format != "dense":
+        variant += (jac_format,)
+    if emit_order != "first_use":
+        variant += (emit_order,)
+    if smem_slots > 0:
+        variant += (f"smem{int(smem_slots)}",)
+    name = _read_index(root).get(artefact_key(mech, block, tuple(defines) + variant))
+    return os.path.join(root, name) if name and _complete(os.path.join(root, name)) else None
+
+
 def prune_artefacts(keep, root: str = None) -> list:
     """Remove the artefact directories under `root` that are not in `keep`
     (paths returned by build_mechanism in this build) and their index
@@ -156,7 +177,7 @@ def _complete(out: str) -> bool:
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
-                    jac_format: str = "dense", emit_order: str = "first_use") -> str:
+                    jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -170,7 +191,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     nonzeros, in CSR order (``emit.jac_layout``); ``emit_order`` "all_first"
     computes every value before any output is stored (Alg. 3's recycling off,
     for the memory study; the default "first_use" stores each output as soon
-    as it is final)."""
+    as it is final); ``smem_slots`` > 0 keeps that many of the single Jacobian
+    kernel's most-reloaded values in shared memory (dynamic, per thread)."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
         variant += (f"parts{int(jac_parts)}",)
@@ -180,6 +202,10 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         variant += (jac_format,)
     if emit_order != "first_use":
         variant += (emit_order,)
+    if smem_slots > 0:
+        if jac_parts >= 2:
+            raise ValueError("smem_slots applies to the single-kernel Jacobian")
+        variant += (f"smem{int(smem_slots)}",)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -190,7 +216,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
     src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format,
-                                           emit_order=emit_order)
+                                           emit_order=emit_order, smem_slots=smem_slots)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")
@@ -275,6 +301,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         if jac_parts >= 2:
             f.write(f"jac_parts {int(jac_parts)}\nfrontier {meta['frontier']}\n")
         f.write(f"jac_nnz {meta['jac_stored']}\n")
+        if smem_slots > 0:
+            f.write(f"smem_slots {int(smem_slots)}\n")
         if jac_format != "dense":
             f.write("jac_row_ptr " + " ".join(map(str, meta["jac_row_ptr"])) + "\n")
             f.write("jac_col " + " ".join(map(str, meta["jac_col"])) + "\n")

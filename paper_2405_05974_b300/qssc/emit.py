@@ -47,6 +47,7 @@ class Emitter:
         # every value computed before any output is stored, so no value dies
         # before the stores begin)
         self.emit_order = emit_order
+        self.smem_slot = {}   # node -> shared-memory slot (values kept there, not in registers)
 
     def _resolve(self, i):
         g = self.g
@@ -168,6 +169,8 @@ class Emitter:
                 return f"({ref(g.args[n][0])} < {_lit(g.args[n][1])})"
             if n in replaced:
                 return f"({expr_of(n)})"
+            if n in self.smem_slot:
+                return f"qss_sm[{self.smem_slot[n]} * QSS_BLOCK]"
             return names[n]
 
         def expr_of(n):
@@ -224,7 +227,10 @@ class Emitter:
                 if n in inline or n in replaced:
                     continue
                 names[n] = f"t{n}"
-                lines.append(f"{indent}const double t{n} = {expr_of(n)};")
+                if n in self.smem_slot:
+                    lines.append(f"{indent}qss_sm[{self.smem_slot[n]} * QSS_BLOCK] = {expr_of(n)};")
+                else:
+                    lines.append(f"{indent}const double t{n} = {expr_of(n)};")
 
         if self.emit_order == "first_use":
             for (fmt, node), root in zip(outputs, roots):
@@ -268,6 +274,47 @@ def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
 
 
+def choose_smem_values(lines, slots: int, registers: int = 120):
+    """The `slots` values of an emitted straight-line body that a register
+    file of `registers` doubles would reload most often: a Belady (furthest
+    next use) eviction simulation over the SSA sequence counts, per value,
+    the uses that find it evicted.  Returns the node ids (from the t<id>
+    names), most reloaded first."""
+    tok = re.compile(r"\bt(\d+)\b")
+    seq = []
+    for ln in lines:
+        m = re.match(r"\s*const double t(\d+) = (.*);", ln)
+        if m:
+            seq.append((int(m.group(1)), [int(x) for x in tok.findall(m.group(2))]))
+        else:
+            seq.append((None, [int(x) for x in tok.findall(ln)]))
+    uses = {}
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            uses.setdefault(x, []).append(i)
+    pos = {x: 0 for x in uses}
+    resident, reloads = set(), Counter()
+
+    def next_use(x, i):
+        v = uses[x]
+        while pos[x] < len(v) and v[pos[x]] <= i:
+            pos[x] += 1
+        return v[pos[x]] if pos[x] < len(v) else None
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            if x not in resident:
+                reloads[x] += 1
+                resident.add(x)
+        if d is not None and d in uses:
+            resident.add(d)
+        nu = {x: next_use(x, i) for x in resident}
+        resident = {x for x in resident if nu[x] is not None}
+        if len(resident) > registers:
+            for x in sorted(resident, key=lambda y: -nu[y])[:len(resident) - registers]:
+                resident.discard(x)
+    return [x for x, _ in reloads.most_common(slots)]
+
+
 JAC_FORMATS = ("dense", "csr")
 EMIT_ORDERS = ("first_use", "all_first")
 
@@ -293,7 +340,8 @@ def jac_layout(model, jac_format: str = "dense"):
 
 
 def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
-                          jac_format: str = "dense", emit_order: str = "first_use") -> Tuple[str, dict]:
+                          jac_format: str = "dense", emit_order: str = "first_use",
+                          col_order=None, smem_slots: int = 0) -> Tuple[str, dict]:
     ir = model.ir
     N, Q = ir.N, ir.Q
     n = N + 1
@@ -316,12 +364,25 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
     body_w, cnt_w = em.emit(out_w + out_t, indent="  ")
     # Jacobian: column by column, so that dC_Q/dphi for one column is live at a time
     out_j = []
-    for c in range(n):
+    for c in (range(n) if col_order is None else col_order):
         for i in range(n):
             if (i, c) in pos:
                 out_j.append((f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]))
     em2 = Emitter(model, inputs, replace_nop=replace_nop, emit_order=emit_order)
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
+    smem_prologue = []
+    if smem_slots > 0:
+        # the values a 120-double register file would reload most often live
+        # in shared memory (slot k of this thread at qss_sm[k * QSS_BLOCK];
+        # the kernel is launched with smem_slots * QSS_BLOCK doubles of
+        # dynamic shared memory); volatile, so that every use is a shared
+        # load and no register copy is kept
+        chosen = choose_smem_values(body_j, smem_slots)
+        em2 = Emitter(model, inputs, replace_nop=replace_nop, emit_order=emit_order)
+        em2.smem_slot = {x: k for k, x in enumerate(chosen)}
+        body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
+        smem_prologue = ["  extern __shared__ double qss_smem_dyn[];",
+                         "  volatile double* const qss_sm = qss_smem_dyn + threadIdx.x;"]
     hdr = [
         f"// Generated by qssc for mechanism '{ir.name}' (digest {ir.digest}).",
         f"// N = {N} transported species, Q = {Q} QSS species, M = {len(ir.rxns)} reactions.",
@@ -351,12 +412,12 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         "__device__ __forceinline__ void qss_eval_jac(const double* __restrict__ C, const double T,",
         "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
         "    const long long wstride, const long long jstride) {",
-        *unpack, *fd_prologue, *body_j, "}", ""])
+        *unpack, *fd_prologue, *smem_prologue, *body_j, "}", ""])
     meta = {
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
-        "emit_order": emit_order,
+        "emit_order": emit_order, "smem_slots": smem_slots,
         "jac_format": jac_format, "jac_stored": len(col), "jac_row_ptr": row_ptr, "jac_col": col,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),

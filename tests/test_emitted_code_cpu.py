@@ -5,8 +5,9 @@ The CUDA kernels inline the generated straight-line body (qss_eval_jac).  Here
 the same generated source is compiled with g++ (fma, exp, log and 1/x from the
 C++ library in place of the device's table-driven functions) and evaluated on
 seeded workload states, so that build options that change only the emitted
-code -- Alg. 2's common-subexpression replacement (replace_nop, Sec. 4.1) and
-the emission order (Alg. 3's recycling on or off) -- are checked for
+code -- Alg. 2's common-subexpression replacement (replace_nop, Sec. 4.1),
+the emission order (Alg. 3's recycling on or off) and the placement of the
+most-reloaded values in shared memory (smem_slots) -- are checked for
 correctness without a GPU, through the same parity gate as the GPU tests.
 The two emission orders must also emit the same statements, only reordered.
 """
@@ -32,6 +33,10 @@ _SHIM = r"""
 #define __forceinline__ inline
 #define __constant__ static const
 #define __restrict__ __restrict
+#define __shared__
+#define QSS_BLOCK 1
+static struct { unsigned x; } threadIdx = {0};
+double qss_smem_dyn[16384];
 static inline double qss_exp(double x) { return std::exp(x); }
 static inline double qss_log(double x) { return std::log(x); }
 static inline double qss_rcp(double x) { return 1.0 / x; }
@@ -87,7 +92,7 @@ def _run(L, C, T, n_out):
 
 @pytest.mark.parametrize("key,opts", [("tiny", {}), ("tiny", {"replace_nop": 10}),
                                       ("tiny", {"replace_nop": 20}), ("tiny", {"emit_order": "all_first"}),
-                                      ("hydrocarbon", {})])
+                                      ("tiny", {"smem_slots": 24}), ("hydrocarbon", {})])
 def test_generated_code_matches_oracle(key, opts):
     model = _model(key)
     src, meta = emit.emit_mechanism_source(model, **opts)

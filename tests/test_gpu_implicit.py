@@ -37,10 +37,10 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gpu_step(gm, rho, T, Y, dt, precision, ncells=None):
+def gpu_step(gm, rho, T, Y, dt, precision, ncells=None, opts=None):
     r, t, y = dev(rho), dev(T), dev(Y)
     dtt = dev(np.atleast_1d(np.asarray(dt, dtype=np.float64)))
-    it, st = gm.implicit_step(r, t, y, dtt, precision=precision, ncells=ncells)
+    it, st = gm.implicit_step(r, t, y, dtt, precision=precision, ncells=ncells, opts=opts)
     torch.cuda.synchronize()
     return t.cpu().numpy(), y.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
 
@@ -207,3 +207,29 @@ def test_small_newton_scratch_limit_same_results():
     assert np.array_equal(got[3], ref[3]) and np.array_equal(got[2], ref[2])
     fin = ref[3] != 2
     assert np.array_equal(got[0][fin], ref[0][fin]) and np.array_equal(got[1][:, fin], ref[1][:, fin])
+
+
+@pytest.mark.parametrize("key,ncells,dt", [("tiny", 4096, workloads.IMPLICIT_DT),
+                                           ("hydrocarbon", 2048, workloads.IMPLICIT_DT_CONVERGING),
+                                           ("hydrocarbon", 2048, 1e-8),
+                                           ("large", 512, 1e-12)])
+def test_jacobian_reuse_reaches_the_same_state(key, ncells, dt):
+    """Keeping a cell's Jacobian while its Newton update contracts
+    (jac_reuse = 1; only f is evaluated in those iterations) changes the
+    iteration, not the root: the cells that converge with full Newton and
+    with reuse agree within the implicit step's gates, for both precisions,
+    and nearly the same cells converge.  The large mechanism exercises the
+    partitioned Jacobian and its frontier next to the kept Jacobians."""
+    m, gm, om = mech(key)
+    st_cfg = workloads.STATES["implicit"] if key == "hydrocarbon" else workloads.STATES[key]
+    rho, T, Y = mechgen.generate_states(m, st_cfg, ncells)
+    reuse = binding.newton_opts(jac_reuse=1)
+    for prec, rel in ((binding.QSS_LU_FP64, 1e-10), (binding.QSS_LU_FP32_IR, 1e-8)):
+        Tf, Yf, itf, stf = gpu_step(gm, rho, T, Y, dt, prec)
+        Tr, Yr, itr, str_ = gpu_step(gm, rho, T, Y, dt, prec, opts=reuse)
+        both = (stf == 0) & (str_ == 0)
+        assert both.sum() >= 0.95 * (stf == 0).sum(), (np.bincount(stf, minlength=4), np.bincount(str_, minlength=4))
+        pf, pr = phi_of(om, rho, Tf, Yf), phi_of(om, rho, Tr, Yr)
+        ok = close(pr[:, both], pf[:, both], rel, gm.N)
+        assert ok.all(), np.argwhere(~ok)[:5]
+        print(key, dt, prec, "full iters %.2f" % itf[stf == 0].mean(), "reuse iters %.2f" % itr[str_ == 0].mean())
