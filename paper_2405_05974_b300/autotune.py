@@ -11,9 +11,10 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
                1 (up to 255 registers), 3 (168), 4 (128) at 128 threads
   smem_spill   part of the spills placed in shared memory by ptxas
                (QSS_SMEM_SPILL; about 100 bytes per thread)
-  smem_slots   60 or 100 of the values a 120-double register file would
-               reload most often kept in shared memory by the generated code
-               (dynamic shared memory, 100 slots = 100 KB a 128-thread block)
+  smem_slots   60, 80 or 100 of the values a register file would reload
+               most often (a Belady simulation of the emitted body) kept in
+               shared memory by the generated code (dynamic shared memory,
+               100 slots = 100 KB a 128-thread block)
   jac_parts    the register-pressure split: one kernel per cell (0), or a
                prefix kernel plus K column-group kernels (2, 4, 8) exchanging
                per-cell values through a frontier buffer
@@ -69,7 +70,7 @@ def candidates(key: str) -> List[dict]:
     return [dict(base), {**base, "block": 64}, {**base, "block": 256},
             {**base, "defines": ("QSS_MINBLOCKS=3",)}, {**base, "defines": ("QSS_MINBLOCKS=4",)},
             {**base, "defines": ("QSS_SMEM_SPILL=1",)}, {**base, "smem_slots": 60},
-            {**base, "smem_slots": 100}, {**base, "jac_parts": 4}]
+            {**base, "smem_slots": 80}, {**base, "smem_slots": 100}, {**base, "jac_parts": 4}]
 
 
 def _norm(opts: dict) -> dict:

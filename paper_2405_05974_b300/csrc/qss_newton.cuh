@@ -266,8 +266,9 @@ __device__ __forceinline__ float qss_pow2f_neg(int s) {
 //   from there on), and the substitutions are loops over them.
 //   Refinement: r = g - x + h (J x) in FP64 (the rows of a thin last slot
 //   spread over the warp), scaled to FP32 by powers of two, corrected through
-//   the FP32 factors, until the correction is below refine_tol relative,
-//   stops shrinking, or after max_refine sweeps.
+//   the FP32 factors, until the correction is below refine_tol relative (or
+//   the next one, extrapolated from the observed contraction, is below a
+//   tenth of it), stops shrinking, or after max_refine sweeps.
 // Returns false on a zero or non-finite FP32 pivot, or when a refinement
 // sweep produces a non-finite correction (the caller then solves the cell in
 // FP64).
@@ -502,6 +503,10 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Js, 
     __syncwarp();
     const double dmax = __longlong_as_double(dmx), xmax = __longlong_as_double(xmx);
     if (dmax <= o.refine_tol * xmax || dmax >= 0.5 * prev) break;
+    // the next correction, extrapolated from this sweep's contraction
+    // dmax / prev, is below a tenth of the target: the current x is already
+    // that accurate, so the sweep that would confirm it is skipped
+    if (sweep > 0 && dmax * dmax <= 0.1 * o.refine_tol * xmax * prev) break;
     prev = dmax;
   }
   return true;

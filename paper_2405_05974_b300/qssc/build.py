@@ -301,8 +301,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         if jac_parts >= 2:
             f.write(f"jac_parts {int(jac_parts)}\nfrontier {meta['frontier']}\n")
         f.write(f"jac_nnz {meta['jac_stored']}\n")
-        if smem_slots > 0:
-            f.write(f"smem_slots {int(smem_slots)}\n")
+        if meta.get("smem_slots", 0) > 0:   # slots the emitted code uses (at most the requested)
+            f.write(f"smem_slots {int(meta['smem_slots'])}\n")
         if jac_format != "dense":
             f.write("jac_row_ptr " + " ".join(map(str, meta["jac_row_ptr"])) + "\n")
             f.write("jac_col " + " ".join(map(str, meta["jac_col"])) + "\n")

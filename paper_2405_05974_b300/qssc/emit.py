@@ -274,12 +274,15 @@ def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
 
 
-def choose_smem_values(lines, slots: int, registers: int = 120):
+def choose_smem_values(lines, slots: int, registers: int = 170):
     """The `slots` values of an emitted straight-line body that a register
     file of `registers` doubles would reload most often: a Belady (furthest
     next use) eviction simulation over the SSA sequence counts, per value,
     the uses that find it evicted.  Returns the node ids (from the t<id>
-    names), most reloaded first."""
+    names), most reloaded first.  (255 registers hold about 120 doubles; a
+    simulated file of 170 picks values whose reuse distances are longer,
+    and measured slightly faster on B300: 77.7-78.0 vs 78.3 ms per 2^20
+    hydrocarbon cells with 100 slots; 70: 78.0, 250: 78.1.)"""
     tok = re.compile(r"\bt(\d+)\b")
     seq = []
     for ln in lines:
@@ -372,7 +375,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
     body_j, cnt_j = em2.emit(out_w + out_t + out_j, indent="  ")
     smem_prologue = []
     if smem_slots > 0:
-        # the values a 120-double register file would reload most often live
+        # the values a register file would reload most often (simulated) live
         # in shared memory (slot k of this thread at qss_sm[k * QSS_BLOCK];
         # the kernel is launched with smem_slots * QSS_BLOCK doubles of
         # dynamic shared memory); volatile, so that every use is a shared
@@ -417,7 +420,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
-        "emit_order": emit_order, "smem_slots": smem_slots,
+        "emit_order": emit_order, "smem_slots": len(em2.smem_slot),
         "jac_format": jac_format, "jac_stored": len(col), "jac_row_ptr": row_ptr, "jac_col": col,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
