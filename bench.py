@@ -745,8 +745,9 @@ def parity_on_sample(mech, sample, seconds=20.0):
         tol = 1e-10 * np.abs(rf) + 1e-20
         ok = (err <= tol + 16 * b) & np.isfinite(x)
         needed = ok & (err > tol)
+        big = np.abs(rf) > 1e-20     # relative errors of entries above the absolute floor
         d = {"entries": int(x.size), "fail": int((~ok).sum()), "needed_bound": int(needed.sum()),
-             "max_rel": float(np.max(err / np.maximum(np.abs(rf), 1e-300)))}
+             "max_rel": float(np.max(err[big] / np.abs(rf[big]))) if big.any() else 0.0}
         if needed.any() and time.perf_counter() - t0 < seconds:
             cells = np.unique(np.nonzero(needed)[-1])
             q = om.eval_q128(sample["rho"][cells], sample["T"][cells],
@@ -756,7 +757,8 @@ def parity_on_sample(mech, sample, seconds=20.0):
             eq = np.abs(xv - qv)
             d["needed_within_target_of_binary128"] = int((eq <= 1e-10 * np.abs(qv) + 1e-20).sum())
             d["needed_within_gate_of_binary128"] = int((eq <= 1e-10 * np.abs(qv) + 1e-20 + 16 * bv).sum())
-            d["needed_max_rel_to_binary128"] = float(np.max(eq / np.maximum(np.abs(qv), 1e-300)))
+            qb = np.abs(qv) > 1e-20
+            d["needed_max_rel_to_binary128"] = float(np.max(eq[qb] / np.abs(qv[qb]))) if qb.any() else 0.0
         out[name] = d
     out["gate"] = "|x - x_ref| <= 1e-10 |x_ref| + 1e-20 + 16 e_ref (e_ref: the oracle's running-error bound)"
     return out

@@ -231,8 +231,11 @@ typedef struct {
                        /* iteration (only f is evaluated then, and the       */
                        /* iteration matrix is refactored from the kept J);   */
                        /* a slower contraction evaluates a fresh Jacobian.   */
-                       /* The converged state satisfies the same stopping    */
-                       /* rule; the iteration count may differ.              */
+                       /* A kept-J update whose norm grows is discarded and  */
+                       /* the cell retries with a fresh Jacobian.  The       */
+                       /* converged state satisfies the same stopping rule;  */
+                       /* these iterations converge linearly, so allow more  */
+                       /* of them (max_iter about 40).                       */
 } qss_newton_opts;
 
 int qss_implicit_step(qss_mech_t mech, int64_t ncells, int64_t ld, const double* dt,

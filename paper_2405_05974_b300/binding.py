@@ -38,9 +38,14 @@ class NewtonOpts(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("jac_reuse", ctypes.c_int)]
 
 
-def newton_opts(max_iter=20, rtol=1e-12, atol_C=1e-20, atol_T=1e-10, max_refine=10, refine_tol=1e-8,
+def newton_opts(max_iter=None, rtol=1e-12, atol_C=1e-20, atol_T=1e-10, max_refine=10, refine_tol=1e-8,
                 jac_reuse=0) -> NewtonOpts:
-    """qss_newton_opts with the library's defaults (full Newton)."""
+    """qss_newton_opts with the library's defaults (full Newton, at most 20
+    iterations).  With jac_reuse the default cap is 40: iterations that keep
+    the Jacobian converge linearly, and each costs a source-term evaluation
+    instead of a Jacobian."""
+    if max_iter is None:
+        max_iter = 40 if jac_reuse else 20
     return NewtonOpts(max_iter, rtol, atol_C, atol_T, max_refine, refine_tol, jac_reuse)
 
 

@@ -524,7 +524,9 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Js, 
 //         e]) for later iterations; the cell continues on LIST3 (f only);
 // mode 2: J from JK (kept); the cell continues on LIST3 while its update
 //         norm contracts by QSS_REUSE_RATE2 (squared), else on LIST2 (fresh
-//         J).  DN[s] holds the previous iteration's squared norm.
+//         J); an update whose norm grew, or that is not finite, is not
+//         applied (the cell retries from the same state with a fresh J).
+//         DN[s] holds the previous iteration's squared norm.
 template <bool FP32IR>
 __device__ __forceinline__ void qss_newton_update(
     long long c0, const double* __restrict__ dt, int dt_stride, double* __restrict__ PHI,
@@ -697,16 +699,19 @@ __device__ __forceinline__ void qss_newton_update(
       if (lane == 0) { ST[s] = QSS_CELL_SINGULAR; ACT[s] = 0; }
       continue;
     }
-    // phi += x; weighted RMS of the update over the lanes; next list
-    double acc = 0.0;
+    // phi + x and the weighted RMS of the update over the lanes; a kept-J
+    // update whose norm grew (or that turned non-finite) is discarded: the
+    // cell retries from the same state with a fresh Jacobian
+    double acc = 0.0, pv[QSS_NSLOT];
     bool pfin = true;
 #pragma unroll
     for (int sl = 0; sl < QSS_NSLOT; ++sl) {
       const int i = lane + 32 * sl;
+      pv[sl] = 0.0;
       if (i < QSS_NN) {
         const double x = xo[sl];
         const double p = PHI[i * sld + s] + x;
-        PHI[i * sld + s] = p;
+        pv[sl] = p;
         const double wgt = o.rtol * fabs(p) + (i < QSS_N ? o.atol_C : o.atol_T);
         const double qv = x / wgt;
         acc = fma(qv, qv, acc);
@@ -716,8 +721,19 @@ __device__ __forceinline__ void qss_newton_update(
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     pfin = __all_sync(FULL, pfin);
+    const bool reject = mode == 2 && !(pfin && acc <= DN[s]);
+    if (!reject) {
+#pragma unroll
+      for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+        const int i = lane + 32 * sl;
+        if (i < QSS_NN) PHI[i * sld + s] = pv[sl];
+      }
+    }
     if (lane == 0) {
-      if (!pfin) {
+      if (reject) {
+        if (it >= o.max_iter) ACT[s] = 0;          // status stays MAXITER
+        else LIST2[atomicAdd(NACT2, 1)] = s;       // fresh J at the same state
+      } else if (!pfin) {
         ST[s] = QSS_CELL_NONFINITE;
         ACT[s] = 0;
       } else if (acc <= (double)QSS_NN) {
