@@ -8,7 +8,9 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
 
   block        threads per block: 64, 128, 256 (one cell per thread)
   minblocks    register budget through __launch_bounds__(block, minblocks):
-               1 (up to 255 registers), 3 (168), 4 (128) at 128 threads
+               1 (up to 255 registers), 3 (168), 4 (128) at 128 threads;
+               also 3 and 4 combined with 64 and 48 shared-memory slots
+               (what three or four blocks per SM leave room for)
   smem_spill   part of the spills placed in shared memory by ptxas
                (QSS_SMEM_SPILL; about 100 bytes per thread)
   smem_slots   60, 80 or 100 of the values a register file would reload
@@ -23,21 +25,26 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
 not in the grid: on this part an FP64 instruction occupies the FP64 pipe for
 the whole warp whatever its active lanes (measured), so lanes that compute
 different DAG nodes multiply the FP64 time by K; the column split across
-kernels is the register-pressure split that keeps every lane busy.)
+kernels is the register-pressure split that keeps every lane busy.  Two cells
+per thread, the generated body duplicated, doubles the live values and the
+stack and measured 5 % slower, so one cell per thread throughout.)
 
 Each candidate artefact is built ahead of time (``--build-only``, CPU), then
 timed with CUDA events on two batch sizes of the workload's states (65536
-cells, the serving size class, and 2^19 cells, larger than L2); the fastest at
-the large size is recorded for (GPU name, mechanism digest) in the JSON table
-together with the whole grid's times.  A non-default variant must be at least
-2 % faster than the default to be chosen.
+cells, the serving size class, and 2^20 cells, the benchmark's batch); per
+size bucket the fastest is recorded for (GPU name, mechanism digest) in the
+JSON table together with the whole grid's times (a batch takes the choice of
+the smallest timed size at or above its cells, else the largest size's).  A
+non-default variant must be at least 2 % faster than the default to be
+chosen.
 
     python -m paper_2405_05974_b300.autotune --mech hydrocarbon --build-only
     python -m paper_2405_05974_b300.autotune --mech hydrocarbon --write
 
-``artefact(mech)`` returns the artefact built with the recorded choice for the
-current GPU (the default build when the table has no entry); the benchmark and
-the serving loop load mechanisms through it.
+``artefact(mech, ncells=...)`` returns the artefact built with the recorded
+choice for the current GPU and that batch size (the default build when the
+table has no entry); the benchmark and the serving loop load mechanisms
+through it.
 """
 from __future__ import annotations
 
@@ -50,7 +57,7 @@ from .qssc.build import build_mechanism, load_meta
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 MIN_GAIN = 0.02      # relative speed-up a non-default variant must show
-SIZES = (1 << 16, 1 << 19)
+SIZES = (1 << 16, 1 << 20)
 
 
 def _digest(mech: dict) -> str:
@@ -70,13 +77,19 @@ def candidates(key: str) -> List[dict]:
     return [dict(base), {**base, "block": 64}, {**base, "block": 256},
             {**base, "defines": ("QSS_MINBLOCKS=3",)}, {**base, "defines": ("QSS_MINBLOCKS=4",)},
             {**base, "defines": ("QSS_SMEM_SPILL=1",)}, {**base, "smem_slots": 60},
-            {**base, "smem_slots": 80}, {**base, "smem_slots": 100}, {**base, "jac_parts": 4}]
+            {**base, "smem_slots": 80}, {**base, "smem_slots": 100},
+            # a smaller register budget (more resident warps) with as many
+            # shared-memory slots as that many blocks per SM leave room for
+            {**base, "defines": ("QSS_MINBLOCKS=3",), "smem_slots": 64},
+            {**base, "defines": ("QSS_MINBLOCKS=4",), "smem_slots": 48},
+            {**base, "jac_parts": 4}]
 
 
 def _norm(opts: dict) -> dict:
     o = dict(opts)
-    if "defines" in o:
-        o["defines"] = list(o["defines"])
+    for k in ("defines", "ptxas"):
+        if k in o:
+            o[k] = list(o[k])
     return o
 
 
@@ -87,32 +100,60 @@ def load_table(path: str = TABLE) -> Dict[str, dict]:
         return json.load(f)
 
 
-def choice_for(mech: dict, gpu_name: str, table: Optional[dict] = None) -> dict:
-    """Build options recorded for (GPU, mechanism); {} if none."""
+def _opts(c: dict) -> dict:
+    c = dict(c)
+    for k in ("defines", "ptxas"):
+        if k in c:
+            c[k] = tuple(c[k])
+    return c
+
+
+def choice_for(mech: dict, gpu_name: str, table: Optional[dict] = None, ncells: Optional[int] = None) -> dict:
+    """Build options recorded for (GPU, mechanism); {} if none.  With
+    `ncells`, the choice of the size bucket that batch falls in (the
+    smallest timed size >= ncells, else the largest), where the record has
+    per-size choices."""
     table = load_table() if table is None else table
     rec = table.get(gpu_name, {}).get(_digest(mech))
     if not rec or "choice" not in rec:
         return {}
-    c = dict(rec["choice"])
-    if "defines" in c:
-        c["defines"] = tuple(c["defines"])
-    return c
+    by_size = rec.get("choice_by_size")
+    if ncells is not None and by_size:
+        sizes = sorted(int(n) for n in by_size)
+        n = next((x for x in sizes if x >= ncells), sizes[-1])
+        return _opts(by_size[str(n)])
+    return _opts(rec["choice"])
 
 
-def artefact(mech: dict, gpu_name: Optional[str] = None, defaults: Optional[dict] = None, **build_kw) -> str:
+def all_choices(mech: dict, gpu_name: str, table: Optional[dict] = None) -> List[dict]:
+    """Every distinct choice recorded for (GPU, mechanism), all size buckets."""
+    table = load_table() if table is None else table
+    rec = table.get(gpu_name, {}).get(_digest(mech)) or {}
+    out = []
+    for c in [rec.get("choice")] + list((rec.get("choice_by_size") or {}).values()):
+        if c is not None and _opts(c) not in out:
+            out.append(_opts(c))
+    return out
+
+
+def artefact(mech: dict, gpu_name: Optional[str] = None, defaults: Optional[dict] = None,
+             ncells: Optional[int] = None, **build_kw) -> str:
     """The mechanism's artefact with the tuned Jacobian kernel for this GPU:
-    the recorded choice, else `defaults` (the workload's build options);
-    explicit keyword build options override either."""
+    the recorded choice (for batches of `ncells` cells, when given), else
+    `defaults` (the workload's build options); explicit keyword build
+    options override either."""
     if gpu_name is None:
         import torch
         gpu_name = torch.cuda.get_device_name() if torch.cuda.is_available() else ""
-    return build_mechanism(mech, **{**(choice_for(mech, gpu_name) or dict(defaults or {})), **build_kw})
+    return build_mechanism(mech, **{**(choice_for(mech, gpu_name, ncells=ncells) or dict(defaults or {})),
+                                    **build_kw})
 
 
 def all_tuned_artefacts(mechs: Dict[str, dict], table: Optional[dict] = None):
-    """Build every artefact the table selects for any GPU (ahead of time)."""
+    """Build every artefact the table selects for any GPU and size bucket
+    (ahead of time)."""
     table = load_table() if table is None else table
-    return [build_mechanism(m, **choice_for(m, gpu, table)) for gpu in table for m in mechs.values()]
+    return [build_mechanism(m, **c) for gpu in table for m in mechs.values() for c in all_choices(m, gpu, table)]
 
 
 def time_jacobian(art: str, key: str, ncells: int, reps: int = 5, device: int = 0) -> float:
@@ -160,13 +201,19 @@ def tune(key: str, sizes=SIZES, device: int = 0) -> dict:
         jk = "qss_jac_kernel" if "qss_jac_kernel" in k else "qss_jac_prefix_kernel"
         res.append({"opts": _norm(opts), "ms": {str(n): time_jacobian(art, key, n, device=device) for n in sizes},
                     "regs": k[jk].get("regs"), "stack": k[jk].get("stack"), "spill_st": k[jk].get("spill_st")})
+    def pick(n):
+        best = min(range(len(res)), key=lambda i: res[i]["ms"][n])
+        if best != 0 and res[best]["ms"][n] > (1.0 - MIN_GAIN) * res[0]["ms"][n]:
+            best = 0
+        return res[best]["opts"]
+
     big = str(max(sizes))
-    best = min(range(len(res)), key=lambda i: res[i]["ms"][big])
-    if best != 0 and res[best]["ms"][big] > (1.0 - MIN_GAIN) * res[0]["ms"][big]:
-        best = 0
     return {"gpu": torch.cuda.get_device_name(device), "digest": _digest(mech), "name": mech.get("name"),
-            "sizes": list(sizes), "choice": res[best]["opts"], "candidates": res,
-            "rule": f"fastest at {big} cells; a non-default variant must win by {MIN_GAIN:.0%}"}
+            "sizes": list(sizes), "choice": pick(big), "choice_by_size": {str(n): pick(str(n)) for n in sizes},
+            "candidates": res,
+            "rule": f"per size bucket, the fastest at that size (a batch takes the smallest timed size >= its "
+                    f"cells, else the largest; 'choice' is the largest size's); a non-default variant must "
+                    f"win by {MIN_GAIN:.0%}"}
 
 
 def build_candidates(keys) -> List[str]:
@@ -201,7 +248,7 @@ def main(argv=None):
         table = load_table(a.table)
         for rec in recs:
             table.setdefault(rec["gpu"], {})[rec["digest"]] = {
-                k: rec[k] for k in ("name", "choice", "sizes", "candidates", "rule")}
+                k: rec[k] for k in ("name", "choice", "choice_by_size", "sizes", "candidates", "rule")}
         with open(a.table, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
     if a.out:

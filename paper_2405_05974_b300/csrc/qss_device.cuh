@@ -61,6 +61,18 @@ __device__ __forceinline__ double qss_rcp(double x) {
   return fma(y0, fma(e, e, e), y0);
 }
 
+// An integer with |n| < 2^24 as a double, off the FP64 pipe (which also
+// executes the int -> double conversion on this part): the float conversion
+// is exact for such n, and the float's fields widen to the double's with
+// integer operations -- sign kept, exponent re-biased by 1023 - 127 = 896
+// (0x38000000 in the high word), the 23 mantissa bits split 20 / 3 between
+// the high and low words.  Zero has no biased exponent and is selected.
+__device__ __forceinline__ double qss_small_int_to_double(int n) {
+  const unsigned fb = __float_as_uint((float)n);
+  const unsigned hi = (fb & 0x80000000u) | (((fb & 0x7fffffffu) >> 3) + 0x38000000u);
+  return __hiloint2double(fb ? (int)hi : 0, (int)(fb << 29));
+}
+
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989), 2048 entries:
 //   x = (2048 k + j) ln2/2048 + r,  |r| <= ln2/4096,
 //   exp(x) = 2^k * 2^(j/2048) * (1 + q),  q = r + r^2/2 + r^3/6.
@@ -69,15 +81,16 @@ __device__ __forceinline__ double qss_rcp(double x) {
 // cubic is below 3.5e-17 relative; the result is within one ulp of exp(x)
 // (CPU emulation of these operations against exact values).  The 16 KB table
 // stays in L1.  |x| >= 708 and NaN take the library exp (subnormal and
-// overflowing results, never reached by the workloads' arguments).  8 FP64
-// instructions.
+// overflowing results, never reached by the workloads' arguments).  n as a
+// double comes from integer operations (qss_small_int_to_double), not from
+// t - 1.5 * 2^52.  7 FP64 instructions.
 __device__ __forceinline__ double qss_exp_table(double x) {
   const int hx = __double2hiint(x) & 0x7fffffff;
   if (hx >= 0x40862000) return exp(x);
   const double shifter = 6755399441055744.0;   // 1.5 * 2^52
   const double t = fma(x, QSS_EXP_INV_STEP, shifter);
-  const int n = __double2loint(t);
-  const double nd = t - shifter;
+  const int n = __double2loint(t);             // |n| < 708 * 2048 / ln2 < 2^21
+  const double nd = qss_small_int_to_double(n);
   double r = fma(-nd, QSS_EXP_STEP_HI, x);
   r = fma(-nd, QSS_EXP_STEP_LO, r);
   double p = fma(r, 1.0 / 6.0, 0.5);
@@ -97,7 +110,8 @@ __device__ __forceinline__ double qss_exp_table(double x) {
 // the first sum exact, log1p(r) = r + r^2 q(r) with the Taylor terms up to
 // r^7 (truncation below 2^-59 relative).  m, j and y come from integer
 // operations on the bits.  Zero, negative, subnormal, infinite and NaN
-// arguments take the library log.  13 FP64 instructions.
+// arguments take the library log.  12 FP64 instructions (m as a double from
+// integer operations).
 __device__ __forceinline__ double qss_log_table(double x) {
   const long long xb = __double_as_longlong(x);
   if ((unsigned long long)(xb - 0x0010000000000000LL) >= 0x7fe0000000000000ULL) return log(x);
@@ -117,7 +131,7 @@ __device__ __forceinline__ double qss_log_table(double x) {
   q = fma(q, r, 1.0 / 3.0);
   q = fma(q, r, -0.5);
   const double p = fma(r2, q, r);
-  const double md = (double)(int)m;
+  const double md = qss_small_int_to_double((int)m);   // -1022 <= m <= 1024
   const double head = fma(md, QSS_LOG_LN2_HI, lhi);
   const double tail = fma(md, QSS_LOG_LN2_LO, llo) + p;
   return head + tail;

@@ -146,7 +146,6 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
   int* NU = ULIST[1] + S;
   long long sld = chunk, l = ld, pl = p0ld;
   int rc;
-  const int upd_threads = m->upd_threads[precision];   // warps of 32 lanes, one cell per warp at a time
   int mode = 0;
   double* nulld = nullptr;
   int* nulli = nullptr;
@@ -168,7 +167,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
       if (!reuse) {
         void* a_upd[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
                          &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od, &mode, &nulld, &nulld, &nulli, &nulli};
-        if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_upd, st, 0))) return rc;
+        if ((rc = launch_update(m, precision, cells, a_upd, st))) return rc;
         continue;
       }
       // f alone for the cells that keep their Jacobian (list ULIST[cur])
@@ -184,10 +183,10 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
       int m1 = 1, m2 = 2;
       void* a_u1[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F, &M64, &ACT, &ST, &IT,
                       &lc, &nc, &l2, &nn, &sld, &fn0, &fn1, &od, &m1, &JK, &DN, &ul2, &unn};
-      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_u1, st, 0))) return rc;
+      if ((rc = launch_update(m, precision, cells, a_u1, st))) return rc;
       void* a_u2[] = {&cc0, &dt, &dt_stride, &PHI, &PHI0, &F2, &M64, &ACT, &ST, &IT,
                       &ulc, &unc, &l2, &nn, &sld, &fn0, &fn1, &od, &m2, &JK, &DN, &ul2, &unn};
-      if ((rc = launch_cells(m, m->f_newton[precision], cells, upd_threads, a_u2, st, 0))) return rc;
+      if ((rc = launch_update(m, precision, cells, a_u2, st))) return rc;
     }
     void* a_fin[] = {&cells, &cc0, &l, &rho, &T, &Y, &PHI, &ST, &IT, &iters, &cell_status, &sld, &ncap};
     if ((rc = launch_cells(m, m->f_newton_finish, cells, m->block, a_fin, st, 0))) return rc;

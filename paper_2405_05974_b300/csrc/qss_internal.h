@@ -20,6 +20,7 @@ struct qss_mech_s {
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   CUfunction f_integ[4] = {nullptr, nullptr, nullptr, nullptr};   // init, gather, accept, finish
   int upd_threads[2] = {128, 128};   // block size of the update kernels (their launch bound)
+  int64_t upd_grid_max[2] = {0, 0};  // update blocks resident on the device at once (0: unknown)
   // partitioned Jacobian (jac_parts >= 2): prefix kernel + column-group kernels
   int jac_parts = 0, frontier = 0;   // frontier: doubles per cell between them
   CUmodule mod_prefix = nullptr;
@@ -68,6 +69,10 @@ std::string lib_dir();
 int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx);
 int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
                  CUstream stream, unsigned shmem);
+// a Newton update kernel (precision 0 FP64, 1 FP32-IR) over a list of up to
+// ncells cells: one warp per cell as far as the device holds such warps at
+// once, the warps striding over the list beyond that
+int launch_update(qss_mech_s* m, int precision, int64_t ncells, void** args, CUstream stream);
 // wdot, Tdot and J of ncells cells, monolithic or partitioned.  State from
 // (rho, T, Y) with leading dimension ld, J SoA with ld; or, in list mode (phi,
 // list, nact given), of the listed cells with J cell-contiguous.  fr/fld: the

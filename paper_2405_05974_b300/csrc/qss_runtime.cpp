@@ -71,6 +71,23 @@ int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** 
   return QSS_OK;
 }
 
+int launch_update(qss_mech_s* m, int precision, int64_t ncells, void** args, CUstream stream) {
+  if (ncells == 0) return QSS_OK;
+  const int block = m->upd_threads[precision], warps = std::max(block / 32, 1);
+  // one warp per listed cell, capped at the blocks that are resident at once
+  // (a small batch then spreads over every SM instead of queueing 32 cells
+  // on each of ncells / 32 warps); without the occupancy figure, ncells / 32
+  // warps as before
+  int64_t grid = (ncells + warps - 1) / warps;
+  if (m->upd_grid_max[precision] > 0) grid = std::min(grid, m->upd_grid_max[precision]);
+  else grid = (ncells + block - 1) / block;
+  if (grid > INT_MAX) return fail(QSS_ERR_INVALID_ARG, "ncells too large for one launch");
+  CU_TRY(drv().cuCtxSetCurrent(m->ctx));
+  CU_TRY(drv().cuLaunchKernel(m->f_newton[precision], (unsigned)grid, 1, 1, (unsigned)block, 1, 1, 0, stream,
+                              args, nullptr));
+  return QSS_OK;
+}
+
 int64_t chunk_cells(const qss_mech_s* m, int64_t cap) {
   if (m->wave_cells > 0 && cap >= m->wave_cells) return cap / m->wave_cells * m->wave_cells;
   return std::max<int64_t>(32, cap / 32 * 32);
@@ -269,6 +286,13 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
                                                         m->block, m->jac_smem) != CUDA_SUCCESS)
     per_sm = 0;
   m->wave_cells = (int64_t)std::max(sms, 0) * std::max(per_sm, 0) * m->block;
+  for (int i = 0; i < 2; ++i) {
+    int upd_per_sm = 0;
+    if (m->f_newton[i] && sms > 0 &&
+        drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&upd_per_sm, m->f_newton[i], m->upd_threads[i], 0) ==
+            CUDA_SUCCESS)
+      m->upd_grid_max[i] = (int64_t)sms * std::max(upd_per_sm, 0);
+  }
   *out = m;
   return QSS_OK;
 }

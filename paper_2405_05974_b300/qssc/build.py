@@ -125,12 +125,8 @@ def _write_index(root: str, fast: str, name: str):
         os.replace(tmp, os.path.join(root, "index.json"))
 
 
-def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
-                  t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
-                  jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0):
-    """The directory of an artefact already built with these options for the
-    current templates, or None (never compiles)."""
-    root = root or DEFAULT_ROOT
+def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas) -> tuple:
+    """The build options other than block and defines, as index-key parts."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
         variant += (f"parts{int(jac_parts)}",)
@@ -141,7 +137,21 @@ def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), ja
     if emit_order != "first_use":
         variant += (emit_order,)
     if smem_slots > 0:
+        if jac_parts >= 2:
+            raise ValueError("smem_slots applies to the single-kernel Jacobian")
         variant += (f"smem{int(smem_slots)}",)
+    for o in ptxas:
+        variant += (f"ptxas:{o}",)
+    return variant
+
+
+def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
+                  t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
+                  jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0, ptxas=()):
+    """The directory of an artefact already built with these options for the
+    current templates, or None (never compiles)."""
+    root = root or DEFAULT_ROOT
+    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas)
     name = _read_index(root).get(artefact_key(mech, block, tuple(defines) + variant))
     return os.path.join(root, name) if name and _complete(os.path.join(root, name)) else None
 
@@ -177,7 +187,8 @@ def _complete(out: str) -> bool:
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
-                    jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0) -> str:
+                    jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0,
+                    ptxas=()) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -192,20 +203,10 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     computes every value before any output is stored (Alg. 3's recycling off,
     for the memory study; the default "first_use" stores each output as soon
     as it is final); ``smem_slots`` > 0 keeps that many of the single Jacobian
-    kernel's most-reloaded values in shared memory (dynamic, per thread)."""
-    variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
-    if jac_parts >= 2:
-        variant += (f"parts{int(jac_parts)}",)
-    if replace_nop > 0:
-        variant += (f"nop{int(replace_nop)}",)
-    if jac_format != "dense":
-        variant += (jac_format,)
-    if emit_order != "first_use":
-        variant += (emit_order,)
-    if smem_slots > 0:
-        if jac_parts >= 2:
-            raise ValueError("smem_slots applies to the single-kernel Jacobian")
-        variant += (f"smem{int(smem_slots)}",)
+    kernel's most-reloaded values in shared memory (dynamic, per thread);
+    ``ptxas`` are extra ptxas options (``"regUsageLevel=0"`` is passed as
+    ``-Xptxas -regUsageLevel=0``)."""
+    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -230,6 +231,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
             parts[f"mech_jac_g{i}.inc"] = gsrc
     hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES}
     flags = [f"-DQSS_BLOCK={block}", *[f"-D{d}" for d in defines]]
+    for o in ptxas:
+        flags += ["-Xptxas", f"-{o}"]
     # the directory is keyed by what is compiled: the generated sources, the
     # templates and the flags (a generator change that emits the same code
     # keeps its artefacts)
@@ -289,6 +292,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
             meta["kernels"][f"{k}[{name[5:]}]" if name.startswith("jac_g") else k] = v
     meta["block"] = block
     meta["defines"] = list(defines)
+    meta["ptxas"] = list(ptxas)
     meta["codegen_s"] = round(t1 - t0, 3)
     meta["nvcc_s"] = secs
     meta["artefact_key"] = art_name.rsplit("_", 1)[1]

@@ -268,7 +268,7 @@ def algorithmic_flops(counts) -> int:
     return counts["dag_flops"]
 
 
-def fp64_instructions(counts, exp_cost=8, log_cost=13, rcp_cost=3) -> int:
+def fp64_instructions(counts, exp_cost=7, log_cost=12, rcp_cost=3) -> int:
     """Estimated FP64-pipe instructions per cell of the emitted code."""
     return (counts["add"] + counts["mul"] + counts["fma"] + exp_cost * counts["exp"]
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])

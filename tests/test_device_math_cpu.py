@@ -1,4 +1,4 @@
-"""CPU emulation of the device exponential and reciprocal (qss_device.cuh):
+"""CPU emulation of the device exponential, logarithm and reciprocal (qss_device.cuh):
 the same operations in the same order on binary64 values, each fma rounded
 once (exact rationals), with the table and constants read from the generated
 qss_exp_table.inc.  Pins the algorithms and their constants without a GPU:
@@ -25,6 +25,25 @@ def ulps(y, exact):
     return abs(y - exact) / math.ulp(abs(exact))
 
 
+def small_int_to_double(n):
+    """qss_small_int_to_double: the float of n (exact for |n| < 2^24) widened
+    to binary64 by integer operations on its fields."""
+    fb = struct.unpack("<I", struct.pack("<f", float(n)))[0]
+    hi = (fb & 0x80000000) | (((fb & 0x7fffffff) >> 3) + 0x38000000)
+    hi = hi if fb else 0
+    lo = (fb << 29) & 0xffffffff
+    return struct.unpack("<d", struct.pack("<Q", (hi << 32) | lo))[0]
+
+
+def test_small_int_to_double_exact():
+    rng = random.Random(11)
+    ns = list(range(-70000, 70000)) + [rng.randrange(-(1 << 24) + 1, 1 << 24) for _ in range(20000)]
+    ns += [(1 << k) + d for k in range(24) for d in (-1, 0, 1)] + [-(1 << 24) + 1, (1 << 24) - 1]
+    for n in ns:
+        y = small_int_to_double(n)
+        assert y == float(n) and math.copysign(1.0, y) == (-1.0 if n < 0 else 1.0), n
+
+
 def _exp_table():
     src = open(os.path.join(CSRC, "qss_exp_table.inc")).read()
     const = dict(re.findall(r"#define (QSS_EXP_\w+) (\S+)", src))
@@ -39,8 +58,8 @@ def exp_emulated(x, L, inv, hi, lo, tab):
     t = fma(x, inv, shifter)
     n = struct.unpack("<q", struct.pack("<d", t))[0] & 0xffffffff
     n = n - (1 << 32) if n >= 1 << 31 else n
-    nd = t - shifter
-    assert nd == n
+    nd = small_int_to_double(n)
+    assert nd == t - shifter
     r = fma(-nd, hi, x)
     r = fma(-nd, lo, r)
     p = fma(r, 1.0 / 6.0, 0.5)
@@ -129,7 +148,8 @@ def log_emulated(x, base, ln2hi, ln2lo, tab):
     q = fma(q, r, 1.0 / 3.0)
     q = fma(q, r, -0.5)
     p = fma(r2, q, r)
-    md = float(m)
+    md = small_int_to_double(m)
+    assert md == float(m)
     head = fma(md, ln2hi, lhi)
     tail = fma(md, ln2lo, llo) + p
     return head + tail

@@ -8,7 +8,9 @@ seeded workload states, so that build options that change only the emitted
 code -- Alg. 2's common-subexpression replacement (replace_nop, Sec. 4.1),
 the emission order (Alg. 3's recycling on or off) and the placement of the
 most-reloaded values in shared memory (smem_slots) -- are checked for
-correctness without a GPU, through the same parity gate as the GPU tests.
+correctness without a GPU, through the same parity gate as the GPU tests
+(the hydrocarbon variants too, whose CUDA builds take up to 1.5 hours to
+compile and are only timed on the GPU, by the benchmark's memory study).
 The two emission orders must also emit the same statements, only reordered.
 """
 import collections
@@ -92,7 +94,10 @@ def _run(L, C, T, n_out):
 
 @pytest.mark.parametrize("key,opts", [("tiny", {}), ("tiny", {"replace_nop": 10}),
                                       ("tiny", {"replace_nop": 20}), ("tiny", {"emit_order": "all_first"}),
-                                      ("tiny", {"smem_slots": 24}), ("hydrocarbon", {})])
+                                      ("tiny", {"smem_slots": 24}), ("hydrocarbon", {}),
+                                      ("hydrocarbon", {"replace_nop": 10}), ("hydrocarbon", {"replace_nop": 20}),
+                                      ("hydrocarbon", {"emit_order": "all_first"}),
+                                      ("hydrocarbon", {"smem_slots": 100})])
 def test_generated_code_matches_oracle(key, opts):
     model = _model(key)
     src, meta = emit.emit_mechanism_source(model, **opts)

@@ -130,8 +130,9 @@ def test_full_size_sampled_cells(key):
     cells checked against the oracle."""
     from paper_2405_05974_b300 import autotune
     m, _, om = mech(key)
-    gm = binding.Mechanism(autotune.artefact(m, torch.cuda.get_device_name(0), defaults=workloads.build_options(key)), 0)
     nc = workloads.NCELLS[key]
+    gm = binding.Mechanism(autotune.artefact(m, torch.cuda.get_device_name(0), defaults=workloads.build_options(key),
+                                             ncells=nc), 0)
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], nc)
     r, t, y = dev(rho), dev(T), dev(Y)
     J, w, td = gm.jacobian(r, t, y)
@@ -183,18 +184,32 @@ def test_invalid_arguments_rejected():
     assert b"null" in lib.qss_last_error()
 
 
-@pytest.mark.parametrize("key", ["tiny", "hydrocarbon", "large"])
-def test_tuned_variant_matches_default(key):
-    """The Jacobian kernel variant the autotuner records for this GPU (block
-    size, register budget, shared-memory placement of values, column
-    partition) computes the same DAG: its wdot, Tdot and J pass the gate
-    against the oracle on a sample of a ragged batch larger than one wave,
-    and an implicit step gives the default artefact's statuses and a state
-    within the implicit step's gate (the variants may differ from the
-    default build in the compiler's multiply-add contraction only)."""
+def _tuned_cases():
+    """(workload, size bucket) of every choice the table records for this
+    GPU; the bucket's cell count selects it through autotune.artefact."""
+    from paper_2405_05974_b300 import autotune
+    out = []
+    for key in ("tiny", "hydrocarbon", "large"):
+        sizes = sorted({int(n) for gpu in autotune.load_table().values() for rec in gpu.values()
+                        if rec.get("name", "").startswith(workloads.mechanism(key)["name"])
+                        for n in (rec.get("choice_by_size") or {})}) or [None]
+        out += [(key, n) for n in sizes]
+    return out
+
+
+@pytest.mark.parametrize("key,bucket", _tuned_cases())
+def test_tuned_variant_matches_default(key, bucket):
+    """The Jacobian kernel variant the autotuner records for this GPU and
+    size bucket (block size, register budget, shared-memory placement of
+    values, column partition) computes the same DAG: its wdot, Tdot and J
+    pass the gate against the oracle on a sample of a ragged batch larger
+    than one wave, and an implicit step gives the default artefact's
+    statuses and a state within the implicit step's gate (the variants may
+    differ from the default build in the compiler's multiply-add
+    contraction only)."""
     from paper_2405_05974_b300 import autotune
     m, gm, om = mech(key)
-    art = autotune.artefact(m, torch.cuda.get_device_name(0), defaults=workloads.build_options(key))
+    art = autotune.artefact(m, torch.cuda.get_device_name(0), defaults=workloads.build_options(key), ncells=bucket)
     gt = binding.Mechanism(art, 0)
     nc = {"tiny": 40001, "hydrocarbon": 40001, "large": 9001}[key]
     rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], nc)
