@@ -276,9 +276,11 @@ def implicit_bench(gm, mech, ncells, dt):
     res = {}
     out = {}
     reuse = binding.newton_opts(jac_reuse=1)
-    for prec, name, opts in ((binding.QSS_LU_FP64, "fp64", None), (binding.QSS_LU_FP32_IR, "fp32ir", None),
-                             (binding.QSS_LU_FP64, "fp64_reuse", reuse),
-                             (binding.QSS_LU_FP32_IR, "fp32ir_reuse", reuse)):
+    forms = [(binding.QSS_LU_FP64, "fp64", None), (binding.QSS_LU_FP32_IR, "fp32ir", None),
+             (binding.QSS_LU_FP64, "fp64_reuse", reuse), (binding.QSS_LU_FP32_IR, "fp32ir_reuse", reuse)]
+    if gm.has_jac32:
+        forms += [(binding.QSS_LU_MIXED, "mixed", None), (binding.QSS_LU_MIXED, "mixed_reuse", reuse)]
+    for prec, name, opts in forms:
         times = []
         for rep in range(2):
             t, y = d(T), d(Y)
@@ -300,34 +302,18 @@ def implicit_bench(gm, mech, ncells, dt):
                      "status_counts": {nm: int((stn == i).sum()) for i, nm in enumerate(STATUS)},
                      "newton_iters_mean": float(itn[conv].mean()) if conv.any() else None,
                      "newton_iters_max": int(itn[conv].max()) if conv.any() else None}
-    a, b = out["fp64"], out["fp32ir"]
-    both = (a[2] == 0) & (b[2] == 0)
-    rel = _rel_err(gm, _phi(gm, rho, b[0], b[1]), _phi(gm, rho, a[0], a[1]))[both]
-    differ = a[2] != b[2]
-    # cells both forms converged on but to different states: the backward-
-    # Euler system can have more than one root, and the Newton path (which the
-    # precision of the solve perturbs) decides which one is found; count how
-    # many of those states hold a negative concentration (a non-physical root)
-    pa_, pb_ = _phi(gm, rho, a[0], a[1]), _phi(gm, rho, b[0], b[1])
-    far = np.zeros(both.shape, bool)
-    far[both] = rel > 1e-8
-    neg = (pa_[:gm.N] < 0).any(0) | (pb_[:gm.N] < 0).any(0)
-    res["fp32ir_vs_fp64"] = {"cells_converged_both": int(both.sum()),
-                             "cells_beyond_1e-8": int(far.sum()),
-                             "of_those_with_a_negative_concentration": int((far & neg).sum()),
-                             "example_cells_beyond_1e-8": np.nonzero(far)[0][:8].tolist(),
-                             "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
-                             "median_rel": float(np.median(rel)) if both.any() else None,
-                             "max_rel": float(rel.max()) if both.any() else None,
-                             "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell",
-                             "status_differs": int(differ.sum()),
-                             "status_pairs_fp64_to_fp32ir": {
-                                 f"{STATUS[i]}->{STATUS[j]}": int(((a[2] == i) & (b[2] == j)).sum())
-                                 for i in range(4) for j in range(4) if i != j and
-                                 ((a[2] == i) & (b[2] == j)).any()}}
+    for other in [x for x in ("fp32ir", "mixed") if x in out]:
+        res[other + "_vs_fp64"] = _vs_fp64(gm, rho, out["fp64"], out[other])
     res["speedup_fp32ir_over_fp64"] = res["fp32ir"]["cells_per_s"] / res["fp64"]["cells_per_s"]
+    if "mixed" in out:
+        res["speedup_mixed_over_fp64"] = res["mixed"]["cells_per_s"] / res["fp64"]["cells_per_s"]
+        res["speedup_mixed_reuse_over_fp64"] = res["mixed_reuse"]["cells_per_s"] / res["fp64"]["cells_per_s"]
+        res["converged_speedup_mixed_over_fp64"] = (res["mixed"]["converged_cells_per_s"] /
+                                                    max(res["fp64"]["converged_cells_per_s"], 1e-30))
     # Jacobian reuse (opt-in) against full Newton of the same precision
-    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8)):
+    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8), ("mixed", 1e-8)):
+        if name not in out:
+            continue
         f, rr = out[name], out[name + "_reuse"]
         both = (f[2] == 0) & (rr[2] == 0)
         rel = _rel_err(gm, _phi(gm, rho, rr[0], rr[1]), _phi(gm, rho, f[0], f[1]))[both]
@@ -339,9 +325,36 @@ def implicit_bench(gm, mech, ncells, dt):
     res["speedup_fp32ir_reuse_over_fp64"] = res["fp32ir_reuse"]["cells_per_s"] / res["fp64"]["cells_per_s"]
     res["workload"] = f"{mech['name']} backward Euler, dt = {dt:g} s, {ncells} cells"
     res["forms"] = ("fp64 / fp32ir: full Newton (the analytic Jacobian every iteration, the oracle's "
-                    "definition); *_reuse: a cell keeps its Jacobian while its update norm contracts by 0.3x "
-                    "per iteration (jac_reuse = 1)")
+                    "definition); mixed: fp32ir with the Jacobian's derivative terms assembled in FP32 "
+                    "(qss_jacobian_mixed; rates, K_c, the QSS solve and the residual in FP64); *_reuse: a cell "
+                    "keeps its Jacobian while its update norm contracts by 0.3x per iteration (jac_reuse = 1)")
     return res, (rho, T, Y, out)
+
+
+def _vs_fp64(gm, rho, a, b):
+    """Form b's implicit-step results against the FP64 form's (a)."""
+    both = (a[2] == 0) & (b[2] == 0)
+    rel = _rel_err(gm, _phi(gm, rho, b[0], b[1]), _phi(gm, rho, a[0], a[1]))[both]
+    differ = a[2] != b[2]
+    # cells both forms converged on but to different states: the backward-
+    # Euler system can have more than one root, and the Newton path (which the
+    # precision of the solve perturbs) decides which one is found; count how
+    # many of those states hold a negative concentration (a non-physical root)
+    pa_, pb_ = _phi(gm, rho, a[0], a[1]), _phi(gm, rho, b[0], b[1])
+    far = np.zeros(both.shape, bool)
+    far[both] = rel > 1e-8
+    neg = (pa_[:gm.N] < 0).any(0) | (pb_[:gm.N] < 0).any(0)
+    return {"cells_converged_both": int(both.sum()), "cells_beyond_1e-8": int(far.sum()),
+            "of_those_with_a_negative_concentration": int((far & neg).sum()),
+            "example_cells_beyond_1e-8": np.nonzero(far)[0][:8].tolist(),
+            "frac_within_1e-8": float(np.mean(rel <= 1e-8)) if both.any() else None,
+            "median_rel": float(np.median(rel)) if both.any() else None,
+            "max_rel": float(rel.max()) if both.any() else None,
+            "metric": "max_k |dphi_k| / (|phi_k| + 10 atol_k) per cell",
+            "status_differs": int(differ.sum()),
+            "status_pairs_from_fp64": {
+                f"{STATUS[i]}->{STATUS[j]}": int(((a[2] == i) & (b[2] == j)).sum())
+                for i in range(4) for j in range(4) if i != j and ((a[2] == i) & (b[2] == j)).any()}}
 
 
 def implicit_cpu_baseline(gm, mech, dt, data, seconds):
@@ -373,7 +386,10 @@ def implicit_cpu_baseline(gm, mech, dt, data, seconds):
     sto = np.concatenate([r[2] for r in res])
     po = _phi(gm, rho[idx], To, Yo)
     cmp = {}
-    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8), ("fp64_reuse", 1e-10), ("fp32ir_reuse", 1e-8)):
+    for name, gate in (("fp64", 1e-10), ("fp32ir", 1e-8), ("fp64_reuse", 1e-10), ("fp32ir_reuse", 1e-8),
+                       ("mixed", 1e-8), ("mixed_reuse", 1e-8)):
+        if name not in out:
+            continue
         Tg, Yg, stg = out[name]
         pg = _phi(gm, rho[idx], Tg[idx], Yg[:, idx])
         both = (sto == 0) & (stg[idx] == 0)
@@ -499,6 +515,7 @@ def implicit_capacity(gm, key, prec, ncells=65536):
 # serving: Poisson request stream over the continuous-batching server
 # ---------------------------------------------------------------------------
 def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, load=0.7):
+    """precision: one for every mechanism, or a dict by workload key."""
     import torch
     from paper_2405_05974_b300 import binding, mechgen, workloads
     rng = np.random.default_rng(seed)
@@ -530,7 +547,8 @@ def serve_bench(mechs, weights, precision, seconds, capacity_cells_s, seed=104, 
         rh = torch.from_numpy(rho[off:off + n].copy()).pin_memory()
         th = torch.from_numpy(T[off:off + n].copy()).pin_memory()
         yh = torch.from_numpy(np.ascontiguousarray(Y[:, off:off + n])).pin_memory()
-        reqs.append((srv.submit(gm, rh, th, yh, dt, precision), n))
+        prec = precision[key] if isinstance(precision, dict) else precision
+        reqs.append((srv.submit(gm, rh, th, yh, dt, prec), n))
         t_next += rng.exponential(1.0 / rate)
     for rid, _ in reqs:
         srv.wait(rid)
@@ -584,6 +602,8 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
         opts["jac_parts"] = jac_parts
     if jac_format != "dense":
         opts["jac_format"] = jac_format
+    if key in workloads.MIXED_JACOBIAN:
+        opts["jac32"] = True     # the mixed-precision kernels beside the FP64 ones (same FP64 cubins)
     art = autotune.artefact(mech, torch.cuda.get_device_name(local), defaults=workloads.build_options(key),
                             ncells=ncells, **opts)
     meta = load_meta(art)
@@ -622,6 +642,28 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
         g1.record(stream)
         torch.cuda.synchronize()
     barrier(pg)
+    # the mixed-precision Jacobian (derivative terms in FP32) on the same
+    # cells, timed the same way after the FP64 steps (it overwrites J)
+    mixed = None
+    if gm.has_jac32:
+        J32 = torch.empty_like(J)
+        for _ in range(3):
+            gm.jacobian(r, t, y, jac=J32, wdot=w, Tdot=td, stream=stream, mixed=True)
+        m_ms = []
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gm.jacobian(r, t, y, jac=J32, wdot=w, Tdot=td, stream=stream, mixed=True)
+            e1.record(stream)
+            e1.synchronize()
+            m_ms.append(e0.elapsed_time(e1))
+        mixed = {"kernel": "qss_jac32_kernel", "ms": float(np.mean(m_ms)),
+                 "cells_per_s": ncells / (float(np.mean(m_ms)) * 1e-3),
+                 "fp64_instr_per_cell_est": meta.get("fp64_instr_jac32"),
+                 "form": "qss_jacobian_mixed: wdot, Tdot and everything they need in FP64, the Jacobian's "
+                         "derivative terms in FP32 (stored as FP64); the Newton matrix of the mixed implicit step"}
     sample = None
     if keep_sample:
         # a seeded sample of the timed step's cells, with their outputs, for
@@ -631,11 +673,17 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
         sample = {"idx": idx, "rho": rho[idx], "T": T[idx], "Y": np.ascontiguousarray(Y[:, idx]),
                   "jac": J.index_select(1, ii).cpu().numpy(), "wdot": w.index_select(1, ii).cpu().numpy(),
                   "Tdot": td.index_select(0, ii).cpu().numpy(), "jac_format": jac_format}
+        if mixed is not None:
+            sample["jac32"] = J32.index_select(1, ii).cpu().numpy()
+    if mixed is not None:
+        del J32
     per = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms = max_over_ranks(pg, float(np.sum(per)) if flush is not None else g0.elapsed_time(g1))
     ms_step = total_ms / steps
     value = ncells * world * steps / (total_ms * 1e-3)
     kernel_ms = float(np.mean(per))
+    if mixed is not None:
+        mixed["speedup_over_fp64_kernel"] = kernel_ms / mixed["ms"]
     parts = int(meta.get("jac_parts", 0) or 0)
     flops_cell = meta["flops_jac_parts"] if parts >= 2 else meta["flops_jac"]
     achieved = flops_cell * ncells / (kernel_ms * 1e-3) / 1e12
@@ -688,6 +736,7 @@ def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=Tr
                                                          "timed steps" if flush_l2 else
                                                          "inputs and outputs larger than L2 (no flush)"),
            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": steps * launches_per_step,
+           "mixed_jacobian": mixed,
            "clocks": clk.summary(),
            "kernel": {"ptxas": {k: v for k, v in meta["kernels"].items() if k.startswith("qss_jac")},
                       "defines": meta.get("defines", []),
@@ -762,6 +811,16 @@ def parity_on_sample(mech, sample, seconds=20.0):
             d["needed_max_rel_to_binary128"] = float(np.max(eq[qb] / np.abs(qv[qb]))) if qb.any() else 0.0
         out[name] = d
     out["gate"] = "|x - x_ref| <= 1e-10 |x_ref| + 1e-20 + 16 e_ref (e_ref: the oracle's running-error bound)"
+    if "jac32" in sample and sample["jac_format"] == "dense":
+        # the mixed-precision Jacobian against the FP32 form of the same bound
+        x, rf = sample["jac32"], ref["jac"]
+        err = np.abs(x - rf)
+        bound = 2.0 ** 29 * eb["jac"] + 1e-20
+        big = np.abs(rf) > 1e-20
+        out["jac32"] = {"entries": int(x.size), "fail": int((~(err <= bound)).sum()),
+                        "max_err_over_bound": float(np.max(err / bound)),
+                        "median_rel": float(np.median(err[big] / np.abs(rf[big]))) if big.any() else 0.0,
+                        "gate": "|J - J_ref| <= 2^29 e_ref + 1e-20 (the FP32 form of the FP64 rounding bound)"}
     return out
 
 
@@ -873,7 +932,8 @@ def main():
         # the tuned variant of each mechanism for the serving size class
         # (batches of up to 65536 cells)
         arts = {k: autotune.artefact(workloads.mechanism(k), gpu_name, defaults=workloads.build_options(k),
-                                     ncells=65536) for k in ("tiny", "hydrocarbon", "large")}
+                                     ncells=65536, **({"jac32": True} if k in workloads.MIXED_JACOBIAN else {}))
+                for k in ("tiny", "hydrocarbon", "large")}
         mechs = {k: (gm if os.path.samefile(arts[k], gm.dir) else binding.Mechanism(arts[k], local))
                  for k in arts}
         weights = [0.2, 0.6, 0.2]
@@ -884,8 +944,13 @@ def main():
                    "budget_bytes": 60 << 30, "load": 0.7, "graphs": True,
                    "capacity": "cells/s of one implicit step of 65536 cells per mechanism, "
                                "combined by the mix's cell-weighted harmonic mean"}
-        for prec, name in ((binding.QSS_LU_FP32_IR, "fp32ir"), (binding.QSS_LU_FP64, "fp64")):
-            caps = {k: implicit_capacity(mechs[k], k, prec) for k in mechs}
+        # mixed: the mixed-precision Jacobian where the artefact has it (the
+        # large mechanism's partitioned Jacobian has no mixed form: FP32-IR)
+        mixed = {k: (binding.QSS_LU_MIXED if mechs[k].has_jac32 else binding.QSS_LU_FP32_IR) for k in mechs}
+        serving["mixed_precision_by_mechanism"] = {k: ("mixed" if v == binding.QSS_LU_MIXED else "fp32ir")
+                                                   for k, v in mixed.items()}
+        for prec, name in ((mixed, "mixed"), (binding.QSS_LU_FP32_IR, "fp32ir"), (binding.QSS_LU_FP64, "fp64")):
+            caps = {k: implicit_capacity(mechs[k], k, prec[k] if isinstance(prec, dict) else prec) for k in mechs}
             cap = 1.0 / sum(w / caps[k] for w, k in zip(weights, mechs))
             serving[name] = serve_bench(mechs, weights, prec, a.serve_seconds, cap)
             serving[name]["capacity_cells_per_s"] = {**caps, "mix": cap}

@@ -70,8 +70,10 @@ typedef enum {
   QSS_ERR_UNIMPLEMENTED = -8
 } qss_status;
 
-/* Linear-algebra precision of the implicit step's Newton systems. */
-enum { QSS_LU_FP64 = 0, QSS_LU_FP32_IR = 1 };
+/* Precision of the implicit step's Newton systems: FP64 LU; FP32 LU with
+ * FP64 residual refinement; the same FP32-IR solve of a matrix whose
+ * Jacobian's derivative terms were assembled in FP32 (qss_jacobian_mixed). */
+enum { QSS_LU_FP64 = 0, QSS_LU_FP32_IR = 1, QSS_LU_MIXED = 2 };
 
 /* Per-cell outcome of qss_implicit_step. */
 enum {
@@ -122,6 +124,25 @@ int qss_wdot(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho, con
  * arrays; jac [nnz][ld] is required (nnz = (N+1)^2 for a dense artefact, see
  * qss_mech_jac_pattern), wdot [N][ld] and Tdot [ld] may be NULL (they are
  * computed anyway). */
+/* Mixed-precision form of qss_jacobian for the Newton iteration matrix
+ * (same arguments, layouts and outputs).  Everything the source term needs --
+ * Arrhenius exponentials, equilibrium constants, third bodies and falloff,
+ * the QSS solve of Eq. full_QSSsystem, the rates of progress -- is evaluated
+ * in FP64 by the operations of qss_jacobian, so wdot and Tdot are its FP64
+ * values (to within the reassociation the compiler may apply); the nodes only
+ * the Jacobian needs (the rate derivatives, dC_Q/dphi and the chain-rule
+ * products of Eq. JQSS) are evaluated in FP32 and stored as doubles.  Each
+ * entry's error is bounded to first order by 2^29 times the FP64 rounding
+ * bound of the same evaluation (the unit-roundoff ratio), about 1e-7 of the
+ * entry where its terms do not cancel.  The paper evaluates the Jacobian in
+ * FP64 throughout; this form serves implicit solvers, where J only shapes the
+ * Newton matrix and the FP64 residual fixes the solution.  Errors: as
+ * qss_jacobian; QSS_ERR_UNIMPLEMENTED if the artefact was built without the
+ * mixed-precision kernel (build option jac32). */
+int qss_jacobian_mixed(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
+                       const double* T, const double* Y, double* jac, double* wdot, double* Tdot,
+                       void* stream);
+
 int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
                  const double* T, const double* Y, double* jac, double* wdot, double* Tdot,
                  void* stream);
@@ -211,9 +232,12 @@ int qss_jacobian_host(qss_mech_t mech, int64_t ncells, const double* rho, const 
  * refine_tol relative (or max_refine sweeps); a cell whose FP32
  * factorisation meets a zero or non-finite pivot, or whose refinement turns
  * non-finite, is solved in FP64 for that iteration instead, so the mixed form
- * reports QSS_CELL_SINGULAR only where the FP64 form would.  Rates,
- * equilibrium constants, the QSS solve and the Newton residual stay FP64 in
- * both forms.
+ * reports QSS_CELL_SINGULAR only where the FP64 form would.  QSS_LU_MIXED
+ * solves as QSS_LU_FP32_IR with J from qss_jacobian_mixed (derivative terms
+ * in FP32): an inexact Newton iteration whose FP64 residual G fixes the root,
+ * so a converged cell meets the same stopping rule; it may take an iteration
+ * more.  Rates, equilibrium constants, the QSS solve and the Newton residual
+ * stay FP64 in every form.
  * T [ld] and Y [N][ld] are updated in place (device arrays); dt is a device
  * array [ld] (dt_stride = 1) or a single device value (dt_stride = 0).
  * iters and cell_status (device int32 [ld]) may be NULL.

@@ -20,6 +20,7 @@ QSS_ERRORS = {-1: "INVALID_ARG", -2: "MECH_FORMAT", -3: "CUDA", -4: "OOM", -5: "
               -6: "TIMEOUT", -7: "BUDGET", -8: "UNIMPLEMENTED"}
 QSS_LU_FP64 = 0
 QSS_LU_FP32_IR = 1
+QSS_LU_MIXED = 2
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -99,6 +100,7 @@ def lib():
                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         L.qss_wdot.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_jacobian.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.qss_jacobian_mixed.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.qss_mech_set_frontier_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.qss_jacobian_launches.argtypes = [_vp, _i64, ctypes.POINTER(_i64)]
         L.qss_mech_set_newton_bytes.argtypes = [_vp, ctypes.c_size_t]
@@ -188,6 +190,9 @@ class Mechanism:
         self.jac_nnz = nnz.value
         self.jac_row_ptr = [rp[i] for i in range(self.N + 2)]
         self.jac_col = [ci[i] for i in range(self.jac_nnz)]
+        # the artefact carries the mixed-precision Jacobian kernel (jac32)
+        with open(os.path.join(artefact_dir, "meta.txt")) as f:
+            self.has_jac32 = any(ln.split()[:2] == ["jac32", "1"] for ln in f)
 
     @classmethod
     def from_dict(cls, mech: dict, device: int = 0, **build_kw):
@@ -238,14 +243,16 @@ class Mechanism:
         return wdot, Tdot
 
     def jacobian(self, rho, T, Y, jac=None, wdot=None, Tdot=None, ncells=None, stream=None,
-                 want_rates=True):
+                 want_rates=True, mixed=False):
+        """qss_jacobian, or with mixed=True qss_jacobian_mixed (derivative
+        terms in FP32)."""
         nc, ld = self._check_state(rho, T, Y, ncells)
         jac = self._out(jac, (self.jac_nnz, ld), T)
         if want_rates:
             wdot = self._out(wdot, (self.N, ld), T)
             Tdot = self._out(Tdot, (ld,), T)
-        check(lib().qss_jacobian(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot),
-                                 _ptr(Tdot), _stream(stream)))
+        fn = lib().qss_jacobian_mixed if mixed else lib().qss_jacobian
+        check(fn(self.h, nc, ld, _ptr(rho), _ptr(T), _ptr(Y), _ptr(jac), _ptr(wdot), _ptr(Tdot), _stream(stream)))
         return jac, wdot, Tdot
 
     def jac_dense(self, jac):

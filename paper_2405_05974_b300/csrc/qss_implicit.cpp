@@ -87,7 +87,7 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
                         const qss_newton_opts* opts, qss_newton_opts* o) {
   if (!m) return fail(QSS_ERR_INVALID_ARG, "null mechanism");
   if (ncells < 0 || ld < ncells) return fail(QSS_ERR_INVALID_ARG, "bad sizes (ncells < 0 or ld < ncells)");
-  if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR)
+  if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR && precision != QSS_LU_MIXED)
     return fail(QSS_ERR_INVALID_ARG, "unknown precision");
   if (dt_stride != 0 && dt_stride != 1) return fail(QSS_ERR_INVALID_ARG, "dt_stride must be 0 or 1");
   *o = {20, 1e-12, 1e-20, 1e-10, 10, 1e-8, 0};
@@ -97,8 +97,10 @@ int check_implicit_args(qss_mech_s* m, int64_t ncells, int64_t ld, const double*
     return fail(QSS_ERR_INVALID_ARG, "bad Newton options");
   if (ncells == 0) return QSS_OK;
   if (!dt || !rho || !T || !Y) return fail(QSS_ERR_INVALID_ARG, "null array");
-  if (!m->f_newton[precision] || !m->f_newton_setup || !m->f_newton_finish)
+  if (!m->f_newton[lu_kind(precision)] || !m->f_newton_setup || !m->f_newton_finish)
     return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no Newton kernels");
+  if (precision == QSS_LU_MIXED && !m->jac32)
+    return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no mixed-precision Jacobian (jac32)");
   return QSS_OK;
 }
 
@@ -161,7 +163,7 @@ int implicit_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* dt,
       const int* nc = NACT + cur;
       int* nn = NACT + nxt;
       if ((rc = jac_launch(m, cells, sld, nullptr, nullptr, nullptr, M64, F, F + (size_t)m->N * S, PHI,
-                           lc, nc, nn, FR, (int64_t)S, st)))
+                           lc, nc, nn, FR, (int64_t)S, st, precision == QSS_LU_MIXED)))
         return rc;
       int* l2 = LIST[nxt];
       if (!reuse) {

@@ -15,7 +15,10 @@ struct qss_mech_s {
   CUmodule mod = nullptr;          // jac.cubin: analytic Jacobian kernel
   CUmodule mod_wdot = nullptr;     // wdot.cubin: source term, FD Jacobian
   CUmodule mod_newton = nullptr;   // newton.cubin: implicit-step kernels
+  CUmodule mod_jac32 = nullptr;    // jac32.cubin: mixed-precision Jacobian (artefacts built with jac32)
   CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;   // f_wdot also has a list mode
+  CUfunction f_jac32 = nullptr;    // qss_jac32_kernel (single-kernel artefacts built with jac32)
+  int jac32 = 0;                   // meta.txt: the artefact carries the mixed-precision Jacobian
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   CUfunction f_integ[4] = {nullptr, nullptr, nullptr, nullptr};   // init, gather, accept, finish
@@ -27,6 +30,11 @@ struct qss_mech_s {
   CUfunction f_prefix = nullptr;
   std::vector<CUmodule> mod_group;
   std::vector<CUfunction> f_group;
+  // their mixed-precision forms (jac32_prefix.cubin, jac32_g<i>.cubin)
+  CUmodule mod_prefix32 = nullptr;
+  CUfunction f_prefix32 = nullptr;
+  std::vector<CUmodule> mod_group32;
+  std::vector<CUfunction> f_group32;
   // frontier scratch of the device-array path; fr_done orders its reuse
   // across streams (recorded after each call's last group kernel)
   CUdeviceptr fr_scratch = 0;
@@ -62,6 +70,9 @@ struct qss_mech_s {
 };
 
 namespace qss {
+// The Newton update kernel of a precision (the mixed form factors like
+// QSS_LU_FP32_IR; only its Jacobian kernel differs)
+inline int lu_kind(int precision) { return precision == QSS_LU_MIXED ? QSS_LU_FP32_IR : precision; }
 extern thread_local std::string g_err;
 int fail(int code, const std::string& msg);
 int cu_fail(CUresult r, const char* what);
@@ -69,7 +80,8 @@ std::string lib_dir();
 int ctx_for_device(int device, CUdevice* dev, CUcontext* ctx);
 int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** args,
                  CUstream stream, unsigned shmem);
-// a Newton update kernel (precision 0 FP64, 1 FP32-IR) over a list of up to
+// a Newton update kernel (precision 0 FP64, 1 FP32-IR, 2 mixed: the FP32-IR
+// update) over a list of up to
 // ncells cells: one warp per cell as far as the device holds such warps at
 // once, the warps striding over the list beyond that
 int launch_update(qss_mech_s* m, int precision, int64_t ncells, void** args, CUstream stream);
@@ -77,11 +89,12 @@ int launch_update(qss_mech_s* m, int precision, int64_t ncells, void** args, CUs
 // (rho, T, Y) with leading dimension ld, J SoA with ld; or, in list mode (phi,
 // list, nact given), of the listed cells with J cell-contiguous.  fr/fld: the
 // frontier scratch of a partitioned Jacobian (fld >= ncells; unused
-// otherwise).
+// otherwise).  mixed: the mixed-precision Jacobian kernel (the caller has
+// checked that the artefact has it).
 int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
                const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
                const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
-               CUstream s);
+               CUstream s, bool mixed = false);
 bool jac_pattern_ok(qss_mech_s* m);
 // The chunk (in cells) for at most `cap` cells of scratch: a multiple of the
 // Jacobian kernel's wave when at least one wave fits, else of 32 (>= 32).

@@ -73,6 +73,7 @@ int launch_cells(qss_mech_s* m, CUfunction f, int64_t ncells, int block, void** 
 
 int launch_update(qss_mech_s* m, int precision, int64_t ncells, void** args, CUstream stream) {
   if (ncells == 0) return QSS_OK;
+  precision = lu_kind(precision);
   const int block = m->upd_threads[precision], warps = std::max(block / 32, 1);
   // one warp per listed cell, capped at the blocks that are resident at once
   // (a small batch then spreads over every SM instead of queueing 32 cells
@@ -96,9 +97,14 @@ int64_t chunk_cells(const qss_mech_s* m, int64_t cap) {
 int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
                const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
                const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
-               CUstream s) {
+               CUstream s, bool mixed) {
   long long nc = ncells, l = ld;
   int rc;
+  if (mixed && !m->jac32) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no mixed-precision Jacobian (jac32)");
+  if (mixed && m->jac_parts < 2) {
+    void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
+    return launch_cells(m, m->f_jac32, ncells, m->block, args, s, 0);
+  }
   if (m->jac_parts < 2) {
     void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
     return launch_cells(m, m->f_jac, ncells, m->block, args, s, m->jac_smem);
@@ -106,11 +112,11 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   if (!fr || fld < ncells) return fail(QSS_ERR_INVALID_ARG, "frontier scratch too small");
   long long fl = fld;
   void* pa[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot, &fr, &fl, &phi, &list, &nact, &nact_next};
-  if ((rc = launch_cells(m, m->f_prefix, ncells, m->block, pa, s, 0))) return rc;
+  if ((rc = launch_cells(m, mixed ? m->f_prefix32 : m->f_prefix, ncells, m->block, pa, s, 0))) return rc;
   const double* frc = fr;
   for (int i = 0; i < m->jac_parts; ++i) {
     void* ga[] = {&nc, &frc, &fl, &jac, &l, &nact};
-    if ((rc = launch_cells(m, m->f_group[i], ncells, m->block, ga, s, 0))) return rc;
+    if ((rc = launch_cells(m, mixed ? m->f_group32[i] : m->f_group[i], ncells, m->block, ga, s, 0))) return rc;
   }
   return QSS_OK;
 }
@@ -181,6 +187,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "frontier") ls >> m->frontier;
     else if (key == "jac_nnz") ls >> m->jac_nnz;
     else if (key == "smem_slots") ls >> m->smem_slots;
+    else if (key == "jac32") ls >> m->jac32;
     else if (key == "jac_row_ptr" || key == "jac_col") {
       std::vector<int32_t>& v = key == "jac_col" ? m->jac_col : m->jac_row_ptr;
       int32_t x;
@@ -193,6 +200,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
       m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
       m->smem_slots < 0 || m->smem_slots > 1024 || (m->smem_slots > 0 && m->jac_parts >= 2) ||
+      m->jac32 < 0 || m->jac32 > 1 ||
       !jac_pattern_ok(m)) {
     delete m;
     return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
@@ -212,8 +220,17 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     for (int i = 0; i < m->jac_parts; ++i)
       need.push_back({&m->mod_group[i], "jac_g" + std::to_string(i) + ".cubin", "qss_jac_group_kernel",
                       &m->f_group[i]});
+    if (m->jac32) {
+      m->mod_group32.assign(m->jac_parts, nullptr);
+      m->f_group32.assign(m->jac_parts, nullptr);
+      need.push_back({&m->mod_prefix32, "jac32_prefix.cubin", "qss_jac_prefix_kernel", &m->f_prefix32});
+      for (int i = 0; i < m->jac_parts; ++i)
+        need.push_back({&m->mod_group32[i], "jac32_g" + std::to_string(i) + ".cubin", "qss_jac_group_kernel",
+                        &m->f_group32[i]});
+    }
   } else {
     need.push_back({&m->mod, "jac.cubin", "qss_jac_kernel", &m->f_jac});
+    if (m->jac32) need.push_back({&m->mod_jac32, "jac32.cubin", "qss_jac32_kernel", &m->f_jac32});
   }
   need.push_back({&m->mod_wdot, "wdot.cubin", "qss_wdot_kernel", &m->f_wdot});
   need.push_back({&m->mod_wdot, "wdot.cubin", "qss_jac_fd_kernel", &m->f_jac_fd});
@@ -229,9 +246,13 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     }
     if (code) {
       if (m->mod) drv().cuModuleUnload(m->mod);
+      if (m->mod_jac32) drv().cuModuleUnload(m->mod_jac32);
       if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
       if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
       for (CUmodule g : m->mod_group)
+        if (g) drv().cuModuleUnload(g);
+      if (m->mod_prefix32) drv().cuModuleUnload(m->mod_prefix32);
+      for (CUmodule g : m->mod_group32)
         if (g) drv().cuModuleUnload(g);
       drv().cuDevicePrimaryCtxRelease(m->dev);
       delete m;
@@ -311,7 +332,11 @@ void qss_mech_free(qss_mech_t m) {
   if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
   for (CUmodule g : m->mod_group)
     if (g) drv().cuModuleUnload(g);
+  if (m->mod_prefix32) drv().cuModuleUnload(m->mod_prefix32);
+  for (CUmodule g : m->mod_group32)
+    if (g) drv().cuModuleUnload(g);
   if (m->mod) drv().cuModuleUnload(m->mod);
+  if (m->mod_jac32) drv().cuModuleUnload(m->mod_jac32);
   if (m->mod_wdot) drv().cuModuleUnload(m->mod_wdot);
   if (m->mod_newton) drv().cuModuleUnload(m->mod_newton);
   drv().cuDevicePrimaryCtxRelease(m->dev);
@@ -349,16 +374,17 @@ int qss_wdot(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const 
   return launch_cells(m, m->f_wdot, ncells, m->block, args, (CUstream)stream, 0);
 }
 
-int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
-                 const double* Y, double* jac, double* wdot, double* Tdot, void* stream) {
+static int jacobian_impl(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                         const double* Y, double* jac, double* wdot, double* Tdot, void* stream, bool mixed) {
   int rc = check_cells(m, ncells, ld);
   if (rc) return rc;
+  if (mixed && !m->jac32) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no mixed-precision Jacobian (jac32)");
   if (ncells == 0) return QSS_OK;
   if (!rho || !T || !Y || !jac) return fail(QSS_ERR_INVALID_ARG, "null array");
   CUstream s = (CUstream)stream;
   if (m->jac_parts < 2)
     return jac_launch(m, ncells, ld, rho, T, Y, jac, wdot, Tdot, nullptr, nullptr, nullptr, nullptr,
-                      nullptr, 0, s);
+                      nullptr, 0, s, mixed);
   // partitioned: chunks of cells through the handle's frontier scratch (at
   // most fr_budget bytes), its reuse ordered after the previous call by an
   // event
@@ -397,11 +423,21 @@ int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, co
     const int64_t cs = std::min<int64_t>(want, ncells - c0);
     if ((rc = jac_launch(m, cs, ld, rho + c0, T + c0, Y + c0, jac + c0, wdot ? wdot + c0 : nullptr,
                          Tdot ? Tdot + c0 : nullptr, nullptr, nullptr, nullptr, nullptr, fr,
-                         m->fr_cells, s)))
+                         m->fr_cells, s, mixed)))
       return rc;
   }
   CU_TRY(drv().cuEventRecord(m->fr_done, s));
   return QSS_OK;
+}
+
+int qss_jacobian(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                 const double* Y, double* jac, double* wdot, double* Tdot, void* stream) {
+  return jacobian_impl(m, ncells, ld, rho, T, Y, jac, wdot, Tdot, stream, false);
+}
+
+int qss_jacobian_mixed(qss_mech_t m, int64_t ncells, int64_t ld, const double* rho, const double* T,
+                       const double* Y, double* jac, double* wdot, double* Tdot, void* stream) {
+  return jacobian_impl(m, ncells, ld, rho, T, Y, jac, wdot, Tdot, stream, true);
 }
 
 int qss_debug_status(qss_mech_t m, int* status) {

@@ -497,11 +497,13 @@ int qss_serve_submit(qss_server_t s, qss_mech_t mech, int64_t ncells, const doub
                      uint64_t* req_id) {
   if (!s || !mech || !req_id) return fail(QSS_ERR_INVALID_ARG, "null argument");
   if (ncells <= 0 || !rho || !T || !Y) return fail(QSS_ERR_INVALID_ARG, "bad request arrays");
-  if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR)
+  if (precision != QSS_LU_FP64 && precision != QSS_LU_FP32_IR && precision != QSS_LU_MIXED)
     return fail(QSS_ERR_INVALID_ARG, "unknown precision");
   if (!(dt > 0)) return fail(QSS_ERR_INVALID_ARG, "dt must be positive");
   if (mech->ctx != s->ctx) return fail(QSS_ERR_INVALID_ARG, "mechanism loaded on another device");
-  if (!mech->f_newton[precision]) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no Newton kernels");
+  if (!mech->f_newton[lu_kind(precision)]) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no Newton kernels");
+  if (precision == QSS_LU_MIXED && !mech->jac32)
+    return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no mixed-precision Jacobian (jac32)");
   size_t soff;
   if (batch_bytes(mech, ncells, precision, s->newton.jac_reuse != 0, &soff) > s->arena->size() ||
       ncells > s->max_batch_cells) {

@@ -35,7 +35,8 @@ DEFAULT_ROOT = os.path.join(REPO, "build", "mech")
 NVCC = os.environ.get("QSS_NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc", "qss_cells.cuh",
-             "qss_jac_kernel.cuh", "qss_jac_parts.cuh", "qss_wdot_kernels.cuh", "qss_newton.cuh"]
+             "qss_jac_kernel.cuh", "qss_jac_parts.cuh", "qss_wdot_kernels.cuh", "qss_newton.cuh",
+             "qss_convert.h", "qss_jac32_kernel.cuh"]
 ARTEFACT_FILES = ("wdot.cubin", "newton.cubin", "meta.txt", "meta.json")
 COMPILER_VERSION = "1"
 
@@ -125,7 +126,8 @@ def _write_index(root: str, fast: str, name: str):
         os.replace(tmp, os.path.join(root, "index.json"))
 
 
-def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas) -> tuple:
+def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
+             jac32=False) -> tuple:
     """The build options other than block and defines, as index-key parts."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
@@ -142,16 +144,22 @@ def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_ord
         variant += (f"smem{int(smem_slots)}",)
     for o in ptxas:
         variant += (f"ptxas:{o}",)
+    if jac32:
+        if replace_nop > 0 or (jac_variant, t_column) != ("exact", "analytic"):
+            raise ValueError("jac32 is built for the exact Jacobian with the analytic T column")
+        variant += ("jac32",)
     return variant
 
 
 def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
                   t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
-                  jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0, ptxas=()):
+                  jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0, ptxas=(),
+                  jac32: bool = False):
     """The directory of an artefact already built with these options for the
     current templates, or None (never compiles)."""
     root = root or DEFAULT_ROOT
-    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas)
+    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
+                       jac32)
     name = _read_index(root).get(artefact_key(mech, block, tuple(defines) + variant))
     return os.path.join(root, name) if name and _complete(os.path.join(root, name)) else None
 
@@ -188,7 +196,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
                     jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0,
-                    ptxas=()) -> str:
+                    ptxas=(), jac32: bool = False) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -205,8 +213,11 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     as it is final); ``smem_slots`` > 0 keeps that many of the single Jacobian
     kernel's most-reloaded values in shared memory (dynamic, per thread);
     ``ptxas`` are extra ptxas options (``"regUsageLevel=0"`` is passed as
-    ``-Xptxas -regUsageLevel=0``)."""
-    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas)
+    ``-Xptxas -regUsageLevel=0``); ``jac32`` also builds ``jac32.cubin``, the
+    mixed-precision Jacobian kernel (derivative terms in FP32,
+    ``emit.emit_jac32_source``) of the mixed-precision implicit step."""
+    variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
+                       jac32)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -229,6 +240,16 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         parts["mech_jac_prefix.inc"] = prefix_src
         for i, gsrc in enumerate(group_srcs):
             parts[f"mech_jac_g{i}.inc"] = gsrc
+    if jac32 and jac_parts < 2:
+        src32, meta32 = emit.emit_jac32_source(model, jac_format)
+        parts["mech_jac32.inc"] = src32
+        meta.update(meta32)
+    elif jac32:
+        p32, g32, pm32 = emit.emit_partitioned_source(model, int(jac_parts), jac_format, mixed=True)
+        parts["mech_jac32_prefix.inc"] = p32
+        for i, gsrc in enumerate(g32):
+            parts[f"mech_jac32_g{i}.inc"] = gsrc
+        meta.update({"ops_prefix32": pm32["ops_prefix"], "ops_groups32": pm32["ops_groups"]})
     hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES}
     flags = [f"-DQSS_BLOCK={block}", *[f"-D{d}" for d in defines]]
     for o in ptxas:
@@ -243,7 +264,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     if not force and _complete(out):
         _write_index(root, fast, art_name)
         return out
-    tmp = out + ".tmp%d" % os.getpid()
+    tmp = out + ".tmp%d_%d" % (os.getpid(), threading.get_ident())   # one per concurrent build
     os.makedirs(tmp, exist_ok=True)
     for pname, text in parts.items():
         with open(os.path.join(tmp, pname), "w") as f:
@@ -266,6 +287,21 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         units["jac"] = (pre + '#include "mech_jac.inc"\n#include "qss_jac_kernel.cuh"\n',
                         {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"],
                          "qss_jac_kernel.cuh": hdr["qss_jac_kernel.cuh"]})
+    if jac32 and jac_parts >= 2:
+        jp = {"qss_jac_parts.cuh": hdr["qss_jac_parts.cuh"], "qss_convert.h": hdr["qss_convert.h"]}
+        cv = '#include "qss_convert.h"\n'
+        units["jac32_prefix"] = (pre + cv + '#include "mech_jac32_prefix.inc"\n#define QSS_JAC_PREFIX\n'
+                                 '#include "qss_jac_parts.cuh"\n',
+                                 {**common, **cells, **jp, "mech_jac32_prefix.inc": parts["mech_jac32_prefix.inc"]})
+        for i in range(int(jac_parts)):
+            nm = f"mech_jac32_g{i}.inc"
+            units[f"jac32_g{i}"] = (pre + cv + f'#include "{nm}"\n#define QSS_JAC_GROUP\n#include "qss_jac_parts.cuh"\n',
+                                    {**common, **cells, **jp, nm: parts[nm]})
+    elif jac32:
+        units["jac32"] = (pre + '#include "qss_convert.h"\n#include "mech_jac32.inc"\n#include "qss_jac32_kernel.cuh"\n',
+                          {**common, **cells, "qss_convert.h": hdr["qss_convert.h"],
+                           "mech_jac32.inc": parts["mech_jac32.inc"],
+                           "qss_jac32_kernel.cuh": hdr["qss_jac32_kernel.cuh"]})
     units.update({
         "wdot": (pre + '#include "mech_wdot.inc"\n#include "qss_wdot_kernels.cuh"\n',
                  {**common, **cells, "mech_wdot.inc": parts["mech_wdot.inc"],
@@ -289,7 +325,11 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     meta["kernels"] = {}
     for name in units:
         for k, v in _parse_ptxas(logs[name]).items():
-            meta["kernels"][f"{k}[{name[5:]}]" if name.startswith("jac_g") else k] = v
+            if name.startswith("jac_g"):
+                k = f"{k}[{name[5:]}]"
+            elif name.startswith("jac32_"):
+                k = f"{k}[{name}]"
+            meta["kernels"][k] = v
     meta["block"] = block
     meta["defines"] = list(defines)
     meta["ptxas"] = list(ptxas)
@@ -305,6 +345,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         if jac_parts >= 2:
             f.write(f"jac_parts {int(jac_parts)}\nfrontier {meta['frontier']}\n")
         f.write(f"jac_nnz {meta['jac_stored']}\n")
+        if jac32:
+            f.write("jac32 1\n")
         if meta.get("smem_slots", 0) > 0:   # slots the emitted code uses (at most the requested)
             f.write(f"smem_slots {int(meta['smem_slots'])}\n")
         if jac_format != "dense":

@@ -32,6 +32,16 @@ def _lit(v: float) -> str:
     return r
 
 
+def _lit32(v: float) -> str:
+    """A single-precision literal of v (rounded to the nearest float)."""
+    import numpy as np
+    with np.errstate(over="ignore"):
+        f = float(np.float32(v))
+    if f != f or f in (float("inf"), float("-inf")):
+        raise ValueError(f"constant {v} has no single-precision value")
+    return _lit(f) + "f"
+
+
 class Emitter:
     def __init__(self, model, input_names: Dict[int, str], leaves: Dict[int, str] = None,
                  replace_nop: int = 0, emit_order: str = "first_use"):
@@ -67,9 +77,16 @@ class Emitter:
             return [self._resolve(a[0])]
         return [self._resolve(x) for x in a]
 
-    def emit(self, outputs: List[Tuple[str, int]], indent="  "):
+    def emit(self, outputs: List[Tuple[str, int]], indent="  ", fp64_outputs: int = None):
         """outputs: list of (store-statement format with {v}, node).  Returns
-        (code lines, op counts)."""
+        (code lines, op counts).
+
+        fp64_outputs = k (mixed precision): the nodes the first k outputs
+        need are computed in FP64 as usual; every other node (the part only
+        the later outputs need: the Jacobian's derivative terms) is computed
+        in FP32 (`const float`, fmaf), its FP64 operands converted once each
+        (qss_f32, at their first FP32 use) and its stored results widened
+        back (qss_f64)."""
         g = self.g
         roots = [self._resolve(n) for _, n in outputs]
         # needed set and reference counts
@@ -86,6 +103,20 @@ class Emitter:
                 stack.append(c)
         for r in roots:
             refc[r] += 1
+        # mixed precision: FP32 for the nodes that the FP64 outputs do not need
+        f32 = set()
+        if fp64_outputs is not None:
+            if self.replace_nop or self.smem_slot:
+                raise ValueError("mixed precision is emitted without replacement or shared-memory slots")
+            val = set()
+            stack = list(roots[:fp64_outputs])
+            while stack:
+                n = stack.pop()
+                if n in val:
+                    continue
+                val.add(n)
+                stack.extend(self._children(n))
+            f32 = seen - val
         # which nodes are folded into their user (fma, negation, constants)
         inline = set()
         for n in seen:
@@ -148,65 +179,98 @@ class Emitter:
         names: Dict[int, str] = {}
         lines: List[str] = []
         counts = Counter()
+        conv = {}      # FP64 value -> the name of its FP32 copy (mixed precision)
+        pending = []   # conversions to emit before the next line
 
-        def ref(n):
+        def as32(x, key):
+            if key not in conv:
+                conv[key] = f"s{len(conv)}"
+                pending.append(f"{indent}const float {conv[key]} = qss_f32({x});")
+                counts["cvt_f32"] += 1
+            return conv[key]
+
+        def is32(n):
+            n = self._resolve(n)
+            op = g.op[n]
+            if n in self.leaves or op in (CONST, VAR, LT):
+                return False
+            if op in (NEG, FACT):
+                return is32(g.args[n][0])
+            return n in f32
+
+        def ref(n, f=False):
+            """C expression of node n's value; f: in an FP32 expression."""
             n = self._resolve(n)
             op = g.op[n]
             if n in self.leaves:
-                return self.leaves[n]
+                return as32(self.leaves[n], ("leaf", n)) if f else self.leaves[n]
             if op == CONST:
                 v = g.val[n]
-                return _lit(v) if v >= 0 else f"({_lit(v)})"
+                lit = _lit32(v) if f else _lit(v)
+                return lit if v >= 0 else f"({lit})"
             if op == VAR:
                 if n not in self.inputs:
                     raise KeyError(f"unbound variable {g.name[n]}")
-                return self.inputs[n]
+                return as32(self.inputs[n], n) if f else self.inputs[n]
             if op == NEG:
-                return f"(-{ref(g.args[n][0])})"
+                return f"(-{ref(g.args[n][0], f)})"
             if op == FACT:
-                return ref(g.args[n][0])
+                return ref(g.args[n][0], f)
             if op == LT:
-                return f"({ref(g.args[n][0])} < {_lit(g.args[n][1])})"
+                c = self._resolve(g.args[n][0])
+                if is32(c):
+                    return f"({ref(c, True)} < {_lit32(g.args[n][1])})"
+                return f"({ref(c)} < {_lit(g.args[n][1])})"
             if n in replaced:
                 return f"({expr_of(n)})"
             if n in self.smem_slot:
                 return f"qss_sm[{self.smem_slot[n]} * QSS_BLOCK]"
-            return names[n]
+            if n in f32:
+                if not f:
+                    raise AssertionError("an FP32 value used by an FP64 expression")
+                return names[n]
+            return as32(names[n], n) if f else names[n]
+
+        def out_ref(n):
+            return f"qss_f64({ref(n, True)})" if is32(n) else ref(n)
 
         def expr_of(n):
             op = g.op[n]
+            f = n in f32
+            k = "f32_" if f else ""
             a = [self._resolve(x) for x in g.args[n]]
             if n in fma_of:
                 which, mnode = fma_of[n]
                 other = a[1 - which]
                 ma, mb = [self._resolve(x) for x in g.args[mnode]]
-                counts["fma"] += 1
+                counts[k + "fma"] += 1
+                fn = "fmaf" if f else "fma"
                 if op == ADD:
-                    return f"fma({ref(ma)}, {ref(mb)}, {ref(other)})"
+                    return f"{fn}({ref(ma, f)}, {ref(mb, f)}, {ref(other, f)})"
                 if which == 1:   # other - ma*mb
-                    return f"fma(-{ref(ma)}, {ref(mb)}, {ref(other)})"
-                return f"fma({ref(ma)}, {ref(mb)}, -{ref(other)})"
+                    return f"{fn}(-{ref(ma, f)}, {ref(mb, f)}, {ref(other, f)})"
+                return f"{fn}({ref(ma, f)}, {ref(mb, f)}, -{ref(other, f)})"
             if op == ADD:
-                counts["add"] += 1
-                return f"{ref(a[0])} + {ref(a[1])}"
+                counts[k + "add"] += 1
+                return f"{ref(a[0], f)} + {ref(a[1], f)}"
             if op == SUB:
-                counts["add"] += 1
-                return f"{ref(a[0])} - {ref(a[1])}"
+                counts[k + "add"] += 1
+                return f"{ref(a[0], f)} - {ref(a[1], f)}"
             if op == MUL:
-                counts["mul"] += 1
-                return f"{ref(a[0])} * {ref(a[1])}"
+                counts[k + "mul"] += 1
+                return f"{ref(a[0], f)} * {ref(a[1], f)}"
             if op == RECIP:
-                counts["rcp"] += 1
-                return f"qss_rcp({ref(a[0])})"
+                counts[k + "rcp"] += 1
+                return f"__frcp_rn({ref(a[0], True)})" if f else f"qss_rcp({ref(a[0])})"
             if op == EXP:
-                counts["exp"] += 1
-                return f"qss_exp({ref(a[0])})"
+                counts[k + "exp"] += 1
+                return f"expf({ref(a[0], True)})" if f else f"qss_exp({ref(a[0])})"
             if op == LOG:
-                counts["log"] += 1
-                return f"qss_log({ref(a[0])})"
+                counts[k + "log"] += 1
+                return f"logf({ref(a[0], True)})" if f else f"qss_log({ref(a[0])})"
             if op == SELECT:
-                counts["select"] += 1
-                return f"({ref(g.args[n][0])} ? {ref(a[1])} : {ref(a[2])})"
+                counts[k + "select"] += 1
+                return f"({ref(g.args[n][0])} ? {ref(a[1], f)} : {ref(a[2], f)})"
             raise ValueError(op)
 
         done = set()
@@ -227,20 +291,29 @@ class Emitter:
                 if n in inline or n in replaced:
                     continue
                 names[n] = f"t{n}"
+                e = expr_of(n)
+                lines.extend(pending)
+                pending.clear()
                 if n in self.smem_slot:
-                    lines.append(f"{indent}qss_sm[{self.smem_slot[n]} * QSS_BLOCK] = {expr_of(n)};")
+                    lines.append(f"{indent}qss_sm[{self.smem_slot[n]} * QSS_BLOCK] = {e};")
                 else:
-                    lines.append(f"{indent}const double t{n} = {expr_of(n)};")
+                    lines.append(f"{indent}const {'float' if n in f32 else 'double'} t{n} = {e};")
+
+        def store(fmt, root):
+            v = out_ref(root)
+            lines.extend(pending)
+            pending.clear()
+            lines.append(indent + fmt.format(v=v))
 
         if self.emit_order == "first_use":
             for (fmt, node), root in zip(outputs, roots):
                 visit(root)
-                lines.append(indent + fmt.format(v=ref(root)))
+                store(fmt, root)
         else:
             for root in roots:
                 visit(root)
             for (fmt, node), root in zip(outputs, roots):
-                lines.append(indent + fmt.format(v=ref(root)))
+                store(fmt, root)
         # algorithmic count: each DAG operation once, independent of fusion
         dag = Counter()
         for n in seen:
@@ -431,6 +504,47 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
     return src, meta
 
 
+def emit_jac32_source(model, jac_format: str = "dense") -> Tuple[str, dict]:
+    """The mixed-precision Jacobian device function
+
+        qss_eval_jac32(C, T, wdot, Tdot, jac, wstride, jstride)
+
+    with qss_eval_jac's interface.  Everything wdot and Tdot need -- state,
+    thermo, Arrhenius exponentials, equilibrium constants, third bodies and
+    falloff, the QSS solve, the rates of progress -- is computed in FP64 by
+    the operations qss_eval_jac uses, so wdot and Tdot are its values; the
+    nodes only the Jacobian needs (the derivatives of the rates, dC_Q/dphi,
+    the chain-rule products G + P X) are computed in FP32 and stored widened
+    to FP64.  For the Newton iteration matrix of the mixed-precision implicit
+    step, whose residual stays FP64."""
+    ir = model.ir
+    N = ir.N
+    n = N + 1
+    pos, _, _ = jac_layout(model, jac_format)
+    if model.fd_vars is not None:
+        raise ValueError("the mixed-precision Jacobian needs the analytic temperature column")
+    inputs = {model.C[k]: f"C{k}" for k in range(N)}
+    inputs[model.T] = "T"
+    out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
+    out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
+    out_j = []
+    for c in range(n):
+        for i in range(n):
+            if (i, c) in pos:
+                out_j.append((f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]))
+    em = Emitter(model, inputs)
+    body, cnt = em.emit(out_w + out_t + out_j, indent="  ", fp64_outputs=len(out_w) + len(out_t))
+    unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
+    src = "\n".join([
+        "__device__ __forceinline__ void qss_eval_jac32(const double* __restrict__ C, const double T,",
+        "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
+        "    const long long wstride, const long long jstride) {",
+        *unpack, *body, "}", ""])
+    meta = {"ops_jac32": dict(cnt), "flops_jac32": algorithmic_flops(cnt),
+            "fp64_instr_jac32": fp64_instructions(cnt)}
+    return src, meta
+
+
 # ---------------------------------------------------------------------------
 # Partitioned Jacobian: a shared prefix kernel and K column-group kernels
 # ---------------------------------------------------------------------------
@@ -547,12 +661,16 @@ def partition_jacobian(model, K: int, split_t: bool = True):
     return groups, sorted(frontier), needs
 
 
-def emit_partitioned_source(model, K: int, jac_format: str = "dense"):
+def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: bool = False):
     """Sources of the partitioned Jacobian: the prefix device function
     qss_jac_prefix(C, T, wdot, Tdot, wstride, fr, fstride) and, per group,
     qss_jac_group(fr, fstride, jac, jstride).  The frontier array fr holds,
     per cell, C_1..C_N and T in slots 0..N, then the prefix values the groups
-    read (slot N + 1 + i for the i-th frontier node)."""
+    read (slot N + 1 + i for the i-th frontier node).  mixed: the
+    mixed-precision form (emit_jac32_source's split): the prefix computes
+    what wdot and Tdot need in FP64 and its other values in FP32 (stored to
+    the FP64 frontier widened); the group kernels, whose nodes wdot and Tdot
+    never need, compute in FP32 from the frontier values narrowed."""
     ir = model.ir
     N = ir.N
     n = N + 1
@@ -572,7 +690,10 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense"):
     out_w = [(f"if (wdot) wdot[{i} * wstride] = {{v}};", model.wdot[i]) for i in range(N)]
     out_t = [("if (Tdot) Tdot[0] = {v};", model.Tdot)]
     out_f = [(f"fr[{slot[x]} * fstride] = {{v}};", x) for x in frontier]
-    body_p, cnt_p = Emitter(model, inputs).emit(out_w + out_t + out_f, indent="  ")
+    if mixed and model.fd_vars is not None:
+        raise ValueError("the mixed-precision Jacobian needs the analytic temperature column")
+    body_p, cnt_p = Emitter(model, inputs).emit(out_w + out_t + out_f, indent="  ",
+                                                fp64_outputs=(len(out_w) + len(out_t)) if mixed else None)
     unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
     store_state = [f"  fr[{k} * fstride] = C{k};" for k in range(N)] + [f"  fr[{N} * fstride] = T;"]
     prefix = "\n".join([
@@ -585,7 +706,7 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense"):
         leaves = {x: f"F{slot[x]}" for x in needs[gi]}
         out_j = [(f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries
                  if (i, c) in pos]
-        body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ")
+        body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ", fp64_outputs=0 if mixed else None)
         loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
         loads += [f"  const double T = fr[{N} * fstride];"]
         # each frontier value is loaded just before its first use: loaded all

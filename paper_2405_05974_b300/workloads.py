@@ -51,6 +51,12 @@ BUILD_OPTIONS = {"large": {"jac_parts": 4}}
 
 def build_options(key: str) -> dict:
     return dict(BUILD_OPTIONS.get(key, {}))
+
+
+# workloads whose artefacts carry the mixed-precision Jacobian kernels
+# (build option jac32: one kernel, or the prefix and column groups of a
+# partitioned Jacobian)
+MIXED_JACOBIAN = ("tiny", "hydrocarbon", "large")
 IMPLICIT_DT = 1.0e-6
 # A second implicit-step size at which plain Newton from the initial state
 # converges in >= 95 % of the hydrocarbon cells (oracle: 96.6 % at 1e-11 s,

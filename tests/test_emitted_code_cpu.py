@@ -139,3 +139,96 @@ def test_emission_orders_emit_the_same_statements(key):
     first_store = min(i for i, ln in enumerate(lb) if not ln.startswith("const double t"))
     assert all(not ln.startswith("const double t") for ln in lb[first_store:])
     assert la != lb
+
+
+_SHIM32 = r"""
+#include <math.h>
+#include "qss_convert.h"
+static inline float __frcp_rn(float x) { return 1.0f / x; }
+using std::fmaf;
+"""
+
+_DRIVER32 = _DRIVER.replace("qss_eval_jac(", "qss_eval_jac32(")
+
+
+@pytest.mark.parametrize("key", ["tiny", "hydrocarbon"])
+def test_mixed_precision_jacobian_within_fp32_bound(key):
+    """The mixed-precision Jacobian (derivative terms in FP32, the source
+    term in FP64), compiled on the CPU with the kernels' own bit-pattern
+    conversions: wdot and Tdot pass the FP64 gate, and every Jacobian entry
+    is within 2^29 (= u_32 / u_64) times the oracle's FP64 running-error
+    bound (plus the 1e-20 floor), i.e. within the first-order rounding
+    bound of the same evaluation carried out entirely in FP32."""
+    from paper_2405_05974_b300.qssc.build import CSRC
+    model = _model(key)
+    src, meta = emit.emit_mechanism_source(model)
+    s32, m32 = emit.emit_jac32_source(model)
+    iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
+    d = tempfile.mkdtemp(prefix="qss_emit32_")
+    cpp = os.path.join(d, "gen.cpp")
+    with open(cpp, "w") as f:
+        f.write(_SHIM + _SHIM32 + src[:iw] + s32 + _DRIVER32)
+    so = os.path.join(d, "gen.so")
+    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    p = ctypes.POINTER(ctypes.c_double)
+    L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
+    m = workloads.mechanism(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], 256)
+    om = oracle.OracleMech(m)
+    n = meta["N"] + 1
+    w, td, J = _run(L, om.conc(rho, Y), T, n * n)
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    assert_gate("wdot", w, ref["wdot"], eb["wdot"])
+    assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
+    err = np.abs(J - ref["jac"])
+    assert np.all(np.isfinite(J))
+    assert np.all(err <= 2.0 ** 29 * eb["jac"] + 1e-20), float(np.max(err / (2.0 ** 29 * eb["jac"] + 1e-20)))
+    # the FP64 part is the source term's: the same FP64 operation count
+    assert m32["fp64_instr_jac32"] == meta["fp64_instr_wdot"]
+    assert m32["flops_jac32"] == meta["flops_jac"]
+
+
+@pytest.mark.parametrize("key,K", [("tiny", 2), ("hydrocarbon", 4)])
+def test_partitioned_mixed_precision_jacobian_within_fp32_bound(key, K):
+    """The partitioned form of the mixed-precision Jacobian (prefix kernel in
+    FP64 for the source term and FP32 for its shared derivative values, the
+    column groups in FP32 from the narrowed frontier), compiled on the CPU:
+    the same FP32 bound as the single function, and the same source term."""
+    from paper_2405_05974_b300.qssc.build import CSRC
+    model = _model(key)
+    src, meta = emit.emit_mechanism_source(model)
+    prefix, groups, pmeta = emit.emit_partitioned_source(model, K, mixed=True)
+    n = meta["N"] + 1
+    nfr = pmeta["frontier"]
+    iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
+    body = src[:iw] + prefix + "".join(f"namespace g{i} {{\n{g}}}\n" for i, g in enumerate(groups))
+    calls = "".join(f"    g{i}::qss_jac_group(fr, 1, jac + c, n);\n" for i in range(K))
+    drv = ("extern \"C\" void eval_cells(long long n, const double* C, const double* T, double* wdot,"
+           " double* Tdot, double* jac) {\n"
+           f"  static double fr[{nfr}];\n"
+           "  for (long long c = 0; c < n; ++c) {\n"
+           "    double Cc[QSS_N];\n"
+           "    for (int k = 0; k < QSS_N; ++k) Cc[k] = C[k * n + c];\n"
+           "    qss_jac_prefix(Cc, T[c], wdot + c, Tdot + c, n, fr, 1);\n" + calls + "  }\n}\n")
+    d = tempfile.mkdtemp(prefix="qss_emitp32_")
+    cpp = os.path.join(d, "gen.cpp")
+    with open(cpp, "w") as f:
+        f.write(_SHIM + _SHIM32 + body + drv)
+    so = os.path.join(d, "gen.so")
+    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    p = ctypes.POINTER(ctypes.c_double)
+    L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
+    m = workloads.mechanism(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], 128)
+    om = oracle.OracleMech(m)
+    w, td, J = _run(L, om.conc(rho, Y), T, n * n)
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    assert_gate("wdot", w, ref["wdot"], eb["wdot"])
+    assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
+    err = np.abs(J - ref["jac"])
+    assert np.all(np.isfinite(J))
+    assert np.all(err <= 2.0 ** 29 * eb["jac"] + 1e-20), float(np.max(err / (2.0 ** 29 * eb["jac"] + 1e-20)))

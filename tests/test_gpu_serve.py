@@ -19,7 +19,9 @@ _m = {}
 def mech(key):
     if key not in _m:
         m = workloads.mechanism(key)
-        _m[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0))
+        # with the mixed-precision Jacobian beside the FP64 one (same FP64 kernels)
+        kw = {"jac32": True} if key in workloads.MIXED_JACOBIAN else {}
+        _m[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key), **kw), 0))
     return _m[key]
 
 
@@ -87,7 +89,7 @@ def test_same_result_alone_and_in_the_mix(prec):
         assert torch.equal(got_st, ref_st)
 
 
-@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR])
+@pytest.mark.parametrize("prec", [binding.QSS_LU_FP64, binding.QSS_LU_FP32_IR, binding.QSS_LU_MIXED])
 def test_same_result_with_overlapping_batches(prec):
     """Four streams: batches of three mechanisms run side by side on the
     device (the server reports several in flight at once) while the probe is

@@ -204,3 +204,18 @@ def test_csr_artefact_source_and_meta():
         assert [int(x) for x in txt["jac_col"].split()] == meta["jac_col"]
     dense = qbuild.load_meta(qbuild.build_mechanism(m))
     assert dense["jac_format"] == "dense" and dense["jac_stored"] == (dense["N"] + 1) ** 2
+
+
+def test_mixed_jacobian_build_option_checks():
+    """jac32 (the mixed-precision Jacobian) is built for the exact Jacobian
+    with the analytic temperature column only; the artefact's meta.txt then
+    announces it to the runtime."""
+    m = workloads.mechanism("tiny")
+    for bad in ({"jac_variant": "const_qss"}, {"t_column": "fd"}, {"replace_nop": 10}):
+        with pytest.raises(ValueError):
+            qbuild.build_mechanism(m, jac32=True, **bad)
+    art = qbuild.build_mechanism(m, jac32=True)
+    assert "jac32 1" in open(os.path.join(art, "meta.txt")).read().splitlines()
+    assert os.path.exists(os.path.join(art, "jac32.cubin"))
+    assert "qss_jac32_kernel" in qbuild.load_meta(art)["kernels"]
+    assert "jac32 1" not in open(os.path.join(qbuild.build_mechanism(m), "meta.txt")).read().splitlines()
