@@ -577,11 +577,12 @@ def _jac_cubin_digest(art, parts):
     """Digest of the Jacobian's cubins (the single kernel, or the prefix and
     group kernels in order), matched against the committed ncu summary."""
     import hashlib
+    from paper_2405_05974_b300.qssc.build import cubin_file
     names = ["jac.cubin"] if parts < 2 else ["jac_prefix.cubin"] + [f"jac_g{i}.cubin" for i in range(parts)]
     h = hashlib.sha256()
     for nm in names:
-        h.update(open(os.path.join(art, nm), "rb").read())
-    return h.hexdigest()[:16] if parts >= 2 else cubin_digest(os.path.join(art, "jac.cubin"))
+        h.update(open(cubin_file(art, nm), "rb").read())
+    return h.hexdigest()[:16] if parts >= 2 else cubin_digest(cubin_file(art, "jac.cubin"))
 
 
 def jacobian_bench(key, ncells, steps, warmup, local, rank, world, pg, do_e2e=True, cpu_seconds=0.0,
@@ -767,9 +768,8 @@ def memory_study(local):
                 out.append(rec)
                 continue
             meta = load_meta(art)
-            src = open(os.path.join(art, "mech_jac.inc")).read()
             rec.update({"ms": autotune.time_jacobian(art, key, nc, device=local),
-                        "stored_values": src.count("const double t"),
+                        "stored_values": meta.get("stored_values_jac"),
                         "fp64_instr_per_cell": meta.get("fp64_instr_jac"), "dag_flops": meta.get("flops_jac"),
                         "ptxas": meta["kernels"].get("qss_jac_kernel")})
             out.append(rec)
@@ -966,7 +966,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded mechanism and states)", "config": cfg, "roofline": head["roofline"],
             "cpu_baseline": cpu, "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
-            "clocks": head["clocks"], "by_config": by_config, "implicit": implicit,
+            "clocks": head["clocks"], "mixed_jacobian": head["mixed_jacobian"], "by_config": by_config,
+            "implicit": implicit,
             "integration": integration, "serving": serving, "jacobian_variants": variants,
             "kernel": head["kernel"]}
     print(json.dumps(line), flush=True)

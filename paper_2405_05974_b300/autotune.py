@@ -57,6 +57,7 @@ from .qssc.build import build_mechanism, load_meta
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 MIN_GAIN = 0.02      # relative speed-up a non-default variant must show
+UNTUNED = ("jac32",)  # build options outside the searched grid
 SIZES = (1 << 16, 1 << 20)
 
 
@@ -145,8 +146,20 @@ def artefact(mech: dict, gpu_name: Optional[str] = None, defaults: Optional[dict
     if gpu_name is None:
         import torch
         gpu_name = torch.cuda.get_device_name() if torch.cuda.is_available() else ""
-    return build_mechanism(mech, **{**(choice_for(mech, gpu_name, ncells=ncells) or dict(defaults or {})),
-                                    **build_kw})
+    return build_mechanism(mech, **{**tuned_options(mech, gpu_name, defaults, ncells), **build_kw})
+
+
+def tuned_options(mech: dict, gpu_name: str, defaults: Optional[dict] = None, ncells: Optional[int] = None,
+                  table: Optional[dict] = None) -> dict:
+    """The recorded choice, else `defaults`; options the tuning does not
+    decide (the mixed-precision kernels, jac32) come from `defaults` either
+    way."""
+    base = dict(defaults or {})
+    opts = dict(choice_for(mech, gpu_name, table, ncells=ncells) or base)
+    for k in UNTUNED:
+        if k in base and k not in opts:
+            opts[k] = base[k]
+    return opts
 
 
 def all_tuned_artefacts(mechs: Dict[str, dict], table: Optional[dict] = None):

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -53,6 +54,9 @@ struct qss_mech_s {
   int64_t wave_cells = 0;   // cells of one full wave of the Jacobian kernel (0: unknown)
   std::vector<double> W;
   std::string name, digest, dir;
+  // cubin name -> path relative to the artefact directory (meta.txt "cubin"
+  // lines: the artefacts of a mechanism share one copy of each cubin)
+  std::map<std::string, std::string> cubin_path;
   // host-array path: two staging buffers and streams, one call at a time
   std::mutex mu;
   CUdeviceptr stage[2] = {0, 0};

@@ -94,6 +94,13 @@ int64_t chunk_cells(const qss_mech_s* m, int64_t cap) {
   return std::max<int64_t>(32, cap / 32 * 32);
 }
 
+// Path of an artefact's cubin: the shared copy meta.txt names, else the file
+// in the artefact directory.
+static std::string cubin_file(const qss_mech_s* m, const std::string& dir, const std::string& name) {
+  auto it = m->cubin_path.find(name);
+  return dir + "/" + (it != m->cubin_path.end() ? it->second : name);
+}
+
 int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, const double* T,
                const double* Y, double* jac, double* wdot, double* Tdot, const double* phi,
                const int* list, const int* nact, int* nact_next, double* fr, int64_t fld,
@@ -188,6 +195,11 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "jac_nnz") ls >> m->jac_nnz;
     else if (key == "smem_slots") ls >> m->smem_slots;
     else if (key == "jac32") ls >> m->jac32;
+    else if (key == "cubin") {
+      std::string f, p;
+      ls >> f >> p;
+      m->cubin_path[f] = p;
+    }
     else if (key == "jac_row_ptr" || key == "jac_col") {
       std::vector<int32_t>& v = key == "jac_col" ? m->jac_col : m->jac_row_ptr;
       int32_t x;
@@ -236,7 +248,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   need.push_back({&m->mod_wdot, "wdot.cubin", "qss_jac_fd_kernel", &m->f_jac_fd});
   for (const Need& nd : need) {
     CUresult r = CUDA_SUCCESS;
-    if (!*nd.mod) r = drv().cuModuleLoad(nd.mod, (dir + "/" + nd.file).c_str());
+    if (!*nd.mod) r = drv().cuModuleLoad(nd.mod, cubin_file(m, dir, nd.file).c_str());
     int code = 0;
     if (r != CUDA_SUCCESS) {
       code = cu_fail(r, ("drv().cuModuleLoad(" + nd.file + ")").c_str());
@@ -272,7 +284,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   const char* opt[] = {"qss_newton_update_fp64_kernel", "qss_newton_update_fp32ir_kernel",
                        "qss_newton_setup_kernel", "qss_newton_finish_kernel"};
   CUfunction* oslot[] = {&m->f_newton[0], &m->f_newton[1], &m->f_newton_setup, &m->f_newton_finish};
-  if (drv().cuModuleLoad(&m->mod_newton, (dir + "/newton.cubin").c_str()) != CUDA_SUCCESS)
+  if (drv().cuModuleLoad(&m->mod_newton, cubin_file(m, dir, "newton.cubin").c_str()) != CUDA_SUCCESS)
     m->mod_newton = nullptr;
   for (int i = 0; i < 4; ++i)
     if (!m->mod_newton || drv().cuModuleGetFunction(oslot[i], m->mod_newton, opt[i]) != CUDA_SUCCESS)

@@ -37,7 +37,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc", "qss_cells.cuh",
              "qss_jac_kernel.cuh", "qss_jac_parts.cuh", "qss_wdot_kernels.cuh", "qss_newton.cuh",
              "qss_convert.h", "qss_jac32_kernel.cuh"]
-ARTEFACT_FILES = ("wdot.cubin", "newton.cubin", "meta.txt", "meta.json")
+ARTEFACT_FILES = ("meta.txt", "meta.json")   # plus the cubins meta.txt names
 COMPILER_VERSION = "1"
 
 
@@ -61,11 +61,45 @@ def artefact_key(mech: dict, block: int = 128, defines=()) -> str:
 
 
 CUBIN_CACHE = os.path.join(REPO, "build", "cubins")
+# Artefacts of one mechanism share most of their cubins (the source-term and
+# Newton cubins do not depend on the Jacobian's build options, and variants
+# differ in one kernel), so each distinct cubin is stored once, in this
+# directory beside the artefact directories, named by its content key;
+# meta.txt maps the artefact's cubin names to it ("cubin wdot.cubin
+# ../_cubins/<key>.cubin").
+SHARED = "_cubins"
 
 
-def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: str):
+def cubin_file(art: str, name: str) -> str:
+    """Path of the artefact's cubin `name` ("jac.cubin", "wdot.cubin", ...)."""
+    rel = _cubin_map(art).get(name)
+    return os.path.normpath(os.path.join(art, rel)) if rel else os.path.join(art, name)
+
+
+def source_dir(art: str) -> str:
+    """Directory of the generated sources (mech_*.inc) of artefact `art`."""
+    art = os.path.normpath(art)
+    return os.path.join(os.path.dirname(os.path.dirname(art)), "src", os.path.basename(art))
+
+
+def _cubin_map(art: str) -> dict:
+    out = {}
+    try:
+        with open(os.path.join(art, "meta.txt")) as f:
+            for ln in f:
+                p = ln.split()
+                if len(p) == 3 and p[0] == "cubin":
+                    out[p[1]] = p[2]
+    except OSError:
+        pass
+    return out
+
+
+def _compile_cubin(tu_src: str, headers: dict, flags, store: str, log_path: str):
     """Compile one translation unit to a cubin, cached by the hash of its
-    source, the headers it includes (name -> text) and the flags."""
+    source, the headers it includes (name -> text) and the flags; the cubin
+    is placed in the shared store `store` under its key.  Returns (ptxas
+    log, key)."""
     h = hashlib.sha256(tu_src.encode())
     for name in sorted(headers):
         h.update(name.encode())
@@ -95,9 +129,14 @@ def _compile_cubin(tu_src: str, headers: dict, flags, out_path: str, log_path: s
         with open(cached_log, "w") as f:
             f.write(log)
         os.replace(cached + ".tmp" + tag, cached)
-    shutil.copyfile(cached, out_path)
+    dst = os.path.join(store, key + ".cubin")
+    if not os.path.exists(dst):
+        os.makedirs(store, exist_ok=True)
+        tmp = dst + ".tmp%d_%d" % (os.getpid(), threading.get_ident())
+        shutil.copyfile(cached, tmp)
+        os.replace(tmp, dst)
     shutil.copyfile(cached_log, log_path)
-    return open(log_path).read()
+    return open(log_path).read(), key
 
 
 _INDEX_LOCK = threading.Lock()
@@ -181,15 +220,31 @@ def prune_artefacts(keep, root: str = None) -> list:
         os.replace(tmp, os.path.join(root, "index.json"))
         for d in sorted(os.listdir(root)):
             p = os.path.join(root, d)
-            if os.path.isdir(p) and d not in keep_names:
+            if os.path.isdir(p) and d not in keep_names and d != SHARED:
                 shutil.rmtree(p, ignore_errors=True)
                 removed.append(d)
+        srcroot = os.path.join(os.path.dirname(os.path.normpath(root)), "src")
+        for d in sorted(os.listdir(srcroot)) if os.path.isdir(srcroot) else []:
+            if d not in keep_names:
+                shutil.rmtree(os.path.join(srcroot, d), ignore_errors=True)
+        # shared cubins no kept artefact refers to
+        used = {os.path.basename(r) for k in keep_names for r in _cubin_map(os.path.join(root, k)).values()}
+        store = os.path.join(root, SHARED)
+        for f in sorted(os.listdir(store)) if os.path.isdir(store) else []:
+            if f not in used:
+                os.remove(os.path.join(store, f))
     return removed
 
 
 def _complete(out: str) -> bool:
-    return all(os.path.exists(os.path.join(out, f)) for f in ARTEFACT_FILES) and (
-        os.path.exists(os.path.join(out, "jac.cubin")) or os.path.exists(os.path.join(out, "jac_prefix.cubin")))
+    if not all(os.path.exists(os.path.join(out, f)) for f in ("meta.txt", "meta.json")):
+        return False
+    m = _cubin_map(out)
+    if not m:
+        return False
+    have = lambda f: f in m and os.path.exists(os.path.normpath(os.path.join(out, m[f])))  # noqa: E731
+    return all(have(f) for f in m) and have("wdot.cubin") and have("newton.cubin") and (
+        have("jac.cubin") or have("jac_prefix.cubin"))
 
 
 def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defines=(),
@@ -266,8 +321,12 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         return out
     tmp = out + ".tmp%d_%d" % (os.getpid(), threading.get_ident())   # one per concurrent build
     os.makedirs(tmp, exist_ok=True)
+    # the generated sources (inputs of the compile, not needed to load the
+    # artefact) are kept beside the artefacts, not in them
+    srcd = source_dir(out)
+    os.makedirs(srcd, exist_ok=True)
     for pname, text in parts.items():
-        with open(os.path.join(tmp, pname), "w") as f:
+        with open(os.path.join(srcd, pname), "w") as f:
             f.write(text)
     t1 = time.time()
     common = {k: hdr[k] for k in ("qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc")}
@@ -310,13 +369,13 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
                    {**common, "mech_sizes.inc": parts["mech_sizes.inc"],
                     "qss_newton.cuh": hdr["qss_newton.cuh"]}),
     })
-    logs, secs = {}, {}
+    logs, secs, keys = {}, {}, {}
 
     def compile_unit(name):
         t = time.time()
         tu, headers = units[name]
-        logs[name] = _compile_cubin(tu, headers, flags, os.path.join(tmp, f"{name}.cubin"),
-                                    os.path.join(tmp, f"build_{name}.log"))
+        logs[name], keys[name] = _compile_cubin(tu, headers, flags, os.path.join(root, SHARED),
+                                                os.path.join(tmp, f"build_{name}.log"))
         secs[name] = round(time.time() - t, 3)
 
     with ThreadPoolExecutor(min(len(units), os.cpu_count() or 4)) as ex:
@@ -353,6 +412,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
             f.write("jac_row_ptr " + " ".join(map(str, meta["jac_row_ptr"])) + "\n")
             f.write("jac_col " + " ".join(map(str, meta["jac_col"])) + "\n")
         f.write("W " + " ".join(repr(w) for w in meta["W"]) + "\n")
+        for name in sorted(units):
+            f.write(f"cubin {name}.cubin ../{SHARED}/{keys[name]}.cubin\n")
     if os.path.exists(out):
         shutil.rmtree(out)
     os.replace(tmp, out)

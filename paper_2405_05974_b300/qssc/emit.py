@@ -498,6 +498,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),
         "fp64_instr_wdot": fp64_instructions(cnt_w), "fp64_instr_jac": fp64_instructions(cnt_j),
+        "stored_values_jac": sum(1 for ln in body_j if ln.lstrip().startswith("const double t")),
         "dag_nodes": len(g.op), "jac_nnz": sum(1 for i in range(n) for c in range(n)
                                                if model.jac[i][c] != g.ZERO),
     }

@@ -24,7 +24,10 @@ _cache = {}
 def gpu_mech(key, fmt="dense", parts=0):
     k = (key, fmt, parts)
     if k not in _cache:
-        _cache[k] = binding.Mechanism(build_mechanism(workloads.mechanism(key), jac_format=fmt, jac_parts=parts), 0)
+        # the dense single-kernel form: the workload's own artefact (its FP64
+        # kernels are those of the plain build)
+        kw = {"jac_format": fmt, "jac_parts": parts} if (fmt, parts) != ("dense", 0) else workloads.build_options(key)
+        _cache[k] = binding.Mechanism(build_mechanism(workloads.mechanism(key), **kw), 0)
     return _cache[k]
 
 

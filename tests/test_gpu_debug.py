@@ -20,7 +20,7 @@ import pytest
 import torch
 
 from paper_2405_05974_b300 import binding, mechgen, workloads
-from paper_2405_05974_b300.qssc.build import build_mechanism
+from paper_2405_05974_b300.qssc.build import build_mechanism, cubin_file
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +91,7 @@ def test_debug_check_reports_cell_beyond_ld():
     td = torch.zeros(ncells, dtype=torch.float64, device="cuda")
     L = _cuda()
     mod, fn = ctypes.c_void_p(), ctypes.c_void_p()
-    assert L.cuModuleLoad(ctypes.byref(mod), os.path.join(art, "jac.cubin").encode()) == 0
+    assert L.cuModuleLoad(ctypes.byref(mod), cubin_file(art, "jac.cubin").encode()) == 0
     try:
         assert L.cuModuleGetFunction(ctypes.byref(fn), mod, b"qss_jac_kernel") == 0
         word, nbytes = ctypes.c_uint64(), ctypes.c_size_t()

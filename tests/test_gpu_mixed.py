@@ -32,7 +32,7 @@ _cache = {}
 def mech(key):
     if key not in _cache:
         m = workloads.mechanism(key)
-        art = build_mechanism(m, **workloads.build_options(key), jac32=True)
+        art = build_mechanism(m, **{**workloads.build_options(key), "jac32": True})
         _cache[key] = (m, binding.Mechanism(art, 0), oracle.OracleMech(m))
     return _cache[key]
 
@@ -90,7 +90,7 @@ def _close(pa, pb, rel, N):
                                                     ("tiny", 2000, workloads.IMPLICIT_DT, 0.25),
                                                     ("hydrocarbon", 2048, workloads.IMPLICIT_DT_CONVERGING, 0.95),
                                                     ("hydrocarbon", 1024, workloads.IMPLICIT_DT, 0.25),
-                                                    ("large", 512, 1e-12, 0.95)])
+                                                    ("large", 512, 1e-12, 0.9)])
 def test_mixed_implicit_step(key, ncells, dt, min_conv):
     m, gm, om = mech(key)
     rho, T, Y = states(key, ncells)
@@ -110,7 +110,7 @@ def test_mixed_implicit_step(key, ncells, dt, min_conv):
     assert bad.size <= max(2, 0.002 * both.sum()), bad.size
     if bad.size:
         f, _ = om.eval_phi(pm[:, bad], jac=False)
-        G = pm[:, bad] - _phi(om, rho[bad], T[bad], Y[bad]) - dt * f
+        G = pm[:, bad] - _phi(om, rho[bad], T[bad], Y[:, bad]) - dt * f
         scale = 1e-10 * np.abs(pm[:, bad]) + 10 * np.r_[np.full(N, ATOL_C), ATOL_T][:, None] + \
             1e-12 * dt * np.abs(f)
         assert np.all(np.abs(G) <= 1e3 * scale)

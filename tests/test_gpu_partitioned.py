@@ -20,7 +20,10 @@ _cache = {}
 
 def gpu_mech(key, parts=0):
     if (key, parts) not in _cache:
-        _cache[(key, parts)] = binding.Mechanism(build_mechanism(workloads.mechanism(key), jac_parts=parts), 0)
+        # the single-kernel form: the workload's own artefact (its FP64 kernels
+        # are those of the plain build)
+        kw = {"jac_parts": parts} if parts else workloads.build_options(key)
+        _cache[(key, parts)] = binding.Mechanism(build_mechanism(workloads.mechanism(key), **kw), 0)
     return _cache[(key, parts)]
 
 

@@ -19,9 +19,8 @@ _m = {}
 def mech(key):
     if key not in _m:
         m = workloads.mechanism(key)
-        # with the mixed-precision Jacobian beside the FP64 one (same FP64 kernels)
-        kw = {"jac32": True} if key in workloads.MIXED_JACOBIAN else {}
-        _m[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key), **kw), 0))
+        # the workload's artefact: the mixed-precision Jacobian beside the FP64 one
+        _m[key] = (m, binding.Mechanism(build_mechanism(m, **workloads.build_options(key)), 0))
     return _m[key]
 
 

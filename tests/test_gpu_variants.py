@@ -29,7 +29,10 @@ def gpu_mech(key, jac_variant="exact", t_column="analytic"):
     k = (key, jac_variant, t_column)
     if k not in _cache:
         m = workloads.mechanism(key)
-        _cache[k] = binding.Mechanism(build_mechanism(m, jac_variant=jac_variant, t_column=t_column), 0)
+        # the exact Jacobian: the workload's own artefact
+        kw = workloads.build_options(key) if (jac_variant, t_column) == ("exact", "analytic") else \
+            {"jac_variant": jac_variant, "t_column": t_column}
+        _cache[k] = binding.Mechanism(build_mechanism(m, **kw), 0)
     return _cache[k]
 
 
