@@ -57,7 +57,7 @@ from .qssc.build import build_mechanism, load_meta
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 MIN_GAIN = 0.02      # relative speed-up a non-default variant must show
-UNTUNED = ("jac32",)  # build options outside the searched grid
+UNTUNED = ("jac32", "jac32_slots", "jac32_minblocks")   # options outside the searched grid (the mixed kernel)
 SIZES = (1 << 16, 1 << 20)
 
 

@@ -20,6 +20,8 @@ struct qss_mech_s {
   CUfunction f_wdot = nullptr, f_jac = nullptr, f_jac_fd = nullptr;   // f_wdot also has a list mode
   CUfunction f_jac32 = nullptr;    // qss_jac32_kernel (single-kernel artefacts built with jac32)
   int jac32 = 0;                   // meta.txt: the artefact carries the mixed-precision Jacobian
+  int jac32_slots = 0;             // its FP32 values in dynamic shared memory (per thread)
+  unsigned jac32_smem = 0;         // bytes of dynamic shared memory per block of qss_jac32_kernel
   CUfunction f_newton[2] = {nullptr, nullptr};   // update kernels: FP64 LU, FP32 LU + FP64 refinement
   CUfunction f_newton_setup = nullptr, f_newton_finish = nullptr;
   CUfunction f_integ[4] = {nullptr, nullptr, nullptr, nullptr};   // init, gather, accept, finish

@@ -10,9 +10,14 @@
 
 #include "qss_cells.cuh"
 
-// The derivative part holds its values as floats (one register each), so
-// the kernel keeps the default register budget of one block per SM.
-extern "C" __global__ void __launch_bounds__(QSS_BLOCK, 1)
+// Blocks per SM the register allocation must allow (1: up to 255 registers
+// at 128 threads; 3: 168; 4: 128), a tuning option like QSS_MINBLOCKS of
+// the FP64 kernel.
+#ifndef QSS_J32_MINBLOCKS
+#define QSS_J32_MINBLOCKS 1
+#endif
+
+extern "C" __global__ void __launch_bounds__(QSS_BLOCK, QSS_J32_MINBLOCKS)
 qss_jac32_kernel(long long ncells, long long ld, const double* __restrict__ rho,
                  const double* __restrict__ T, const double* __restrict__ Y,
                  double* __restrict__ jac, double* __restrict__ wdot, double* __restrict__ Tdot,

@@ -110,7 +110,7 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   if (mixed && !m->jac32) return fail(QSS_ERR_UNIMPLEMENTED, "artefact has no mixed-precision Jacobian (jac32)");
   if (mixed && m->jac_parts < 2) {
     void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
-    return launch_cells(m, m->f_jac32, ncells, m->block, args, s, 0);
+    return launch_cells(m, m->f_jac32, ncells, m->block, args, s, m->jac32_smem);
   }
   if (m->jac_parts < 2) {
     void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
@@ -195,6 +195,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "jac_nnz") ls >> m->jac_nnz;
     else if (key == "smem_slots") ls >> m->smem_slots;
     else if (key == "jac32") ls >> m->jac32;
+    else if (key == "jac32_slots") ls >> m->jac32_slots;
     else if (key == "cubin") {
       std::string f, p;
       ls >> f >> p;
@@ -212,7 +213,8 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
       m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
       m->smem_slots < 0 || m->smem_slots > 1024 || (m->smem_slots > 0 && m->jac_parts >= 2) ||
-      m->jac32 < 0 || m->jac32 > 1 ||
+      m->jac32 < 0 || m->jac32 > 1 || m->jac32_slots < 0 || m->jac32_slots > 2048 ||
+      (m->jac32_slots > 0 && (!m->jac32 || m->jac_parts >= 2)) ||
       !jac_pattern_ok(m)) {
     delete m;
     return fail(QSS_ERR_MECH_FORMAT, "inconsistent meta.txt in " + dir);
@@ -278,6 +280,15 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     if (ra != CUDA_SUCCESS) {
       qss_mech_free(m);
       return cu_fail(ra, "cuFuncSetAttribute(qss_jac_kernel, dynamic shared memory)");
+    }
+  }
+  if (m->jac32_slots > 0) {
+    m->jac32_smem = (unsigned)m->jac32_slots * (unsigned)m->block * sizeof(float);
+    CUresult ra = drv().cuFuncSetAttribute(m->f_jac32, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                           (int)m->jac32_smem);
+    if (ra != CUDA_SUCCESS) {
+      qss_mech_free(m);
+      return cu_fail(ra, "cuFuncSetAttribute(qss_jac32_kernel, dynamic shared memory)");
     }
   }
   // optional kernels (implicit step), in newton.cubin

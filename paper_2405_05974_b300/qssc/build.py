@@ -166,7 +166,7 @@ def _write_index(root: str, fast: str, name: str):
 
 
 def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-             jac32=False) -> tuple:
+             jac32=False, jac32_slots=0, jac32_minblocks=1) -> tuple:
     """The build options other than block and defines, as index-key parts."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
@@ -187,18 +187,26 @@ def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_ord
         if replace_nop > 0 or (jac_variant, t_column) != ("exact", "analytic"):
             raise ValueError("jac32 is built for the exact Jacobian with the analytic T column")
         variant += ("jac32",)
+    if jac32_slots > 0:
+        if not jac32 or jac_parts >= 2:
+            raise ValueError("jac32_slots applies to the single-kernel mixed-precision Jacobian")
+        variant += (f"j32smem{int(jac32_slots)}",)
+    if jac32_minblocks != 1:
+        if not jac32 or jac_parts >= 2:
+            raise ValueError("jac32_minblocks applies to the single-kernel mixed-precision Jacobian")
+        variant += (f"j32mb{int(jac32_minblocks)}",)
     return variant
 
 
 def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
                   t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
                   jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0, ptxas=(),
-                  jac32: bool = False):
+                  jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1):
     """The directory of an artefact already built with these options for the
     current templates, or None (never compiles)."""
     root = root or DEFAULT_ROOT
     variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-                       jac32)
+                       jac32, jac32_slots, jac32_minblocks)
     name = _read_index(root).get(artefact_key(mech, block, tuple(defines) + variant))
     return os.path.join(root, name) if name and _complete(os.path.join(root, name)) else None
 
@@ -251,7 +259,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
                     jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0,
-                    ptxas=(), jac32: bool = False) -> str:
+                    ptxas=(), jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -270,9 +278,12 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     ``ptxas`` are extra ptxas options (``"regUsageLevel=0"`` is passed as
     ``-Xptxas -regUsageLevel=0``); ``jac32`` also builds ``jac32.cubin``, the
     mixed-precision Jacobian kernel (derivative terms in FP32,
-    ``emit.emit_jac32_source``) of the mixed-precision implicit step."""
+    ``emit.emit_jac32_source``) of the mixed-precision implicit step, with
+    ``jac32_slots`` of its most-reloaded FP32 values in shared memory and
+    ``jac32_minblocks`` blocks per SM in its register budget (its own
+    __launch_bounds__, so the other cubins are unaffected)."""
     variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-                       jac32)
+                       jac32, jac32_slots, jac32_minblocks)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -296,7 +307,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         for i, gsrc in enumerate(group_srcs):
             parts[f"mech_jac_g{i}.inc"] = gsrc
     if jac32 and jac_parts < 2:
-        src32, meta32 = emit.emit_jac32_source(model, jac_format)
+        src32, meta32 = emit.emit_jac32_source(model, jac_format, smem_slots=jac32_slots)
         parts["mech_jac32.inc"] = src32
         meta.update(meta32)
     elif jac32:
@@ -313,7 +324,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     # templates and the flags (a generator change that emits the same code
     # keeps its artefacts)
     hk = hashlib.sha256(json.dumps([sorted(parts.items()), sorted(hdr.items()), flags,
-                                    meta.get("jac_variant"), meta.get("t_column"), jac_parts]).encode())
+                                    meta.get("jac_variant"), meta.get("t_column"), jac_parts]
+                                   + ([jac32_minblocks] if jac32_minblocks != 1 else [])).encode())
     art_name = f"{mech.get('name', 'mech')}_{hk.hexdigest()[:20]}"
     out = os.path.join(root, art_name)
     if not force and _complete(out):
@@ -374,7 +386,9 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     def compile_unit(name):
         t = time.time()
         tu, headers = units[name]
-        logs[name], keys[name] = _compile_cubin(tu, headers, flags, os.path.join(root, SHARED),
+        uflags = flags + ([f"-DQSS_J32_MINBLOCKS={int(jac32_minblocks)}"] if name == "jac32" and jac32_minblocks != 1
+                          else [])
+        logs[name], keys[name] = _compile_cubin(tu, headers, uflags, os.path.join(root, SHARED),
                                                 os.path.join(tmp, f"build_{name}.log"))
         secs[name] = round(time.time() - t, 3)
 
@@ -406,6 +420,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         f.write(f"jac_nnz {meta['jac_stored']}\n")
         if jac32:
             f.write("jac32 1\n")
+        if meta.get("jac32_slots", 0) > 0:
+            f.write(f"jac32_slots {int(meta['jac32_slots'])}\n")
         if meta.get("smem_slots", 0) > 0:   # slots the emitted code uses (at most the requested)
             f.write(f"smem_slots {int(meta['smem_slots'])}\n")
         if jac_format != "dense":

@@ -58,6 +58,10 @@ class Emitter:
         # before the stores begin)
         self.emit_order = emit_order
         self.smem_slot = {}   # node -> shared-memory slot (values kept there, not in registers)
+        # mixed precision: FP32 values kept in shared memory, by key ("n", node)
+        # for an FP32 node, ("c", key) for the FP32 copy of an FP64 value
+        self.smem32 = {}
+        self.conv_names = {}  # after emit(): FP32-copy name (s<i>) -> its key
 
     def _resolve(self, i):
         g = self.g
@@ -107,7 +111,7 @@ class Emitter:
         f32 = set()
         if fp64_outputs is not None:
             if self.replace_nop or self.smem_slot:
-                raise ValueError("mixed precision is emitted without replacement or shared-memory slots")
+                raise ValueError("mixed precision is emitted without replacement or FP64 shared-memory slots")
             val = set()
             stack = list(roots[:fp64_outputs])
             while stack:
@@ -184,8 +188,14 @@ class Emitter:
 
         def as32(x, key):
             if key not in conv:
-                conv[key] = f"s{len(conv)}"
-                pending.append(f"{indent}const float {conv[key]} = qss_f32({x});")
+                nm = f"s{len(conv)}"
+                self.conv_names[nm] = key
+                if ("c", key) in self.smem32:
+                    conv[key] = f"qss_sm32[{self.smem32[('c', key)]} * QSS_BLOCK]"
+                    pending.append(f"{indent}{conv[key]} = qss_f32({x});")
+                else:
+                    conv[key] = nm
+                    pending.append(f"{indent}const float {nm} = qss_f32({x});")
                 counts["cvt_f32"] += 1
             return conv[key]
 
@@ -294,7 +304,10 @@ class Emitter:
                 e = expr_of(n)
                 lines.extend(pending)
                 pending.clear()
-                if n in self.smem_slot:
+                if ("n", n) in self.smem32:
+                    names[n] = f"qss_sm32[{self.smem32[('n', n)]} * QSS_BLOCK]"
+                    lines.append(f"{indent}{names[n]} = {e};")
+                elif n in self.smem_slot:
                     lines.append(f"{indent}qss_sm[{self.smem_slot[n]} * QSS_BLOCK] = {e};")
                 else:
                     lines.append(f"{indent}const {'float' if n in f32 else 'double'} t{n} = {e};")
@@ -345,6 +358,53 @@ def fp64_instructions(counts, exp_cost=7, log_cost=12, rcp_cost=3) -> int:
     """Estimated FP64-pipe instructions per cell of the emitted code."""
     return (counts["add"] + counts["mul"] + counts["fma"] + exp_cost * counts["exp"]
             + log_cost * counts["log"] + rcp_cost * counts["rcp"])
+
+
+def choose_smem_values32(lines, slots: int, registers: int = 340):
+    """choose_smem_values for a mixed-precision body: the `slots` FP32
+    values (t<id> float nodes and s<i> FP32 copies) that a register file of
+    `registers` 32-bit registers would reload most often (a double takes two
+    of them; furthest-next-use eviction).  Returns their names, most
+    reloaded first."""
+    tok = re.compile(r"\b([ts]\d+)\b")
+    defn = re.compile(r"\s*const (float|double) ([ts]\d+) = (.*);")
+    seq, width = [], {}
+    for ln in lines:
+        m = defn.match(ln)
+        if m:
+            width[m.group(2)] = 1 if m.group(1) == "float" else 2
+            seq.append((m.group(2), tok.findall(m.group(3))))
+        else:
+            seq.append((None, tok.findall(ln)))
+    uses = {}
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            uses.setdefault(x, []).append(i)
+    pos = {x: 0 for x in uses}
+    resident, reloads = set(), Counter()
+
+    def next_use(x, i):
+        v = uses[x]
+        while pos[x] < len(v) and v[pos[x]] <= i:
+            pos[x] += 1
+        return v[pos[x]] if pos[x] < len(v) else None
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            if x not in resident:
+                reloads[x] += 1
+                resident.add(x)
+        if d is not None and d in uses:
+            resident.add(d)
+        nu = {x: next_use(x, i) for x in resident}
+        resident = {x for x in resident if nu[x] is not None}
+        used = sum(width.get(x, 2) for x in resident)
+        if used > registers:
+            for x in sorted(resident, key=lambda y: -nu[y]):
+                if used <= registers:
+                    break
+                resident.discard(x)
+                used -= width.get(x, 2)
+    return [x for x, _ in reloads.most_common() if width.get(x) == 1][:slots]
 
 
 def choose_smem_values(lines, slots: int, registers: int = 170):
@@ -505,7 +565,7 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
     return src, meta
 
 
-def emit_jac32_source(model, jac_format: str = "dense") -> Tuple[str, dict]:
+def emit_jac32_source(model, jac_format: str = "dense", smem_slots: int = 0) -> Tuple[str, dict]:
     """The mixed-precision Jacobian device function
 
         qss_eval_jac32(C, T, wdot, Tdot, jac, wstride, jstride)
@@ -517,7 +577,10 @@ def emit_jac32_source(model, jac_format: str = "dense") -> Tuple[str, dict]:
     nodes only the Jacobian needs (the derivatives of the rates, dC_Q/dphi,
     the chain-rule products G + P X) are computed in FP32 and stored widened
     to FP64.  For the Newton iteration matrix of the mixed-precision implicit
-    step, whose residual stays FP64."""
+    step, whose residual stays FP64.  smem_slots > 0: that many of the FP32
+    values a register file would reload most often (choose_smem_values32)
+    live in dynamic shared memory (slot k of this thread at
+    qss_sm32[k * QSS_BLOCK]; smem_slots * QSS_BLOCK floats per block)."""
     ir = model.ir
     N = ir.N
     n = N + 1
@@ -533,16 +596,26 @@ def emit_jac32_source(model, jac_format: str = "dense") -> Tuple[str, dict]:
         for i in range(n):
             if (i, c) in pos:
                 out_j.append((f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]))
+    nval = len(out_w) + len(out_t)
     em = Emitter(model, inputs)
-    body, cnt = em.emit(out_w + out_t + out_j, indent="  ", fp64_outputs=len(out_w) + len(out_t))
+    body, cnt = em.emit(out_w + out_t + out_j, indent="  ", fp64_outputs=nval)
+    prologue = []
+    if smem_slots > 0:
+        chosen = choose_smem_values32(body, smem_slots)
+        keys = {nm: (("n", int(nm[1:])) if nm[0] == "t" else ("c", em.conv_names[nm])) for nm in chosen}
+        em = Emitter(model, inputs)
+        em.smem32 = {keys[nm]: k for k, nm in enumerate(chosen)}
+        body, cnt = em.emit(out_w + out_t + out_j, indent="  ", fp64_outputs=nval)
+        prologue = ["  extern __shared__ float qss_smem32_dyn[];",
+                    "  volatile float* const qss_sm32 = qss_smem32_dyn + threadIdx.x;"]
     unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
     src = "\n".join([
         "__device__ __forceinline__ void qss_eval_jac32(const double* __restrict__ C, const double T,",
         "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
         "    const long long wstride, const long long jstride) {",
-        *unpack, *body, "}", ""])
+        *unpack, *prologue, *body, "}", ""])
     meta = {"ops_jac32": dict(cnt), "flops_jac32": algorithmic_flops(cnt),
-            "fp64_instr_jac32": fp64_instructions(cnt)}
+            "fp64_instr_jac32": fp64_instructions(cnt), "jac32_slots": len(em.smem32)}
     return src, meta
 
 

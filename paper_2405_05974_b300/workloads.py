@@ -48,8 +48,13 @@ NCELLS = {"tiny": 4096, "hydrocarbon": 1 << 20, "large": 1 << 20, "implicit": 1 
 # within 1 % of each other, 8 groups 7 % slower, and 4 compile fastest)
 # every workload's artefact also carries the mixed-precision Jacobian
 # kernels (jac32: the source term in FP64, the derivative terms in FP32) for
-# the mixed-precision implicit step; the FP64 kernels are the same as without
-BUILD_OPTIONS = {"tiny": {"jac32": True}, "hydrocarbon": {"jac32": True},
+# the mixed-precision implicit step; the FP64 kernels are the same as without.
+# The hydrocarbon mixed kernel is spill-latency bound: 128 registers (four
+# blocks per SM) and 64 FP32 values in shared memory measured fastest on B300
+# (2^20 cells: 49.4 ms, against 60.0 ms at 255 registers without slots; 5
+# blocks / 76 slots 49.3 ms, 6 / 64 51.7 ms, 4 / 96 50.0 ms)
+BUILD_OPTIONS = {"tiny": {"jac32": True},
+                 "hydrocarbon": {"jac32": True, "jac32_slots": 64, "jac32_minblocks": 4},
                  "large": {"jac_parts": 4, "jac32": True}}
 
 

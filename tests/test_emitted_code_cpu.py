@@ -143,6 +143,7 @@ def test_emission_orders_emit_the_same_statements(key):
 
 _SHIM32 = r"""
 #include <math.h>
+float qss_smem32_dyn[65536];
 #include "qss_convert.h"
 static inline float __frcp_rn(float x) { return 1.0f / x; }
 using std::fmaf;
@@ -151,18 +152,20 @@ using std::fmaf;
 _DRIVER32 = _DRIVER.replace("qss_eval_jac(", "qss_eval_jac32(")
 
 
-@pytest.mark.parametrize("key", ["tiny", "hydrocarbon"])
-def test_mixed_precision_jacobian_within_fp32_bound(key):
+@pytest.mark.parametrize("key,slots", [("tiny", 0), ("hydrocarbon", 0), ("hydrocarbon", 200)])
+def test_mixed_precision_jacobian_within_fp32_bound(key, slots):
     """The mixed-precision Jacobian (derivative terms in FP32, the source
     term in FP64), compiled on the CPU with the kernels' own bit-pattern
     conversions: wdot and Tdot pass the FP64 gate, and every Jacobian entry
     is within 2^29 (= u_32 / u_64) times the oracle's FP64 running-error
     bound (plus the 1e-20 floor), i.e. within the first-order rounding
-    bound of the same evaluation carried out entirely in FP32."""
+    bound of the same evaluation carried out entirely in FP32; also with
+    FP32 values placed in (emulated) shared memory."""
     from paper_2405_05974_b300.qssc.build import CSRC
     model = _model(key)
     src, meta = emit.emit_mechanism_source(model)
-    s32, m32 = emit.emit_jac32_source(model)
+    s32, m32 = emit.emit_jac32_source(model, smem_slots=slots)
+    assert m32["jac32_slots"] == slots   # (the hydrocarbon body reloads far more than 200 values)
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     d = tempfile.mkdtemp(prefix="qss_emit32_")
     cpp = os.path.join(d, "gen.cpp")

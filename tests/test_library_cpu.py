@@ -190,10 +190,11 @@ def test_csr_artefact_source_and_meta():
         meta = qbuild.load_meta(art)
         nnz = meta["jac_stored"]
         assert meta["jac_format"] == "csr" and nnz == meta["jac_nnz"] < (meta["N"] + 1) ** 2
-        srcs = [f for f in os.listdir(art) if f.startswith("mech_jac")]
+        srcd = qbuild.source_dir(art)   # the generated sources are kept beside the artefact
+        srcs = [f for f in os.listdir(srcd) if f.startswith("mech_jac")]
         stored = []
         for f in srcs:
-            stored += [int(x) for x in re.findall(r"jac\[(\d+) \* jstride\]", open(os.path.join(art, f)).read())]
+            stored += [int(x) for x in re.findall(r"jac\[(\d+) \* jstride\]", open(os.path.join(srcd, f)).read())]
         assert sorted(stored) == list(range(nnz))
         sizes = open(os.path.join(qbuild.source_dir(art), "mech_sizes.inc")).read()
         assert f"#define QSS_JAC_NNZ {nnz}" in sizes and "#define QSS_JAC_CSR 1" in sizes
