@@ -19,7 +19,8 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
                100 slots = 100 KB a 128-thread block)
   jac_parts    the register-pressure split: one kernel per cell (0), or a
                prefix kernel plus K column-group kernels (2, 4, 8) exchanging
-               per-cell values through a frontier buffer
+               per-cell values through a frontier buffer (with 60 or 100
+               shared-memory slots in each of its kernels as well)
 
 (A warp-slice per cell, K lanes of a warp cooperating on one cell's DAG, is
 not in the grid: on this part an FP64 instruction occupies the FP64 pipe for
@@ -74,7 +75,7 @@ def candidates(key: str) -> List[dict]:
     base = workloads.build_options(key)
     if base.get("jac_parts", 0) >= 2:
         return [dict(base)] + [{**base, "jac_parts": k} for k in (2, 8) if k != base["jac_parts"]] + \
-            [{**base, "block": 64}]
+            [{**base, "block": 64}, {**base, "smem_slots": 60}, {**base, "smem_slots": 100}]
     return [dict(base), {**base, "block": 64}, {**base, "block": 256},
             {**base, "defines": ("QSS_MINBLOCKS=3",)}, {**base, "defines": ("QSS_MINBLOCKS=4",)},
             {**base, "defines": ("QSS_SMEM_SPILL=1",)}, {**base, "smem_slots": 60},

@@ -119,11 +119,12 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   if (!fr || fld < ncells) return fail(QSS_ERR_INVALID_ARG, "frontier scratch too small");
   long long fl = fld;
   void* pa[] = {&nc, &l, &rho, &T, &Y, &wdot, &Tdot, &fr, &fl, &phi, &list, &nact, &nact_next};
-  if ((rc = launch_cells(m, mixed ? m->f_prefix32 : m->f_prefix, ncells, m->block, pa, s, 0))) return rc;
+  const unsigned smem = mixed ? 0u : m->jac_smem;
+  if ((rc = launch_cells(m, mixed ? m->f_prefix32 : m->f_prefix, ncells, m->block, pa, s, smem))) return rc;
   const double* frc = fr;
   for (int i = 0; i < m->jac_parts; ++i) {
     void* ga[] = {&nc, &frc, &fl, &jac, &l, &nact};
-    if ((rc = launch_cells(m, mixed ? m->f_group32[i] : m->f_group[i], ncells, m->block, ga, s, 0))) return rc;
+    if ((rc = launch_cells(m, mixed ? m->f_group32[i] : m->f_group[i], ncells, m->block, ga, s, smem))) return rc;
   }
   return QSS_OK;
 }
@@ -212,7 +213,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   }
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
       m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
-      m->smem_slots < 0 || m->smem_slots > 1024 || (m->smem_slots > 0 && m->jac_parts >= 2) ||
+      m->smem_slots < 0 || m->smem_slots > 1024 ||
       m->jac32 < 0 || m->jac32 > 1 || m->jac32_slots < 0 || m->jac32_slots > 2048 ||
       (m->jac32_slots > 0 && (!m->jac32 || m->jac_parts >= 2)) ||
       !jac_pattern_ok(m)) {
@@ -274,12 +275,18 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     }
   }
   if (m->smem_slots > 0) {
+    // the FP64 Jacobian kernel (or the prefix and every column group of the
+    // partitioned form) keeps smem_slots doubles per thread in shared memory
     m->jac_smem = (unsigned)m->smem_slots * (unsigned)m->block * sizeof(double);
-    CUresult ra = drv().cuFuncSetAttribute(m->f_jac, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
-                                           (int)m->jac_smem);
-    if (ra != CUDA_SUCCESS) {
-      qss_mech_free(m);
-      return cu_fail(ra, "cuFuncSetAttribute(qss_jac_kernel, dynamic shared memory)");
+    std::vector<CUfunction> fs = {m->jac_parts >= 2 ? m->f_prefix : m->f_jac};
+    if (m->jac_parts >= 2) fs.insert(fs.end(), m->f_group.begin(), m->f_group.end());
+    for (CUfunction f : fs) {
+      CUresult ra = drv().cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                             (int)m->jac_smem);
+      if (ra != CUDA_SUCCESS) {
+        qss_mech_free(m);
+        return cu_fail(ra, "cuFuncSetAttribute(Jacobian kernel, dynamic shared memory)");
+      }
     }
   }
   if (m->jac32_slots > 0) {

@@ -178,8 +178,6 @@ def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_ord
     if emit_order != "first_use":
         variant += (emit_order,)
     if smem_slots > 0:
-        if jac_parts >= 2:
-            raise ValueError("smem_slots applies to the single-kernel Jacobian")
         variant += (f"smem{int(smem_slots)}",)
     for o in ptxas:
         variant += (f"ptxas:{o}",)
@@ -273,8 +271,9 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     nonzeros, in CSR order (``emit.jac_layout``); ``emit_order`` "all_first"
     computes every value before any output is stored (Alg. 3's recycling off,
     for the memory study; the default "first_use" stores each output as soon
-    as it is final); ``smem_slots`` > 0 keeps that many of the single Jacobian
-    kernel's most-reloaded values in shared memory (dynamic, per thread);
+    as it is final); ``smem_slots`` > 0 keeps that many of the FP64 Jacobian
+    kernel's most-reloaded values in shared memory (dynamic, per thread; with
+    ``jac_parts`` in the prefix and in each column-group kernel);
     ``ptxas`` are extra ptxas options (``"regUsageLevel=0"`` is passed as
     ``-Xptxas -regUsageLevel=0``); ``jac32`` also builds ``jac32.cubin``, the
     mixed-precision Jacobian kernel (derivative terms in FP32,
@@ -294,14 +293,18 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     ir = qmech.parse(mech)
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
     src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format,
-                                           emit_order=emit_order, smem_slots=smem_slots)
+                                           emit_order=emit_order,
+                                           smem_slots=smem_slots if jac_parts < 2 else 0)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")
     parts = {"mech_sizes.inc": src[:iw], "mech_wdot.inc": src[iw:ij], "mech_jac.inc": src[ij:]}
     if jac_parts >= 2:
-        prefix_src, group_srcs, pmeta = emit.emit_partitioned_source(model, int(jac_parts), jac_format)
+        prefix_src, group_srcs, pmeta = emit.emit_partitioned_source(model, int(jac_parts), jac_format,
+                                                                     smem_slots=smem_slots)
         meta.update(pmeta)
+        # every kernel of the partition is launched with the largest count
+        meta["smem_slots"] = max(pmeta["smem_slots_parts"])
         del parts["mech_jac.inc"]
         parts["mech_jac_prefix.inc"] = prefix_src
         for i, gsrc in enumerate(group_srcs):

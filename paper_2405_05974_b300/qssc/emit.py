@@ -399,12 +399,52 @@ def choose_smem_values32(lines, slots: int, registers: int = 340):
         resident = {x for x in resident if nu[x] is not None}
         used = sum(width.get(x, 2) for x in resident)
         if used > registers:
-            for x in sorted(resident, key=lambda y: -nu[y]):
+            for x in sorted(resident, key=lambda y: (-nu[y], y)):
                 if used <= registers:
                     break
                 resident.discard(x)
                 used -= width.get(x, 2)
     return [x for x, _ in reloads.most_common() if width.get(x) == 1][:slots]
+
+
+def choose_smem_names(lines, slots: int, registers: int = 170):
+    """choose_smem_values over every named double of a column-group body:
+    computed values (t<id>) and the frontier values it loads (F<slot>,
+    defined by their load).  Returns the names, most reloaded first."""
+    tok = re.compile(r"\b([tF]\d+)\b")
+    defn = re.compile(r"\s*const double ([tF]\d+) = (.*);")
+    seq = []
+    for ln in lines:
+        m = defn.match(ln)
+        if m:
+            seq.append((m.group(1), tok.findall(m.group(2))))
+        else:
+            seq.append((None, tok.findall(ln)))
+    uses = {}
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            uses.setdefault(x, []).append(i)
+    pos = {x: 0 for x in uses}
+    resident, reloads = set(), Counter()
+
+    def next_use(x, i):
+        v = uses[x]
+        while pos[x] < len(v) and v[pos[x]] <= i:
+            pos[x] += 1
+        return v[pos[x]] if pos[x] < len(v) else None
+    for i, (d, u) in enumerate(seq):
+        for x in u:
+            if x not in resident:
+                reloads[x] += 1
+                resident.add(x)
+        if d is not None and d in uses:
+            resident.add(d)
+        nu = {x: next_use(x, i) for x in resident}
+        resident = {x for x in resident if nu[x] is not None}
+        if len(resident) > registers:
+            for x in sorted(resident, key=lambda y: (-nu[y], y))[:len(resident) - registers]:
+                resident.discard(x)
+    return [x for x, _ in reloads.most_common(slots)]
 
 
 def choose_smem_values(lines, slots: int, registers: int = 170):
@@ -735,7 +775,8 @@ def partition_jacobian(model, K: int, split_t: bool = True):
     return groups, sorted(frontier), needs
 
 
-def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: bool = False):
+def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: bool = False,
+                            smem_slots: int = 0):
     """Sources of the partitioned Jacobian: the prefix device function
     qss_jac_prefix(C, T, wdot, Tdot, wstride, fr, fstride) and, per group,
     qss_jac_group(fr, fstride, jac, jstride).  The frontier array fr holds,
@@ -744,7 +785,12 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: boo
     mixed-precision form (emit_jac32_source's split): the prefix computes
     what wdot and Tdot need in FP64 and its other values in FP32 (stored to
     the FP64 frontier widened); the group kernels, whose nodes wdot and Tdot
-    never need, compute in FP32 from the frontier values narrowed."""
+    never need, compute in FP32 from the frontier values narrowed.
+    smem_slots > 0 (FP64 form): in the prefix and in every group, the
+    values a 170-double register file would reload most often are kept in
+    dynamic shared memory as in the single kernel (choose_smem_values; in
+    the groups the frontier values are candidates too, choose_smem_names;
+    each kernel is launched with smem_slots * QSS_BLOCK doubles)."""
     ir = model.ir
     N = ir.N
     n = N + 1
@@ -766,42 +812,83 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: boo
     out_f = [(f"fr[{slot[x]} * fstride] = {{v}};", x) for x in frontier]
     if mixed and model.fd_vars is not None:
         raise ValueError("the mixed-precision Jacobian needs the analytic temperature column")
-    body_p, cnt_p = Emitter(model, inputs).emit(out_w + out_t + out_f, indent="  ",
-                                                fp64_outputs=(len(out_w) + len(out_t)) if mixed else None)
+    if mixed and smem_slots > 0:
+        raise ValueError("shared-memory values apply to the FP64 partitioned Jacobian")
+    smem_prologue = ["  extern __shared__ double qss_smem_dyn[];",
+                     "  volatile double* const qss_sm = qss_smem_dyn + threadIdx.x;"]
+
+    def emit_body(outs, leaves=None, fp64_outputs=None):
+        body, cnt = Emitter(model, inputs, leaves).emit(outs, indent="  ", fp64_outputs=fp64_outputs)
+        if smem_slots <= 0:
+            return body, cnt, [], 0
+        chosen = choose_smem_values(body, smem_slots)
+        em = Emitter(model, inputs, leaves)
+        em.smem_slot = {x: k for k, x in enumerate(chosen)}
+        body, cnt = em.emit(outs, indent="  ", fp64_outputs=fp64_outputs)
+        return body, cnt, (smem_prologue if chosen else []), len(chosen)
+
+    body_p, cnt_p, sm_p, used_p = emit_body(out_w + out_t + out_f,
+                                            fp64_outputs=(len(out_w) + len(out_t)) if mixed else None)
+    slots_used = [used_p]
     unpack = [f"  const double C{k} = C[{k}];" for k in range(N)]
     store_state = [f"  fr[{k} * fstride] = C{k};" for k in range(N)] + [f"  fr[{N} * fstride] = T;"]
     prefix = "\n".join([
         "__device__ __forceinline__ void qss_jac_prefix(const double* __restrict__ C, const double T,",
         "    double* __restrict__ wdot, double* __restrict__ Tdot, const long long wstride,",
         "    double* __restrict__ fr, const long long fstride) {",
-        *unpack, *store_state, *fd_prologue, *body_p, "}", ""])
+        *unpack, *store_state, *fd_prologue, *sm_p, *body_p, "}", ""])
     group_src, group_cnt = [], []
-    for gi, entries in enumerate(groups):
-        leaves = {x: f"F{slot[x]}" for x in needs[gi]}
-        out_j = [(f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries
-                 if (i, c) in pos]
-        body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ", fp64_outputs=0 if mixed else None)
-        loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
-        loads += [f"  const double T = fr[{N} * fstride];"]
+    def lazy_loads(body, pending):
         # each frontier value is loaded just before its first use: loaded all
         # at the top, a group's hundreds of values go straight from the load
         # to the spill stack
-        pending = {f"F{slot[x]}": f"  const double F{slot[x]} = fr[{slot[x]} * fstride];" for x in needs[gi]}
+        pending = dict(pending)
         lazy = []
-        for line in body_g:
+        for line in body:
             for nm in _FRONTIER_NAME.findall(line):
                 if nm in pending:
                     lazy.append(pending.pop(nm))
             lazy.append(line)
-        body_g = lazy + list(pending.values())
+        return lazy + list(pending.values())
+
+    for gi, entries in enumerate(groups):
+        leaves = {x: f"F{slot[x]}" for x in needs[gi]}
+        out_j = [(f"jac[{pos[(i, c)]} * jstride] = {{v}};", model.jac[i][c]) for i, c in entries
+                 if (i, c) in pos]
+        fp = 0 if mixed else None
+        body_g, cnt_g = Emitter(model, inputs, leaves).emit(out_j, indent="  ", fp64_outputs=fp)
+        pending = {f"F{slot[x]}": f"  const double F{slot[x]} = fr[{slot[x]} * fstride];" for x in needs[gi]}
+        body_g = lazy_loads(body_g, pending)
+        sm_g, used_g = [], 0
+        if smem_slots > 0:
+            # a group's most-reloaded values are mostly frontier values: those
+            # chosen are loaded into their shared-memory slot (the slot's
+            # expression keeps the F name in a comment, so that the load is
+            # still placed before the first use)
+            chosen = choose_smem_names(body_g, smem_slots)
+            if chosen:
+                node_of = {f"F{slot[x]}": x for x in needs[gi]}
+                leaves2 = dict(leaves)
+                for k, nm in enumerate(chosen):
+                    if nm[0] == "F":
+                        leaves2[node_of[nm]] = f"qss_sm[{k} * QSS_BLOCK /*{nm}*/]"
+                        pending[nm] = f"  qss_sm[{k} * QSS_BLOCK] = fr[{nm[1:]} * fstride];"
+                em = Emitter(model, inputs, leaves2)
+                em.smem_slot = {int(nm[1:]): k for k, nm in enumerate(chosen) if nm[0] == "t"}
+                body_g, cnt_g = em.emit(out_j, indent="  ", fp64_outputs=fp)
+                body_g = lazy_loads(body_g, pending)
+                sm_g, used_g = smem_prologue, len(chosen)
+        slots_used.append(used_g)
+        loads = [f"  const double C{k} = fr[{k} * fstride];" for k in range(N)]
+        loads += [f"  const double T = fr[{N} * fstride];"]
         group_src.append("\n".join([
             f"// entry group {gi} of {K}: columns {sorted({c for _, c in entries if c != N})}"
             + (f" and rows {sorted(i for i, c in entries if c == N)} of the T column" if any(c == N for _, c in entries) else ""),
             "__device__ __forceinline__ void qss_jac_group(const double* __restrict__ fr,",
             "    const long long fstride, double* __restrict__ jac, const long long jstride) {",
-            *loads, *fd_prologue, *body_g, "}", ""]))
+            *loads, *fd_prologue, *sm_g, *body_g, "}", ""]))
         group_cnt.append(cnt_g)
-    meta = {"jac_parts": K, "frontier": n + len(frontier), "groups": groups,
+    meta = {"jac_parts": K, "frontier": n + len(frontier), "groups": groups, "smem_slots_parts": slots_used,
             "ops_prefix": dict(cnt_p), "ops_groups": [dict(c) for c in group_cnt],
             "flops_jac_parts": algorithmic_flops(cnt_p) + sum(algorithmic_flops(c) for c in group_cnt)}
     return prefix, group_src, meta

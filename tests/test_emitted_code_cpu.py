@@ -235,3 +235,52 @@ def test_partitioned_mixed_precision_jacobian_within_fp32_bound(key, K):
     err = np.abs(J - ref["jac"])
     assert np.all(np.isfinite(J))
     assert np.all(err <= 2.0 ** 29 * eb["jac"] + 1e-20), float(np.max(err / (2.0 ** 29 * eb["jac"] + 1e-20)))
+
+
+@pytest.mark.parametrize("key,K,slots", [("tiny", 2, 16), ("hydrocarbon", 4, 60)])
+def test_partitioned_jacobian_with_shared_memory_values(key, K, slots):
+    """The FP64 partitioned Jacobian with its most-reloaded values kept in
+    shared memory (smem_slots in the prefix and in every column group),
+    compiled on the CPU: the same gate against the oracle as the GPU tests.
+    A kernel whose values all fit the simulated register file gets no slots
+    (the tiny mechanism's column groups)."""
+    model = _model(key)
+    src, meta = emit.emit_mechanism_source(model)
+    prefix, groups, pmeta = emit.emit_partitioned_source(model, K, smem_slots=slots)
+    assert len(pmeta["smem_slots_parts"]) == K + 1
+    assert all(0 <= u <= slots for u in pmeta["smem_slots_parts"]) and pmeta["smem_slots_parts"][0] > 0
+    for u, s_ in zip(pmeta["smem_slots_parts"], [prefix] + groups):
+        assert ("qss_sm[" in s_) == (u > 0)
+    n = meta["N"] + 1
+    nfr = pmeta["frontier"]
+    iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
+    # each group is its own kernel (its own dynamic shared memory): one array
+    # per namespace here
+    body = src[:iw] + prefix + "".join(f"namespace g{i} {{\ndouble qss_smem_dyn[16384];\n{g}}}\n"
+                                       for i, g in enumerate(groups))
+    calls = "".join(f"    g{i}::qss_jac_group(fr, 1, jac + c, n);\n" for i in range(K))
+    drv = ("extern \"C\" void eval_cells(long long n, const double* C, const double* T, double* wdot,"
+           " double* Tdot, double* jac) {\n"
+           f"  static double fr[{nfr}];\n"
+           "  for (long long c = 0; c < n; ++c) {\n"
+           "    double Cc[QSS_N];\n"
+           "    for (int k = 0; k < QSS_N; ++k) Cc[k] = C[k * n + c];\n"
+           "    qss_jac_prefix(Cc, T[c], wdot + c, Tdot + c, n, fr, 1);\n" + calls + "  }\n}\n")
+    d = tempfile.mkdtemp(prefix="qss_emitps_")
+    cpp = os.path.join(d, "gen.cpp")
+    with open(cpp, "w") as f:
+        f.write(_SHIM + body + drv)
+    so = os.path.join(d, "gen.so")
+    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    p = ctypes.POINTER(ctypes.c_double)
+    L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
+    m = workloads.mechanism(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], 128)
+    om = oracle.OracleMech(m)
+    w, td, J = _run(L, om.conc(rho, Y), T, n * n)
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    assert_gate("wdot", w, ref["wdot"], eb["wdot"])
+    assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
+    assert_gate("jac", J, ref["jac"], eb["jac"])

@@ -46,6 +46,25 @@ def test_partitioned_parity(key, parts, ncells):
     print(key, parts, r)
 
 
+@pytest.mark.parametrize("key,parts,slots,ncells", [("tiny", 2, 16, 3000), ("hydrocarbon", 4, 60, 1500)])
+def test_partitioned_shared_memory_values(key, parts, slots, ncells):
+    """The partitioned Jacobian with its most-reloaded values in dynamic
+    shared memory (smem_slots in the prefix and in the column groups that
+    spill): the oracle's gate, as the plain partitioned form (the same
+    operations; where values live differs, and with it the compiler's
+    multiply-add contraction of the few products it may fuse itself)."""
+    m = workloads.mechanism(key)
+    om = oracle.OracleMech(m)
+    gm = binding.Mechanism(build_mechanism(m, jac_parts=parts, smem_slots=slots), 0)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    J, w, td = gm.jacobian(dev(rho), dev(T), dev(Y))
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    assert_gate("wdot", w.cpu().numpy(), ref["wdot"], eb["wdot"])
+    assert_gate("Tdot", td.cpu().numpy(), ref["Tdot"], eb["Tdot"])
+    assert_gate("jac", J.cpu().numpy(), ref["jac"], eb["jac"])
+
+
 def test_partitioned_several_frontier_chunks():
     """150000 hydrocarbon cells through a frontier buffer limited to 400 MB
     (about 34000 cells a chunk), against the single-kernel Jacobian
