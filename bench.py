@@ -944,8 +944,8 @@ def main():
                    "budget_bytes": 60 << 30, "load": 0.7, "graphs": True,
                    "capacity": "cells/s of one implicit step of 65536 cells per mechanism, "
                                "combined by the mix's cell-weighted harmonic mean"}
-        # mixed: the mixed-precision Jacobian where the artefact has it (the
-        # large mechanism's partitioned Jacobian has no mixed form: FP32-IR)
+        # mixed: the mixed-precision Jacobian where the artefact has it (single
+        # kernel or partitioned), else FP32-IR
         mixed = {k: (binding.QSS_LU_MIXED if mechs[k].has_jac32 else binding.QSS_LU_FP32_IR) for k in mechs}
         serving["mixed_precision_by_mechanism"] = {k: ("mixed" if v == binding.QSS_LU_MIXED else "fp32ir")
                                                    for k, v in mixed.items()}
