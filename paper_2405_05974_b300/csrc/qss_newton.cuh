@@ -249,6 +249,62 @@ __device__ __forceinline__ float qss_pow2f_neg(int s) {
 #define QSS_R2 (QSS_RLAST <= 1 ? 1 : QSS_RLAST <= 2 ? 2 : QSS_RLAST <= 4 ? 4 : QSS_RLAST <= 8 ? 8 : 16)
 #define QSS_G (32 / QSS_R2)
 
+// One pivot step k of the FP32 factorisation of qss_solve_fp32ir, on rows
+// whose live part is their first W entries (the rows are shifted left one
+// column per step, so from step NN - W on every entry j >= W is zero and
+// stays zero): warp argmax of |A[.][0]| over the rows not yet pivoted (lowest
+// row on ties), the pivot row broadcast, its U part and the multipliers
+// stored to LU, and the elimination fused with the shift.  Returns false on
+// a zero, infinite or NaN pivot.
+template <int W>
+__device__ __forceinline__ bool qss_lu32_step(const int k, float (&A)[QSS_NSLOT][QSS_NN], int (&ord)[QSS_NSLOT],
+                                              const bool (&live)[QSS_NSLOT], float* __restrict__ LU,
+                                              int* __restrict__ piv, float* __restrict__ pinv, const int lane) {
+  int best = -1, brow = QSS_NN;
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+    const int key = (live[sl] && ord[sl] < 0) ? (__float_as_int(A[sl][0]) & 0x7fffffff) : -1;
+    if (key > best) { best = key; brow = lane + 32 * sl; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+    if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+  }
+  if (best <= 0 || best >= 0x7f800000) return false;   // zero, inf or NaN pivot
+  const int pl = brow & 31, ps = brow >> 5;
+  float p[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    float v = A[0][j];
+#pragma unroll
+    for (int sl = 1; sl < QSS_NSLOT; ++sl)
+      if (ps == sl) v = A[sl][j];
+    p[j] = __shfl_sync(0xffffffffu, v, pl);
+  }
+  const float inv = 1.0f / p[0];
+  if (lane == 0) { piv[k] = brow; pinv[k] = inv; }
+  if (lane == pl) {   // the pivot row's U part, columns k..NN-1
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (j < QSS_NN - k) LU[brow * QSS_MSTRIDE + k + j] = p[j];
+  }
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl)
+    if (lane == pl && ps == sl) ord[sl] = k;
+#pragma unroll
+  for (int sl = 0; sl < QSS_NSLOT; ++sl) {
+    const bool el = live[sl] && ord[sl] < 0;
+    const float l = el ? A[sl][0] * inv : 0.0f;
+    if (el) LU[(lane + 32 * sl) * QSS_MSTRIDE + k] = l;
+#pragma unroll
+    for (int j = 0; j + 1 < W; ++j) A[sl][j] = fmaf(-l, p[j + 1], A[sl][j + 1]);
+    A[sl][W - 1] = 0.0f;
+  }
+  return true;
+}
+
 // FP32 LU with FP64 iterative refinement of one cell's Newton system
 // (I - h J) x = g.  J (FP64) is in shared memory, row r at Js[r * QSS_MSTRIDE];
 // the warp's lanes own rows lane + 32 slot.
@@ -259,9 +315,10 @@ __device__ __forceinline__ float qss_pow2f_neg(int s) {
 //   = hm * float(J_rj 2^(eh - s)) with h = hm 2^eh, plus 2^-s on the diagonal
 //   (integer and FP32 operations only).
 //   Factorisation: compact by design (an unrolled FP32 elimination is
-//   fetch-bound): a loop over pivot steps with the live rows in registers
+//   fetch-bound): loops over pivot steps with the live rows in registers
 //   shifted left by one column per step (the pivot column is always entry 0,
-//   the shift folds into the elimination FMA); L and U go to shared memory
+//   the shift folds into the elimination FMA), in four phases of decreasing
+//   static width (qss_lu32_step); L and U go to shared memory
 //   (LU[r][k]: multiplier of row r at step k before its pivot step, its U row
 //   from there on), and the substitutions are loops over them.
 //   Refinement: r = g - x + h (J x) in FP64 (the rows of a thin last slot
@@ -337,52 +394,22 @@ __device__ __forceinline__ bool qss_solve_fp32ir(const double* __restrict__ Js, 
       A[sl][j] = v;
     }
   }
-  // factorisation, one pivot step per iteration
+  // factorisation, one pivot step per iteration, in four phases whose
+  // static width is the live part of the shifted rows (NN - k0 columns from
+  // pivot step k0 on): 2.5/4 of the full-width work for NN = 36
+  constexpr int K1 = (QSS_NN + 3) / 4, K2 = (2 * QSS_NN + 3) / 4, K3 = (3 * QSS_NN + 3) / 4;
 #pragma unroll 1
-  for (int k = 0; k < QSS_NN; ++k) {
-    int best = -1, brow = QSS_NN;
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const int key = (live[sl] && ord[sl] < 0) ? (__float_as_int(A[sl][0]) & 0x7fffffff) : -1;
-      if (key > best) { best = key; brow = lane + 32 * sl; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const int ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
-      if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
-    }
-    if (best <= 0 || best >= 0x7f800000) return false;   // zero, inf or NaN pivot
-    const int pl = brow & 31, ps = brow >> 5;
-    float p[QSS_NN];
-#pragma unroll
-    for (int j = 0; j < QSS_NN; ++j) {
-      float v = A[0][j];
-#pragma unroll
-      for (int sl = 1; sl < QSS_NSLOT; ++sl)
-        if (ps == sl) v = A[sl][j];
-      p[j] = __shfl_sync(0xffffffffu, v, pl);
-    }
-    const float inv = 1.0f / p[0];
-    if (lane == 0) { piv[k] = brow; pinv[k] = inv; }
-    if (lane == pl) {   // the pivot row's U part, columns k..NN-1
-#pragma unroll
-      for (int j = 0; j < QSS_NN; ++j)
-        if (j < QSS_NN - k) LU[brow * QSS_MSTRIDE + k + j] = p[j];
-    }
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl)
-      if (lane == pl && ps == sl) ord[sl] = k;
-#pragma unroll
-    for (int sl = 0; sl < QSS_NSLOT; ++sl) {
-      const bool el = live[sl] && ord[sl] < 0;
-      const float l = el ? A[sl][0] * inv : 0.0f;
-      if (el) LU[(lane + 32 * sl) * QSS_MSTRIDE + k] = l;
-#pragma unroll
-      for (int j = 0; j + 1 < QSS_NN; ++j) A[sl][j] = fmaf(-l, p[j + 1], A[sl][j + 1]);
-      A[sl][QSS_NN - 1] = 0.0f;
-    }
-  }
+  for (int k = 0; k < K1; ++k)
+    if (!qss_lu32_step<QSS_NN>(k, A, ord, live, LU, piv, pinv, lane)) return false;
+#pragma unroll 1
+  for (int k = K1; k < K2; ++k)
+    if (!qss_lu32_step<QSS_NN - K1>(k, A, ord, live, LU, piv, pinv, lane)) return false;
+#pragma unroll 1
+  for (int k = K2; k < K3; ++k)
+    if (!qss_lu32_step<QSS_NN - K2>(k, A, ord, live, LU, piv, pinv, lane)) return false;
+#pragma unroll 1
+  for (int k = K3; k < QSS_NN; ++k)
+    if (!qss_lu32_step<QSS_NN - K3>(k, A, ord, live, LU, piv, pinv, lane)) return false;
   __syncwarp();
   // refinement: r = g - x + h (J x) in FP64, correction from the FP32 factors
 #pragma unroll
