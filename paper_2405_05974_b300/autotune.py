@@ -21,14 +21,16 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
                prefix kernel plus K column-group kernels (2, 4, 8) exchanging
                per-cell values through a frontier buffer (with 60 or 100
                shared-memory slots in each of its kernels as well)
+  cells per thread  1 or 2 (cells_per_thread; 2 at 128 and 64 threads): each
+               thread evaluates two cells, the generated body and its copy
+               interleaved line by line (twice the independent work per
+               warp, twice the live values)
 
 (A warp-slice per cell, K lanes of a warp cooperating on one cell's DAG, is
 not in the grid: on this part an FP64 instruction occupies the FP64 pipe for
 the whole warp whatever its active lanes (measured), so lanes that compute
 different DAG nodes multiply the FP64 time by K; the column split across
-kernels is the register-pressure split that keeps every lane busy.  Two cells
-per thread, the generated body duplicated, doubles the live values and the
-stack and measured 5 % slower, so one cell per thread throughout.)
+kernels is the register-pressure split that keeps every lane busy.)
 
 Each candidate artefact is built ahead of time (``--build-only``, CPU), then
 timed with CUDA events on two batch sizes of the workload's states (65536
@@ -84,6 +86,7 @@ def candidates(key: str) -> List[dict]:
             # shared-memory slots as that many blocks per SM leave room for
             {**base, "defines": ("QSS_MINBLOCKS=3",), "smem_slots": 64},
             {**base, "defines": ("QSS_MINBLOCKS=4",), "smem_slots": 48},
+            {**base, "cells_per_thread": 2}, {**base, "cells_per_thread": 2, "block": 64},
             {**base, "jac_parts": 4}]
 
 

@@ -49,6 +49,9 @@ struct qss_mech_s {
   // dynamic shared memory of the single Jacobian kernel (bytes per block):
   // smem_slots doubles per thread hold its most-reloaded values
   int smem_slots = 0;
+  // cells per thread of the FP64 Jacobian kernel (1, or 2: its grid covers
+  // half the cells)
+  int cpt = 1;
   unsigned jac_smem = 0;
   // stored Jacobian entries per cell and their pattern (CSR; dense = all)
   int64_t jac_nnz = 0;

@@ -114,7 +114,8 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   }
   if (m->jac_parts < 2) {
     void* args[] = {&nc, &l, &rho, &T, &Y, &jac, &wdot, &Tdot, &phi, &list, &nact, &nact_next};
-    return launch_cells(m, m->f_jac, ncells, m->block, args, s, m->jac_smem);
+    // with two cells per thread the grid covers half the cells
+    return launch_cells(m, m->f_jac, (ncells + m->cpt - 1) / m->cpt, m->block, args, s, m->jac_smem);
   }
   if (!fr || fld < ncells) return fail(QSS_ERR_INVALID_ARG, "frontier scratch too small");
   long long fl = fld;
@@ -195,6 +196,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
     else if (key == "frontier") ls >> m->frontier;
     else if (key == "jac_nnz") ls >> m->jac_nnz;
     else if (key == "smem_slots") ls >> m->smem_slots;
+    else if (key == "cpt") ls >> m->cpt;
     else if (key == "jac32") ls >> m->jac32;
     else if (key == "jac32_slots") ls >> m->jac32_slots;
     else if (key == "cubin") {
@@ -213,7 +215,8 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   }
   if (m->N <= 0 || m->Q < 0 || m->M <= 0 || m->block <= 0 || (int)m->W.size() != m->N ||
       m->jac_parts < 0 || m->jac_parts > 64 || (m->jac_parts >= 2 && m->frontier <= m->N) ||
-      m->smem_slots < 0 || m->smem_slots > 1024 ||
+      m->smem_slots < 0 || m->smem_slots > 1024 || m->cpt < 1 || m->cpt > 2 ||
+      (m->cpt == 2 && (m->jac_parts >= 2 || m->smem_slots > 0)) ||
       m->jac32 < 0 || m->jac32 > 1 || m->jac32_slots < 0 || m->jac32_slots > 2048 ||
       (m->jac32_slots > 0 && (!m->jac32 || m->jac_parts >= 2)) ||
       !jac_pattern_ok(m)) {
@@ -336,7 +339,7 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
   if (drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m->jac_parts >= 2 ? m->f_prefix : m->f_jac,
                                                         m->block, m->jac_smem) != CUDA_SUCCESS)
     per_sm = 0;
-  m->wave_cells = (int64_t)std::max(sms, 0) * std::max(per_sm, 0) * m->block;
+  m->wave_cells = (int64_t)std::max(sms, 0) * std::max(per_sm, 0) * m->block * (m->jac_parts >= 2 ? 1 : m->cpt);
   for (int i = 0; i < 2; ++i) {
     int upd_per_sm = 0;
     if (m->f_newton[i] && sms > 0 &&

@@ -36,7 +36,7 @@ NVCC = os.environ.get("QSS_NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 TEMPLATES = ["qss_device.cuh", "qss_exp_table.inc", "qss_log_table.inc", "qss_cells.cuh",
              "qss_jac_kernel.cuh", "qss_jac_parts.cuh", "qss_wdot_kernels.cuh", "qss_newton.cuh",
-             "qss_convert.h", "qss_jac32_kernel.cuh"]
+             "qss_convert.h", "qss_jac32_kernel.cuh", "qss_jac2_kernel.cuh"]
 ARTEFACT_FILES = ("meta.txt", "meta.json")   # plus the cubins meta.txt names
 COMPILER_VERSION = "1"
 
@@ -166,7 +166,7 @@ def _write_index(root: str, fast: str, name: str):
 
 
 def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-             jac32=False, jac32_slots=0, jac32_minblocks=1) -> tuple:
+             jac32=False, jac32_slots=0, jac32_minblocks=1, cells_per_thread=1) -> tuple:
     """The build options other than block and defines, as index-key parts."""
     variant = () if (jac_variant, t_column) == ("exact", "analytic") else (f"{jac_variant}/{t_column}",)
     if jac_parts >= 2:
@@ -193,18 +193,23 @@ def _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_ord
         if not jac32 or jac_parts >= 2:
             raise ValueError("jac32_minblocks applies to the single-kernel mixed-precision Jacobian")
         variant += (f"j32mb{int(jac32_minblocks)}",)
+    if cells_per_thread != 1:
+        if cells_per_thread != 2 or jac_parts >= 2 or smem_slots > 0 or t_column != "analytic":
+            raise ValueError("cells_per_thread = 2 applies to the single FP64 Jacobian kernel without "
+                             "shared-memory values, analytic temperature column")
+        variant += ("cpt2",)
     return variant
 
 
 def find_artefact(mech: dict, root: str = None, block: int = 128, defines=(), jac_variant: str = "exact",
                   t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
                   jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0, ptxas=(),
-                  jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1):
+                  jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1, cells_per_thread: int = 1):
     """The directory of an artefact already built with these options for the
     current templates, or None (never compiles)."""
     root = root or DEFAULT_ROOT
     variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-                       jac32, jac32_slots, jac32_minblocks)
+                       jac32, jac32_slots, jac32_minblocks, cells_per_thread)
     name = _read_index(root).get(artefact_key(mech, block, tuple(defines) + variant))
     return os.path.join(root, name) if name and _complete(os.path.join(root, name)) else None
 
@@ -257,7 +262,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
                     force: bool = False, verbose: bool = False, jac_variant: str = "exact",
                     t_column: str = "analytic", jac_parts: int = 0, replace_nop: int = 0,
                     jac_format: str = "dense", emit_order: str = "first_use", smem_slots: int = 0,
-                    ptxas=(), jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1) -> str:
+                    ptxas=(), jac32: bool = False, jac32_slots: int = 0, jac32_minblocks: int = 1,
+                    cells_per_thread: int = 1) -> str:
     """Generate, compile and cache the artefact of one mechanism.
 
     ``jac_variant`` / ``t_column`` select the Jacobian that the kernels
@@ -274,6 +280,9 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     as it is final); ``smem_slots`` > 0 keeps that many of the FP64 Jacobian
     kernel's most-reloaded values in shared memory (dynamic, per thread; with
     ``jac_parts`` in the prefix and in each column-group kernel);
+    ``cells_per_thread`` = 2 makes each thread of the FP64 Jacobian kernel
+    evaluate two cells (the body and its copy interleaved,
+    ``emit.two_cell_body``, in the kernel of qss_jac2_kernel.cuh);
     ``ptxas`` are extra ptxas options (``"regUsageLevel=0"`` is passed as
     ``-Xptxas -regUsageLevel=0``); ``jac32`` also builds ``jac32.cubin``, the
     mixed-precision Jacobian kernel (derivative terms in FP32,
@@ -282,7 +291,7 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     ``jac32_minblocks`` blocks per SM in its register budget (its own
     __launch_bounds__, so the other cubins are unaffected)."""
     variant = _variant(jac_variant, t_column, jac_parts, replace_nop, jac_format, emit_order, smem_slots, ptxas,
-                       jac32, jac32_slots, jac32_minblocks)
+                       jac32, jac32_slots, jac32_minblocks, cells_per_thread)
     # fast path: the key of (mechanism, options, generator, templates) in the
     # index of built artefacts
     fast = artefact_key(mech, block, tuple(defines) + variant)
@@ -294,7 +303,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     model = qmodel.build_model(ir, jac_variant=jac_variant, t_column=t_column)
     src, meta = emit.emit_mechanism_source(model, replace_nop=replace_nop, jac_format=jac_format,
                                            emit_order=emit_order,
-                                           smem_slots=smem_slots if jac_parts < 2 else 0)
+                                           smem_slots=smem_slots if jac_parts < 2 else 0,
+                                           cells_per_thread=cells_per_thread)
     # sizes and constants / the source term / the Jacobian, one file each
     iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
     ij = src.index("__device__ __forceinline__ void qss_eval_jac")
@@ -328,7 +338,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
     # keeps its artefacts)
     hk = hashlib.sha256(json.dumps([sorted(parts.items()), sorted(hdr.items()), flags,
                                     meta.get("jac_variant"), meta.get("t_column"), jac_parts]
-                                   + ([jac32_minblocks] if jac32_minblocks != 1 else [])).encode())
+                                   + ([jac32_minblocks] if jac32_minblocks != 1 else [])
+                                   + (["cpt2"] if cells_per_thread == 2 else [])).encode())
     art_name = f"{mech.get('name', 'mech')}_{hk.hexdigest()[:20]}"
     out = os.path.join(root, art_name)
     if not force and _complete(out):
@@ -358,9 +369,9 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
             units[f"jac_g{i}"] = (pre + f'#include "{nm}"\n#define QSS_JAC_GROUP\n#include "qss_jac_parts.cuh"\n',
                                   {**common, **cells, **jp, nm: parts[nm]})
     else:
-        units["jac"] = (pre + '#include "mech_jac.inc"\n#include "qss_jac_kernel.cuh"\n',
-                        {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"],
-                         "qss_jac_kernel.cuh": hdr["qss_jac_kernel.cuh"]})
+        kt = "qss_jac2_kernel.cuh" if cells_per_thread == 2 else "qss_jac_kernel.cuh"
+        units["jac"] = (pre + f'#include "mech_jac.inc"\n#include "{kt}"\n',
+                        {**common, **cells, "mech_jac.inc": parts["mech_jac.inc"], kt: hdr[kt]})
     if jac32 and jac_parts >= 2:
         jp = {"qss_jac_parts.cuh": hdr["qss_jac_parts.cuh"], "qss_convert.h": hdr["qss_convert.h"]}
         cv = '#include "qss_convert.h"\n'
@@ -423,6 +434,8 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         f.write(f"jac_nnz {meta['jac_stored']}\n")
         if jac32:
             f.write("jac32 1\n")
+        if cells_per_thread == 2:
+            f.write("cpt 2\n")
         if meta.get("jac32_slots", 0) > 0:
             f.write(f"jac32_slots {int(meta['jac32_slots'])}\n")
         if meta.get("smem_slots", 0) > 0:   # slots the emitted code uses (at most the requested)

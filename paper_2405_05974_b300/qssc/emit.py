@@ -515,9 +515,29 @@ def jac_layout(model, jac_format: str = "dense"):
     return pos, row_ptr, col
 
 
+_RENAME_B = [(re.compile(r"\bt(\d+)\b"), r"tb\1"), (re.compile(r"\bC(\d+)\b"), r"Cb\1"),
+             (re.compile(r"\bT\b"), "Tb"), (re.compile(r"^(\s*)jac\["), r"\1if (jac_b) jac_b["),
+             (re.compile(r"\bwdot\b"), "wdot_b"), (re.compile(r"\bTdot\b"), "Tdot_b")]
+
+
+def two_cell_body(lines):
+    """The Jacobian body for two cells per thread: every line of the one-cell
+    body (cell a) followed by its copy for cell b (values t<id> -> tb<id>,
+    inputs C<k>, T -> Cb<k>, Tb, outputs through jac_b / wdot_b / Tdot_b,
+    a null jac_b skipping cell b's stores), so that the two cells'
+    independent chains interleave."""
+    out = []
+    for ln in lines:
+        b = ln
+        for rx, rep in _RENAME_B:
+            b = rx.sub(rep, b)
+        out += [ln, b]
+    return out
+
+
 def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
                           jac_format: str = "dense", emit_order: str = "first_use",
-                          col_order=None, smem_slots: int = 0) -> Tuple[str, dict]:
+                          col_order=None, smem_slots: int = 0, cells_per_thread: int = 1) -> Tuple[str, dict]:
     ir = model.ir
     N, Q = ir.N, ir.Q
     n = N + 1
@@ -589,11 +609,27 @@ def emit_mechanism_source(model, block_hint=128, replace_nop: int = 0,
         "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
         "    const long long wstride, const long long jstride) {",
         *unpack, *fd_prologue, *smem_prologue, *body_j, "}", ""])
+    if cells_per_thread == 2:
+        # two cells per thread (qss_jac2_kernel.cuh): the one-cell
+        # body and its copy for the second cell, interleaved line by line
+        if smem_slots > 0 or model.fd_vars is not None:
+            raise ValueError("two cells per thread are emitted without shared-memory values and with "
+                             "the analytic temperature column")
+        unpack_b = [f"  const double Cb{k} = Cb_in[{k}];" for k in range(N)]
+        src += "\n".join([
+            "__device__ __forceinline__ void qss_eval_jac2(const double* __restrict__ C, const double T,",
+            "    double* __restrict__ wdot, double* __restrict__ Tdot, double* __restrict__ jac,",
+            "    const double* __restrict__ Cb_in, const double Tb, double* __restrict__ wdot_b,",
+            "    double* __restrict__ Tdot_b, double* __restrict__ jac_b,",
+            "    const long long wstride, const long long jstride) {",
+            *unpack, *unpack_b, *two_cell_body(body_j), "}", ""])
+    elif cells_per_thread != 1:
+        raise ValueError("cells_per_thread is 1 or 2")
     meta = {
         "N": N, "Q": Q, "M": len(ir.rxns), "n": n, "digest": ir.digest, "name": ir.name,
         "W": ir.W, "species": ir.names, "groups": model.groups,
         "jac_variant": model.jac_variant, "t_column": model.t_column, "replace_nop": replace_nop,
-        "emit_order": emit_order, "smem_slots": len(em2.smem_slot),
+        "emit_order": emit_order, "smem_slots": len(em2.smem_slot), "cells_per_thread": cells_per_thread,
         "jac_format": jac_format, "jac_stored": len(col), "jac_row_ptr": row_ptr, "jac_col": col,
         "ops_wdot": dict(cnt_w), "ops_jac": dict(cnt_j),
         "flops_wdot": algorithmic_flops(cnt_w), "flops_jac": algorithmic_flops(cnt_j),

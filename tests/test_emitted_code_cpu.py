@@ -284,3 +284,62 @@ def test_partitioned_jacobian_with_shared_memory_values(key, K, slots):
     assert_gate("wdot", w, ref["wdot"], eb["wdot"])
     assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
     assert_gate("jac", J, ref["jac"], eb["jac"])
+
+
+_DRIVER2 = r"""
+extern "C" void eval_cells2(long long n, const double* C, const double* T, double* wdot, double* Tdot,
+                            double* jac) {
+  // cells c and c + h per call (the kernel's two-cells-per-thread form); an
+  // odd last cell is computed twice, its copy's Jacobian stores skipped
+  const long long h = (n + 1) / 2;
+  for (long long c = 0; c < h; ++c) {
+    const long long d = c + h < n ? c + h : c;
+    double Ca[QSS_N], Cb[QSS_N];
+    for (int k = 0; k < QSS_N; ++k) { Ca[k] = C[k * n + c]; Cb[k] = C[k * n + d]; }
+    qss_eval_jac2(Ca, T[c], wdot + c, Tdot + c, jac + c, Cb, T[d], wdot + d, Tdot + d,
+                  d != c ? jac + d : nullptr, n, n);
+  }
+}
+"""
+
+
+@pytest.mark.parametrize("key,ncells", [("tiny", 255), ("hydrocarbon", 129)])
+def test_two_cells_per_thread_body_matches_oracle(key, ncells):
+    """The two-cells-per-thread Jacobian body (cells_per_thread = 2: the
+    one-cell body and its renamed copy interleaved), compiled on the CPU for
+    an odd number of cells (the last one evaluated as both cells with the
+    second copy's Jacobian stores skipped): the oracle's gate for every cell,
+    and bit for bit the one-cell body's results (the same operations)."""
+    model = _model(key)
+    src1, meta = emit.emit_mechanism_source(model)
+    src, meta2 = emit.emit_mechanism_source(model, cells_per_thread=2)
+    assert meta2["cells_per_thread"] == 2 and "qss_eval_jac2" in src
+    iw = src.index("__device__ __forceinline__ void qss_eval_wdot")
+    ij = src.index("__device__ __forceinline__ void qss_eval_jac")
+    d = tempfile.mkdtemp(prefix="qss_emit2_")
+    cpp = os.path.join(d, "gen.cpp")
+    with open(cpp, "w") as f:
+        f.write(_SHIM + src[:iw] + src[ij:] + _DRIVER2)
+    so = os.path.join(d, "gen.so")
+    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    p = ctypes.POINTER(ctypes.c_double)
+    L.eval_cells2.argtypes = [ctypes.c_longlong, p, p, p, p, p]
+    m = workloads.mechanism(key)
+    rho, T, Y = mechgen.generate_states(m, workloads.STATES[key], ncells)
+    om = oracle.OracleMech(m)
+    C = np.ascontiguousarray(om.conc(rho, Y))
+    T = np.ascontiguousarray(T)
+    n = meta["N"] + 1
+    w = np.zeros((meta["N"], ncells))
+    td = np.zeros(ncells)
+    J = np.zeros((n * n, ncells))
+    q = lambda a: a.ctypes.data_as(p)  # noqa: E731
+    L.eval_cells2(ncells, q(C), q(T), q(w), q(td), q(J))
+    ref = om.eval(rho, T, Y)
+    eb = om.errbound(rho, T, Y)
+    assert_gate("wdot", w, ref["wdot"], eb["wdot"])
+    assert_gate("Tdot", td, ref["Tdot"], eb["Tdot"])
+    assert_gate("jac", J, ref["jac"], eb["jac"])
+    w1, td1, J1 = _run(_compile(src1), C, T, n * n)
+    assert np.array_equal(J, J1) and np.array_equal(w, w1) and np.array_equal(td, td1)
