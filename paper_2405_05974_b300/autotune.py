@@ -21,7 +21,7 @@ mechanism and the GPU, so it is measured.  The searched grid, per mechanism:
                prefix kernel plus K column-group kernels (2, 4, 8) exchanging
                per-cell values through a frontier buffer (with 60 or 100
                shared-memory slots in each of its kernels as well)
-  cells per thread  1 or 2 (cells_per_thread; 2 at 128 and 64 threads): each
+  cells per thread  1 or 2 (cells_per_thread; 2 at 128 threads): each
                thread evaluates two cells, the generated body and its copy
                interleaved line by line (twice the independent work per
                warp, twice the live values)
@@ -86,7 +86,7 @@ def candidates(key: str) -> List[dict]:
             # shared-memory slots as that many blocks per SM leave room for
             {**base, "defines": ("QSS_MINBLOCKS=3",), "smem_slots": 64},
             {**base, "defines": ("QSS_MINBLOCKS=4",), "smem_slots": 48},
-            {**base, "cells_per_thread": 2}, {**base, "cells_per_thread": 2, "block": 64},
+            {**base, "cells_per_thread": 2},
             {**base, "jac_parts": 4}]
 
 
