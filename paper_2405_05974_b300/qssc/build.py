@@ -231,6 +231,10 @@ def prune_artefacts(keep, root: str = None) -> list:
         os.replace(tmp, os.path.join(root, "index.json"))
         for d in sorted(os.listdir(root)):
             p = os.path.join(root, d)
+            # a ".tmp" directory younger than a day belongs to a build still
+            # running in another process
+            if ".tmp" in d and time.time() - os.path.getmtime(p) < 86400:
+                continue
             if os.path.isdir(p) and d not in keep_names and d != SHARED:
                 shutil.rmtree(p, ignore_errors=True)
                 removed.append(d)
