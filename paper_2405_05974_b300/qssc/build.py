@@ -333,9 +333,6 @@ def build_mechanism(mech: dict, root: str = DEFAULT_ROOT, block: int = 128, defi
         for i, gsrc in enumerate(g32):
             parts[f"mech_jac32_g{i}.inc"] = gsrc
         meta.update({"ops_prefix32": pm32["ops_prefix"], "ops_groups32": pm32["ops_groups"]})
-        # one frontier buffer serves both forms: the larger of the two
-        meta["frontier"] = max(meta["frontier"], pm32["frontier"])
-        meta["frontier32"] = pm32["frontier"]
     hdr = {t: open(os.path.join(CSRC, t)).read() for t in TEMPLATES}
     flags = [f"-DQSS_BLOCK={block}", *[f"-D{d}" for d in defines]]
     for o in ptxas:

@@ -713,7 +713,7 @@ def _op_cost(g, x):
     return 1 if op in _MATERIAL else 0
 
 
-def partition_jacobian(model, K: int, split_t: bool = True, values_only: bool = False):
+def partition_jacobian(model, K: int, split_t: bool = True):
     """Split the Jacobian's entries into K groups (whole concentration
     columns, balanced by cost; the temperature column by rows when split_t)
     and its DAG into the part needed by two or more groups (the prefix,
@@ -721,13 +721,7 @@ def partition_jacobian(model, K: int, split_t: bool = True, values_only: bool = 
     Returns (groups, frontier, needs): the (row, column) entries of each
     group, the prefix values a group kernel reads (node ids, in topological
     order), and for each group the frontier nodes it reads.  Every operation
-    of the DAG is computed exactly once.
-
-    values_only: the prefix holds only what wdot and Tdot need (the source
-    term's values); a derivative node that several groups need is computed
-    by each of them instead of being passed through the frontier (the
-    mixed-precision form, where those nodes are FP32 operations that cost
-    little next to the frontier traffic and the prefix's spills)."""
+    of the DAG is computed exactly once."""
     g = model.g
     N = model.ir.N
     n = N + 1
@@ -792,14 +786,6 @@ def partition_jacobian(model, K: int, split_t: bool = True, values_only: bool = 
         load[gi] += col_cost[c]
     m = masks(col_group, K)
     shared = {x for x in order if m[x] & (m[x] - 1)}
-    if values_only:
-        val, st = set(), list(roots_w)
-        while st:
-            x = st.pop()
-            if x not in val:
-                val.add(x)
-                st.extend(kids(x))
-        shared &= val
     # frontier: shared computed values reached from a group's own nodes
     # (through inline operations such as negation)
     needs = []
@@ -833,11 +819,9 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: boo
     per cell, C_1..C_N and T in slots 0..N, then the prefix values the groups
     read (slot N + 1 + i for the i-th frontier node).  mixed: the
     mixed-precision form (emit_jac32_source's split): the prefix computes
-    only what wdot and Tdot need, in FP64, and passes the values the groups
-    use through the frontier; the group kernels, whose nodes wdot and Tdot
-    never need, compute in FP32 from the frontier values narrowed, each
-    recomputing the derivative nodes it shares with other groups
-    (partition_jacobian's values_only).
+    what wdot and Tdot need in FP64 and its other values in FP32 (stored to
+    the FP64 frontier widened); the group kernels, whose nodes wdot and Tdot
+    never need, compute in FP32 from the frontier values narrowed.
     smem_slots > 0 (FP64 form): in the prefix and in every group, the
     values a 170-double register file would reload most often are kept in
     dynamic shared memory as in the single kernel (choose_smem_values; in
@@ -846,9 +830,7 @@ def emit_partitioned_source(model, K: int, jac_format: str = "dense", mixed: boo
     ir = model.ir
     N = ir.N
     n = N + 1
-    # the mixed-precision form passes only the source term's values through
-    # the frontier: the groups recompute the FP32 derivative nodes they share
-    groups, frontier, needs = partition_jacobian(model, K, values_only=mixed)
+    groups, frontier, needs = partition_jacobian(model, K)
     pos, _, _ = jac_layout(model, jac_format)
     slot = {x: n + i for i, x in enumerate(frontier)}
     inputs = {model.C[k]: f"C{k}" for k in range(N)}
