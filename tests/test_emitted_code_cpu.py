@@ -73,7 +73,7 @@ def _compile(src):
     with open(cpp, "w") as f:
         f.write(_SHIM + src[:iw] + src[ij:] + _DRIVER)
     so = os.path.join(d, "gen.so")
-    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
+    subprocess.check_call(["g++", "-O0", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
     L = ctypes.CDLL(so)
     p = ctypes.POINTER(ctypes.c_double)
     L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
@@ -172,7 +172,7 @@ def test_mixed_precision_jacobian_within_fp32_bound(key, slots):
     with open(cpp, "w") as f:
         f.write(_SHIM + _SHIM32 + src[:iw] + s32 + _DRIVER32)
     so = os.path.join(d, "gen.so")
-    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
+    subprocess.check_call(["g++", "-O0", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
     L = ctypes.CDLL(so)
     p = ctypes.POINTER(ctypes.c_double)
     L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
@@ -220,7 +220,7 @@ def test_partitioned_mixed_precision_jacobian_within_fp32_bound(key, K):
     with open(cpp, "w") as f:
         f.write(_SHIM + _SHIM32 + body + drv)
     so = os.path.join(d, "gen.so")
-    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
+    subprocess.check_call(["g++", "-O0", "-shared", "-fPIC", "-ffp-contract=off", "-I", CSRC, "-o", so, cpp])
     L = ctypes.CDLL(so)
     p = ctypes.POINTER(ctypes.c_double)
     L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
@@ -271,7 +271,7 @@ def test_partitioned_jacobian_with_shared_memory_values(key, K, slots):
     with open(cpp, "w") as f:
         f.write(_SHIM + body + drv)
     so = os.path.join(d, "gen.so")
-    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
+    subprocess.check_call(["g++", "-O0", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
     L = ctypes.CDLL(so)
     p = ctypes.POINTER(ctypes.c_double)
     L.eval_cells.argtypes = [ctypes.c_longlong, p, p, p, p, p]
@@ -321,7 +321,7 @@ def test_two_cells_per_thread_body_matches_oracle(key, ncells):
     with open(cpp, "w") as f:
         f.write(_SHIM + src[:iw] + src[ij:] + _DRIVER2)
     so = os.path.join(d, "gen.so")
-    subprocess.check_call(["g++", "-O1", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
+    subprocess.check_call(["g++", "-O0", "-shared", "-fPIC", "-ffp-contract=off", "-o", so, cpp])
     L = ctypes.CDLL(so)
     p = ctypes.POINTER(ctypes.c_double)
     L.eval_cells2.argtypes = [ctypes.c_longlong, p, p, p, p, p]
