@@ -38,6 +38,15 @@ struct qss_mech_s {
   CUfunction f_prefix32 = nullptr;
   std::vector<CUmodule> mod_group32;
   std::vector<CUfunction> f_group32;
+  // the column groups run side by side: group 0 on the caller's stream,
+  // group i > 0 on gst[i - 1], forked after the prefix (ev_fork) and joined
+  // back (ev_join) before anything later on the caller's stream; the fork
+  // is enqueued under fork_mu (the streams and events are the handle's).
+  // Empty gst: the groups run one after another on the caller's stream.
+  std::vector<CUstream> gst;
+  CUevent ev_fork = nullptr;
+  std::vector<CUevent> ev_join;
+  std::mutex fork_mu;
   // frontier scratch of the device-array path; fr_done orders its reuse
   // across streams (recorded after each call's last group kernel)
   CUdeviceptr fr_scratch = 0;

@@ -123,10 +123,25 @@ int jac_launch(qss_mech_s* m, int64_t ncells, int64_t ld, const double* rho, con
   const unsigned smem = mixed ? 0u : m->jac_smem;
   if ((rc = launch_cells(m, mixed ? m->f_prefix32 : m->f_prefix, ncells, m->block, pa, s, smem))) return rc;
   const double* frc = fr;
+  // the groups only read the frontier and write disjoint Jacobian entries:
+  // run them side by side (a few straggler cells in late Newton iterations
+  // then cost one group's latency instead of K), joined back into s before
+  // the frontier is written again
+  const bool fork = (int)m->gst.size() == m->jac_parts - 1 && m->ev_fork;
+  std::unique_lock<std::mutex> lk(m->fork_mu, std::defer_lock);
+  if (fork) {
+    lk.lock();
+    CU_TRY(drv().cuEventRecord(m->ev_fork, s));
+  }
   for (int i = 0; i < m->jac_parts; ++i) {
     void* ga[] = {&nc, &frc, &fl, &jac, &l, &nact};
-    if ((rc = launch_cells(m, mixed ? m->f_group32[i] : m->f_group[i], ncells, m->block, ga, s, smem))) return rc;
+    const CUstream gs = (fork && i > 0) ? m->gst[i - 1] : s;
+    if (gs != s) CU_TRY(drv().cuStreamWaitEvent(gs, m->ev_fork, 0));
+    if ((rc = launch_cells(m, mixed ? m->f_group32[i] : m->f_group[i], ncells, m->block, ga, gs, smem))) return rc;
+    if (gs != s) CU_TRY(drv().cuEventRecord(m->ev_join[i - 1], gs));
   }
+  if (fork)
+    for (int i = 0; i + 1 < m->jac_parts; ++i) CU_TRY(drv().cuStreamWaitEvent(s, m->ev_join[i], 0));
   return QSS_OK;
 }
 
@@ -347,6 +362,27 @@ int qss_mech_load(const char* artefact_dir, int device, qss_mech_t* out) {
             CUDA_SUCCESS)
       m->upd_grid_max[i] = (int64_t)sms * std::max(upd_per_sm, 0);
   }
+  // streams and events of the side-by-side column groups (without them the
+  // groups run in sequence)
+  if (m->jac_parts >= 2) {
+    bool ok = drv().cuEventCreate(&m->ev_fork, CU_EVENT_DISABLE_TIMING) == CUDA_SUCCESS;
+    for (int i = 0; ok && i + 1 < m->jac_parts; ++i) {
+      CUstream st = nullptr;
+      CUevent ev = nullptr;
+      ok = drv().cuStreamCreate(&st, CU_STREAM_NON_BLOCKING) == CUDA_SUCCESS;
+      if (ok) m->gst.push_back(st);
+      ok = ok && drv().cuEventCreate(&ev, CU_EVENT_DISABLE_TIMING) == CUDA_SUCCESS;
+      if (ok) m->ev_join.push_back(ev);
+    }
+    if (!ok) {   // partial set: release it and run the groups in sequence
+      for (CUstream st : m->gst) drv().cuStreamDestroy(st);
+      for (CUevent ev : m->ev_join) drv().cuEventDestroy(ev);
+      if (m->ev_fork) drv().cuEventDestroy(m->ev_fork);
+      m->gst.clear();
+      m->ev_join.clear();
+      m->ev_fork = nullptr;
+    }
+  }
   *out = m;
   return QSS_OK;
 }
@@ -362,6 +398,9 @@ void qss_mech_free(qss_mech_t m) {
   if (m->newton_done) drv().cuEventDestroy(m->newton_done);
   if (m->fr_scratch) drv().cuMemFree(m->fr_scratch);
   if (m->fr_done) drv().cuEventDestroy(m->fr_done);
+  for (CUstream st : m->gst) drv().cuStreamDestroy(st);
+  for (CUevent ev : m->ev_join) drv().cuEventDestroy(ev);
+  if (m->ev_fork) drv().cuEventDestroy(m->ev_fork);
   if (m->mod_prefix) drv().cuModuleUnload(m->mod_prefix);
   for (CUmodule g : m->mod_group)
     if (g) drv().cuModuleUnload(g);
