@@ -164,7 +164,13 @@ int qss_jacobian(qss_mech_t mech, int64_t ncells, int64_t ld, const double* rho,
  * device cannot hold the buffer, qss_jacobian halves the chunk (down to 32
  * cells) and lowers the limit to what fitted.  No effect for a single-kernel
  * Jacobian.  Errors: QSS_ERR_INVALID_ARG if the limit holds fewer than 32
- * cells. */
+ * cells.
+ * The column groups of each chunk run side by side: the first on the
+ * caller's stream, the others on streams the handle creates at load, forked
+ * by an event recorded on the caller's stream after the prefix kernel and
+ * joined back into it before the call returns, so the call stays ordered on
+ * the caller's stream (and a stream capture records the groups as parallel
+ * branches).  The fork is enqueued under a lock of the handle. */
 int qss_mech_set_frontier_bytes(qss_mech_t mech, size_t bytes);
 
 /* Size limit in bytes of the handle's Newton scratch, used by
