@@ -55,7 +55,7 @@ def parse():
                    help="Jacobian as a prefix + this many column-group kernels (default: per workload)")
     p.add_argument("--jac-format", default="dense", choices=["dense", "csr"],
                    help="store every Jacobian entry or only the structural nonzeros")
-    p.add_argument("--serve-seconds", type=float, default=8.0)
+    p.add_argument("--serve-seconds", type=float, default=16.0)
     p.add_argument("--fp64-probe", action="store_true",
                    help="print the FP64 pipe probe grid (latency, warps per SM, active lanes) and exit")
     p.add_argument("--memory-study", action="store_true",
